@@ -1,0 +1,198 @@
+/*
+ * qb.h -- C ABI of the GB300 fixed-precision randomized QB library.
+ *
+ * The library computes A ~= Q B with Q (m x rank) orthonormal, B = Q^T A (rank x n), and picks the
+ * rank adaptively so that ||A - QB||_F < eps, using the error indicator of Theorem 1:
+ * E = ||A||_F^2 - sum_i ||B_i||_F^2 (Algorithm 1), updated row by row (Sect. 3.1).
+ * Two generators of the blocks Q_i, B_i are offered (Yu, Gu, Li, arXiv:1606.09402):
+ *   randQB_EI  (Algorithm 2): per block, sketch A Omega_i, project against Q, orthonormalise,
+ *              re-orthogonalise, B_i = Q_i^T A.  2 + 2P passes over A per block.
+ *   randQB_FP  (Algorithm 4): G = A Omega and H = A^T G for l~ columns at once (one pass over a
+ *              row-major A, Remark 4.2), then the blocked loop builds Q, B from G, H, Omega only
+ *              (the re-orthogonalised B_i formula of Sect. 4.2).  1 + 2P passes per Omega batch.
+ *
+ * Conventions shared by every entry point
+ *   - All matrix pointers are DEVICE pointers unless stated otherwise; the caller owns every
+ *     buffer (A, Q, B, workspace).  The library never allocates device memory.
+ *   - Dense A is row-major: element (i, j) at a[i * ld + j], ld >= n.
+ *   - Q is column-major m x rank_cap: element (i, j) at Q[i + j * ldq], ldq >= m.
+ *   - B is row-major rank_cap x n:    element (i, j) at B[i * ldb + j], ldb >= n.
+ *   - Q and B are double when opts.prec == QB_PREC_FP64 and float when QB_PREC_MIXED.
+ *   - Work is ordered on the given CUDA stream (a cudaStream_t passed as void*, NULL = legacy
+ *     default stream).  The tolerance test needs E on the host once per block, so the call
+ *     synchronises that stream once per block and returns after all its work has completed.
+ *   - Omega is defined by opts.seed alone: Omega(j, c) is a Philox4x32-10 Box-Muller normal of
+ *     row j and global column c (block i of EI and batch q of FP address the same columns).
+ *   - Return value: negative = error, no valid output; 0 = converged; positive = valid output with
+ *     a warning (QB_NOT_CONVERGED: rank cap or Omega budget reached first, Q and B hold the
+ *     valid partial factorisation of info->rank columns; QB_WARN_TOL_FLOOR: the tolerance is
+ *     below the Theorem 3 floor sqrt(4 u / 0.01) ||A||_F, so E may be inaccurate).
+ */
+#ifndef GB300_QB_H
+#define GB300_QB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    QB_OK = 0,
+    QB_NOT_CONVERGED = 1,
+    QB_WARN_TOL_FLOOR = 2,
+    QB_ERR_INVALID_ARG = -1,
+    QB_ERR_NONFINITE = -2,   /* A holds NaN or Inf */
+    QB_ERR_CUDA = -3,        /* a CUDA call failed; qb_last_cuda_error() names it */
+    QB_ERR_BREAKDOWN = -4,   /* reserved: panel factorisation produced non-finite values */
+    QB_ERR_WORKSPACE = -5,   /* ws_bytes below the matching *_workspace() query */
+    QB_ERR_TIMEOUT = -6,     /* a bounded device-side wait ran out (batched path) */
+    QB_ERR_UNSUPPORTED = -7  /* dtype / precision combination not provided */
+} qb_status;
+
+/* status_bits in qb_info */
+#define QB_BIT_BREAKDOWN 1      /* a Cholesky pivot fell below the breakdown threshold and was clamped */
+#define QB_BIT_TOL_FLOOR 2      /* tolerance below the Theorem 3 floor */
+#define QB_BIT_NOT_CONVERGED 4  /* rank cap reached before E < eps^2 */
+
+typedef enum { QB_F64 = 0, QB_F32 = 1, QB_BF16 = 2, QB_BF16X2 = 3 } qb_dtype;
+
+typedef enum {
+    QB_PREC_FP64 = 0,  /* every step in float64 (A must be QB_F64 or CSR float64) */
+    QB_PREC_MIXED = 1  /* BF16 tensor-core passes over A, float32 Q/B, float64 indicator,
+                          float64 b x b Cholesky and triangular inverse */
+} qb_prec;
+
+/* Dense row-major A.  dtype QB_BF16X2 stores A = a_hi + a_lo as two bf16 arrays with the same
+ * ld (see qb_quantize_bf16x2); sketch passes read a_hi only, the passes that form B_i (EI) or
+ * H (FP) read both.  src_norm2 = ||A_src||_F^2 of the float64 source the bf16 arrays were made
+ * from; pass a NaN to have the library compute ||A||_F^2 from the stored A. */
+typedef struct {
+    int64_t m, n, ld;
+    int32_t dtype;
+    int32_t reserved;
+    const void* a;
+    const void* a_lo;
+    double src_norm2;
+} qb_dense;
+
+/* CSR A: rowptr[m+1], colind[nnz] (int32, zero-based, any order inside a row), val[nnz] of
+ * dtype QB_F64 or QB_F32. */
+typedef struct {
+    int64_t m, n, nnz;
+    const int32_t* rowptr;
+    const int32_t* colind;
+    int32_t dtype;
+    int32_t reserved;
+    const void* val;
+} qb_csr;
+
+typedef struct {
+    double tol;          /* eps (absolute) or eps / ||A||_F when relative != 0 (Sect. 5.4) */
+    int32_t relative;    /* nonzero: eps = tol * ||A||_F */
+    int32_t b;           /* block size, 1 <= b <= 64 */
+    int32_t P;           /* power parameter, 0 <= P <= 8 */
+    int32_t row_by_row;  /* nonzero: stop at the row of B_i that meets the tolerance (Sect. 3.1) */
+    uint64_t seed;       /* Omega seed (Philox key) */
+    int64_t rank_cap;    /* capacity of Q and B in columns/rows; <= 0 means min(m, n) */
+    int64_t l_tilde;     /* FP only: Omega batch width; <= 0 means 50 b (Sect. 5.4) */
+    int32_t prec;        /* qb_prec */
+    int32_t flags;       /* reserved, 0 */
+} qb_opts;
+
+typedef struct {
+    int64_t rank;        /* columns of Q / rows of B that are valid */
+    double err2_est;     /* E at exit (may be slightly negative through rounding) */
+    double err_est;      /* sqrt(max(E, 0)) */
+    double normA2;       /* ||A||_F^2 used by the indicator */
+    int64_t passes;      /* passes over A (Table 1 accounting) */
+    int64_t omega_cols;  /* global Omega columns drawn */
+    int32_t status_bits; /* QB_BIT_* */
+    int32_t blocks;      /* blocks of the loop that ran */
+    int64_t launches;    /* kernels launched by this call */
+} qb_info;
+
+/* Human-readable name of a qb_status value. Never NULL. */
+const char* qb_status_str(int32_t status);
+
+/* Name of the last CUDA error seen by the library in this process ("" if none). */
+const char* qb_last_cuda_error(void);
+
+/* Total kernels launched by the library in this process (all calls). */
+int64_t qb_launch_count(void);
+
+/* ---------------------------------------------------------------------------------------------
+ * Dense fixed-precision QB.  algo: 0 = randQB_EI (Algorithm 2), 1 = randQB_FP (Algorithm 4).
+ * Workspace: bytes needed for (A shape, opts, algo); returns 0 on invalid arguments.
+ * Q: ldq >= m, capacity rank_cap columns; B: ldb >= n, capacity rank_cap rows.
+ * ------------------------------------------------------------------------------------------- */
+size_t qb_dense_workspace(const qb_dense* A, const qb_opts* opts, int32_t algo);
+
+/* randQB_EI, Algorithm 2 with the row-by-row stop of Sect. 3.1 and, for P > 0, the power
+ * scheme applied per block to the implicit residual A - QB. */
+int32_t qb_ei_dense(const qb_dense* A, const qb_opts* opts, void* Q, int64_t ldq, void* B,
+                    int64_t ldb, void* ws, size_t ws_bytes, qb_info* info, void* stream);
+
+/* randQB_FP, Algorithm 4 (power scheme on the whole Omega batch, one pass for G = A Omega and
+ * H = A^T G, blocked loop with the re-orthogonalised B_i of Sect. 4.2).  When l~ columns do not
+ * reach the tolerance the next batch of l~ global Omega columns is drawn (Sect. 4.3), its power
+ * iterations act on the implicit residual, and the loop continues with the same Q, B. */
+int32_t qb_fp_dense(const qb_dense* A, const qb_opts* opts, void* Q, int64_t ldq, void* B,
+                    int64_t ldb, void* ws, size_t ws_bytes, qb_info* info, void* stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * Sparse CSR A (the sparse experiments of Sect. 5.1).  Same semantics as the dense calls; the
+ * workspace holds a CSC copy of A built on the device for the A^T products.
+ * ------------------------------------------------------------------------------------------- */
+size_t qb_csr_workspace(const qb_csr* A, const qb_opts* opts, int32_t algo);
+int32_t qb_ei_csr(const qb_csr* A, const qb_opts* opts, void* Q, int64_t ldq, void* B,
+                  int64_t ldb, void* ws, size_t ws_bytes, qb_info* info, void* stream);
+int32_t qb_fp_csr(const qb_csr* A, const qb_opts* opts, void* Q, int64_t ldq, void* B,
+                  int64_t ldb, void* ws, size_t ws_bytes, qb_info* info, void* stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * Single passes over dense A (the hot step of both algorithms, exposed for measurement and
+ * verification).  Same kernels the drivers use; float64 A runs the float64 kernels, bf16 / bf16x2
+ * A the tensor-core kernels (float32 V and outputs).
+ *   qb_apass_sketch: Y (m x w, column-major, ldy) = A V, V n x w column-major (ldv)
+ *                    (G = A Omega of Algorithm 4, A Omega_i of Algorithm 2); a bf16x2 A is read
+ *                    through its hi part only.
+ *   qb_apass_trans:  Z (n x w, column-major, ldz) = A^T V, V m x w column-major (ldv)
+ *                    (H = A^T G of Algorithm 4, B_i^T = A^T Q_i of Algorithm 2).  precise != 0
+ *                    with a bf16x2 A accumulates A_hi V_hi + A_hi V_lo + A_lo V_hi, V split into
+ *                    bf16 hi + lo on the fly; otherwise A_hi bf16(V).
+ * Workspace: qb_apass_workspace(A, w) bytes.
+ * ------------------------------------------------------------------------------------------- */
+size_t qb_apass_workspace(const qb_dense* A, int64_t w);
+int32_t qb_apass_sketch(const qb_dense* A, const void* V, int64_t ldv, int64_t w, void* Y,
+                        int64_t ldy, void* ws, size_t ws_bytes, void* stream);
+int32_t qb_apass_trans(const qb_dense* A, const void* V, int64_t ldv, int64_t w, int32_t precise,
+                       void* Z, int64_t ldz, void* ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * Omega generator (exposed for verification).  Writes Omega rows 0..n-1, global columns
+ * col0..col0+w-1 column-major into out (ld >= n), dtype QB_F64 (float64 Box-Muller on 53-bit
+ * uniforms), QB_F32 (float32 Box-Muller on 24-bit uniforms) or QB_BF16 (the QB_F32 value
+ * rounded to nearest even).
+ * ------------------------------------------------------------------------------------------- */
+int32_t qb_omega(int64_t n, int64_t col0, int64_t w, uint64_t seed, int32_t dtype, void* out,
+                 int64_t ld, void* stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * Quantisation of a float64 row-major source into bf16 hi + lo arrays (A = hi + lo to ~2^-17
+ * relative per entry), with the float64 norms the mixed path needs:
+ *   norms[0] = ||A_src||_F^2, norms[1] = ||A_src - hi - lo||_F^2, norms[2] = ||A_src - hi||_F^2.
+ * norms is a HOST pointer (3 doubles); the call synchronises the stream.  ws must hold
+ * qb_quantize_workspace() bytes.
+ * ------------------------------------------------------------------------------------------- */
+size_t qb_quantize_workspace(int64_t m, int64_t n);
+int32_t qb_quantize_bf16x2(const double* src, int64_t m, int64_t n, int64_t ld_src, void* hi,
+                           void* lo, int64_t ld, double* norms, void* ws, size_t ws_bytes,
+                           void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GB300_QB_H */

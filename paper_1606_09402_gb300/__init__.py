@@ -1,0 +1,295 @@
+"""GB300-native fixed-precision randomized QB factorisation (randQB_EI / randQB_FP).
+
+Thin Python binding over the C ABI of libqb.so (include/qb.h): it only marshals arguments.
+PyTorch provides device memory and the current CUDA stream; every step of the factorisation
+runs in the library's CUDA kernels.
+
+    Q, B, info = qb_fp_dense(A, tol=1e-3, b=64, P=1, seed=9402)         # float64 A
+    hi, lo, norms = quantize_bf16x2(A64)                                    # mixed precision
+    Q, B, info = qb_fp_dense(hi, tol=1e-3, b=64, P=1, seed=9402, a_lo=lo,
+                             src_norm2=norms[0], prec="mixed")
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+from . import _lib
+
+__all__ = ["qb_ei_dense", "qb_fp_dense", "qb_ei_csr", "qb_fp_csr", "qb_omega",
+           "quantize_bf16x2", "qb_apass_sketch", "qb_apass_trans", "QBError", "QBInfo",
+           "launch_count", "status_str"]
+
+
+class QBError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        lib = _lib.load()
+        msg = lib.qb_status_str(code).decode()
+        if code == _lib.QB_ERR_CUDA:
+            msg += " (" + lib.qb_last_cuda_error().decode() + ")"
+        super().__init__(f"{where}: {msg}")
+        self.code = code
+
+
+@dataclass
+class QBInfo:
+    status: int
+    rank: int
+    err2_est: float
+    err_est: float
+    normA2: float
+    passes: int
+    omega_cols: int
+    status_bits: int
+    blocks: int
+    launches: int
+
+    @property
+    def converged(self) -> bool:
+        return self.status in (_lib.QB_OK, _lib.QB_WARN_TOL_FLOOR)
+
+
+def status_str(code: int) -> str:
+    return _lib.load().qb_status_str(code).decode()
+
+
+def launch_count() -> int:
+    return int(_lib.load().qb_launch_count())
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dtype_code(t) -> int:
+    torch = _torch()
+    return {torch.float64: _lib.QB_F64, torch.float32: _lib.QB_F32,
+            torch.bfloat16: _lib.QB_BF16}[t.dtype]
+
+
+def _opts(tol, b, P, seed, relative, rank_cap, l_tilde, row_by_row, prec):
+    return _lib.qb_opts(tol=float(tol), relative=int(bool(relative)), b=int(b), P=int(P),
+                        row_by_row=int(bool(row_by_row)), seed=int(seed) & ((1 << 64) - 1),
+                        rank_cap=int(rank_cap or 0), l_tilde=int(l_tilde or 0),
+                        prec=_lib.QB_PREC_MIXED if prec == "mixed" else _lib.QB_PREC_FP64,
+                        flags=0)
+
+
+def _check_dev(*ts):
+    for t in ts:
+        if t is not None and not t.is_cuda:
+            raise ValueError("tensors must live on a CUDA device")
+
+
+def _alloc_out(m, n, cap, prec, device, out):
+    torch = _torch()
+    dt = torch.float64 if prec != "mixed" else torch.float32
+    if out is not None:
+        Q, B = out
+        assert Q.dtype == dt and B.dtype == dt and Q.shape[1] == m and B.shape[1] == n
+        assert Q.shape[0] >= cap and B.shape[0] >= cap
+        return Q, B
+    # Q is column-major m x cap: stored as a (cap, m) row-major tensor (Q^T)
+    Qt = torch.empty(max(cap, 1), m, dtype=dt, device=device)
+    B = torch.empty(max(cap, 1), n, dtype=dt, device=device)
+    return Qt, B
+
+
+def _info(rc, inf):
+    return QBInfo(rc, int(inf.rank), float(inf.err2_est), float(inf.err_est), float(inf.normA2),
+                  int(inf.passes), int(inf.omega_cols), int(inf.status_bits), int(inf.blocks),
+                  int(inf.launches))
+
+
+def _dense_call(fn, name, A, tol, b, P, seed, relative, rank_cap, l_tilde, row_by_row, prec,
+                a_lo, src_norm2, stream, out, workspace):
+    torch = _torch()
+    lib = _lib.load()
+    _check_dev(A, a_lo)
+    assert A.dim() == 2 and A.stride(1) == 1, "A must be row-major (contiguous rows)"
+    m, n = A.shape
+    if a_lo is not None:
+        assert a_lo.shape == A.shape and a_lo.stride() == A.stride() and a_lo.dtype == torch.bfloat16
+        dt = _lib.QB_BF16X2
+    else:
+        dt = _dtype_code(A)
+    d = _lib.qb_dense(m=m, n=n, ld=A.stride(0), dtype=dt, reserved=0, a=A.data_ptr(),
+                      a_lo=a_lo.data_ptr() if a_lo is not None else None,
+                      src_norm2=float("nan") if src_norm2 is None else float(src_norm2))
+    o = _opts(tol, b, P, seed, relative, rank_cap, l_tilde, row_by_row, prec)
+    algo = 1 if name.startswith("qb_fp") else 0
+    wsb = lib.qb_dense_workspace(C.byref(d), C.byref(o), algo)
+    if wsb == 0:
+        raise QBError(_lib.QB_ERR_INVALID_ARG, name + " workspace query")
+    cap = min(m, n) if not rank_cap or rank_cap <= 0 else min(m, n, int(rank_cap))
+    Qt, B = _alloc_out(m, n, cap, prec, A.device, out)
+    ws = workspace if workspace is not None and workspace.numel() >= wsb else \
+        torch.empty(wsb, dtype=torch.uint8, device=A.device)
+    inf = _lib.qb_info()
+    with torch.cuda.device(A.device):
+        rc = fn(C.byref(d), C.byref(o), C.c_void_p(Qt.data_ptr()), Qt.stride(0),
+                C.c_void_p(B.data_ptr()), B.stride(0), C.c_void_p(ws.data_ptr()), ws.numel(),
+                C.byref(inf), _stream_ptr(stream))
+    if rc < 0:
+        raise QBError(rc, name)
+    info = _info(rc, inf)
+    k = info.rank
+    return Qt[:k].T, B[:k], info
+
+
+def qb_ei_dense(A, tol, b, P=0, seed=0, relative=True, rank_cap=None, row_by_row=True,
+                prec="fp64", a_lo=None, src_norm2=None, stream=None, out=None, workspace=None):
+    """randQB_EI (Algorithm 2) on a dense row-major A; returns (Q, B, QBInfo).
+
+    Q is an m x rank view (column-major storage), B a rank x n row-major view."""
+    return _dense_call(_lib.load().qb_ei_dense, "qb_ei_dense", A, tol, b, P, seed, relative,
+                       rank_cap, None, row_by_row, prec, a_lo, src_norm2, stream, out, workspace)
+
+
+def qb_fp_dense(A, tol, b, P=0, seed=0, relative=True, rank_cap=None, l_tilde=None,
+                row_by_row=True, prec="fp64", a_lo=None, src_norm2=None, stream=None, out=None,
+                workspace=None):
+    """randQB_FP (Algorithm 4) on a dense row-major A; returns (Q, B, QBInfo)."""
+    return _dense_call(_lib.load().qb_fp_dense, "qb_fp_dense", A, tol, b, P, seed, relative,
+                       rank_cap, l_tilde, row_by_row, prec, a_lo, src_norm2, stream, out,
+                       workspace)
+
+
+def _csr_call(fn, name, rowptr, colind, val, shape, tol, b, P, seed, relative, rank_cap, l_tilde,
+              row_by_row, stream, workspace):
+    torch = _torch()
+    lib = _lib.load()
+    _check_dev(rowptr, colind, val)
+    assert rowptr.dtype == torch.int32 and colind.dtype == torch.int32
+    m, n = shape
+    prec = "fp64" if val.dtype == torch.float64 else "mixed"
+    s = _lib.qb_csr(m=m, n=n, nnz=colind.numel(), rowptr=rowptr.data_ptr(),
+                    colind=colind.data_ptr(), dtype=_dtype_code(val), reserved=0,
+                    val=val.data_ptr())
+    o = _opts(tol, b, P, seed, relative, rank_cap, l_tilde, row_by_row, prec)
+    algo = 1 if name.startswith("qb_fp") else 0
+    wsb = lib.qb_csr_workspace(C.byref(s), C.byref(o), algo)
+    if wsb == 0:
+        raise QBError(_lib.QB_ERR_INVALID_ARG, name + " workspace query")
+    cap = min(m, n) if not rank_cap or rank_cap <= 0 else min(m, n, int(rank_cap))
+    Qt, B = _alloc_out(m, n, cap, prec, val.device, None)
+    ws = workspace if workspace is not None and workspace.numel() >= wsb else \
+        torch.empty(wsb, dtype=torch.uint8, device=val.device)
+    inf = _lib.qb_info()
+    with torch.cuda.device(val.device):
+        rc = fn(C.byref(s), C.byref(o), C.c_void_p(Qt.data_ptr()), Qt.stride(0),
+                C.c_void_p(B.data_ptr()), B.stride(0), C.c_void_p(ws.data_ptr()), ws.numel(),
+                C.byref(inf), _stream_ptr(stream))
+    if rc < 0:
+        raise QBError(rc, name)
+    info = _info(rc, inf)
+    k = info.rank
+    return Qt[:k].T, B[:k], info
+
+
+def qb_ei_csr(rowptr, colind, val, shape, tol, b, P=0, seed=0, relative=True, rank_cap=None,
+              row_by_row=True, stream=None, workspace=None):
+    """randQB_EI on a CSR matrix (int32 indices; float64 values -> fp64 path, float32 -> mixed)."""
+    return _csr_call(_lib.load().qb_ei_csr, "qb_ei_csr", rowptr, colind, val, shape, tol, b, P,
+                     seed, relative, rank_cap, None, row_by_row, stream, workspace)
+
+
+def qb_fp_csr(rowptr, colind, val, shape, tol, b, P=0, seed=0, relative=True, rank_cap=None,
+              l_tilde=None, row_by_row=True, stream=None, workspace=None):
+    """randQB_FP on a CSR matrix."""
+    return _csr_call(_lib.load().qb_fp_csr, "qb_fp_csr", rowptr, colind, val, shape, tol, b, P,
+                     seed, relative, rank_cap, l_tilde, row_by_row, stream, workspace)
+
+
+def qb_omega(n, col0, w, seed, dtype=None, device="cuda", stream=None):
+    """Omega rows 0..n-1, global columns col0..col0+w-1, as an n x w tensor (column-major)."""
+    torch = _torch()
+    dtype = dtype or torch.float64
+    out_t = torch.empty(max(w, 1), max(n, 1), dtype=dtype, device=device)  # Omega^T row-major
+    rc = _lib.load().qb_omega(n, col0, w, int(seed) & ((1 << 64) - 1), _dtype_code(out_t),
+                              C.c_void_p(out_t.data_ptr()), out_t.stride(0), _stream_ptr(stream))
+    if rc < 0:
+        raise QBError(rc, "qb_omega")
+    return out_t[:w, :n].T
+
+
+def quantize_bf16x2(A, stream=None):
+    """float64 row-major A -> (hi, lo, norms) with A ~= hi + lo (bf16 each) and
+    norms = (||A||^2, ||A - hi - lo||^2, ||A - hi||^2) in float64."""
+    torch = _torch()
+    _check_dev(A)
+    assert A.dtype == torch.float64 and A.stride(1) == 1
+    m, n = A.shape
+    hi = torch.empty(m, n, dtype=torch.bfloat16, device=A.device)
+    lo = torch.empty(m, n, dtype=torch.bfloat16, device=A.device)
+    lib = _lib.load()
+    wsb = lib.qb_quantize_workspace(m, n)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=A.device)
+    norms = (C.c_double * 3)()
+    rc = lib.qb_quantize_bf16x2(C.c_void_p(A.data_ptr()), m, n, A.stride(0),
+                                C.c_void_p(hi.data_ptr()), C.c_void_p(lo.data_ptr()), n, norms,
+                                C.c_void_p(ws.data_ptr()), wsb, _stream_ptr(stream))
+    if rc < 0:
+        raise QBError(rc, "qb_quantize_bf16x2")
+    return hi, lo, tuple(float(x) for x in norms)
+
+
+def _dense_desc(A, a_lo=None, src_norm2=None):
+    torch = _torch()
+    assert A.dim() == 2 and A.stride(1) == 1, "A must be row-major (contiguous rows)"
+    m, n = A.shape
+    if a_lo is not None:
+        assert a_lo.shape == A.shape and a_lo.stride() == A.stride() and a_lo.dtype == torch.bfloat16
+        dt = _lib.QB_BF16X2
+    else:
+        dt = _dtype_code(A)
+    return _lib.qb_dense(m=m, n=n, ld=A.stride(0), dtype=dt, reserved=0, a=A.data_ptr(),
+                         a_lo=a_lo.data_ptr() if a_lo is not None else None,
+                         src_norm2=float("nan") if src_norm2 is None else float(src_norm2))
+
+
+def _apass(trans, A, V, precise, a_lo, stream):
+    torch = _torch()
+    lib = _lib.load()
+    _check_dev(A, V, a_lo)
+    d = _dense_desc(A, a_lo)
+    m, n = A.shape
+    rows_in, rows_out = (m, n) if trans else (n, m)
+    w = V.shape[1]
+    assert V.shape[0] == rows_in
+    out_dt = torch.float64 if A.dtype == torch.float64 else torch.float32
+    Vt = V.T.contiguous().to(out_dt)            # column-major V stored as V^T row-major
+    Yt = torch.empty(max(w, 1), rows_out, dtype=out_dt, device=A.device)
+    wsb = lib.qb_apass_workspace(C.byref(d), w)
+    if wsb == 0:
+        raise QBError(_lib.QB_ERR_INVALID_ARG, "qb_apass_workspace")
+    ws = torch.empty(wsb, dtype=torch.uint8, device=A.device)
+    with torch.cuda.device(A.device):
+        if trans:
+            rc = lib.qb_apass_trans(C.byref(d), C.c_void_p(Vt.data_ptr()), rows_in, w,
+                                    int(bool(precise)), C.c_void_p(Yt.data_ptr()), rows_out,
+                                    C.c_void_p(ws.data_ptr()), wsb, _stream_ptr(stream))
+        else:
+            rc = lib.qb_apass_sketch(C.byref(d), C.c_void_p(Vt.data_ptr()), rows_in, w,
+                                     C.c_void_p(Yt.data_ptr()), rows_out,
+                                     C.c_void_p(ws.data_ptr()), wsb, _stream_ptr(stream))
+    if rc < 0:
+        raise QBError(rc, "qb_apass_trans" if trans else "qb_apass_sketch")
+    return Yt[:w].T
+
+
+def qb_apass_sketch(A, V, a_lo=None, stream=None):
+    """Y = A V (one pass over a dense row-major A; float32 V/Y for bf16 A, float64 otherwise)."""
+    return _apass(False, A, V, False, a_lo, stream)
+
+
+def qb_apass_trans(A, V, precise=True, a_lo=None, stream=None):
+    """Z = A^T V (one pass over a dense row-major A); ``precise`` uses the hi/lo products."""
+    return _apass(True, A, V, precise, a_lo, stream)

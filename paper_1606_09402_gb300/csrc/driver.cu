@@ -1,0 +1,757 @@
+// Host drivers of randQB_EI (Algorithm 2) and randQB_FP (Algorithm 4) over the kernels of this
+// library, and the C ABI declared in include/qb.h.
+//
+// The drivers are stream-ordered: all arithmetic runs in the library's kernels; the host only
+// sequences launches and, once per block, reads back {E, rows kept, stop} (24 bytes) to decide
+// whether to continue (Algorithm 1's "if E < eps^2 then stop").
+#include "qb_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+namespace qb {
+
+// ------------------------------------------------------------------------------------ process state
+static std::atomic<int64_t> g_launches{0};
+static char g_last_err[256] = "";
+static std::mutex g_err_mu;
+
+void record_cuda_error(cudaError_t e, const char* where) {
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    std::snprintf(g_last_err, sizeof g_last_err, "%s: %s", where, cudaGetErrorString(e));
+}
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+int64_t launches_total() { return g_launches.load(); }
+
+int num_sms() {
+    static int cache[64] = {0};
+    int dev = 0;
+    QB_CUDA(cudaGetDevice(&dev));
+    if (dev < 64 && cache[dev]) return cache[dev];
+    int v = 0;
+    QB_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev));
+    if (dev < 64) cache[dev] = v;
+    return v;
+}
+
+namespace {
+
+constexpr double U64 = 1.1102230246251565e-16;   // 2^-53
+constexpr double THM3_DELTA = 0.01;
+
+// ------------------------------------------------------------------------------------ context
+struct Ctx {
+    cudaStream_t st = nullptr;
+    bool f64 = true;        // work precision of Q, B, G, H, Omega
+    size_t es = 8;
+    GemmScratch scr;
+    double* W = nullptr;    // 64 x 64 Gram
+    double* R = nullptr;
+    double* Rinv = nullptr;
+    double* Racc = nullptr;
+    double* rn = nullptr;   // 64 row norms
+    double* state = nullptr;  // E, keep, stop, E_prev
+    double* part = nullptr;   // 3 x 1024 reduction partials
+    int* flags = nullptr;     // [0] non-finite, [1] breakdown
+    double tau = 1e-14;       // Cholesky breakdown threshold (relative to max Gram diagonal)
+    Acc acc_gram = ACC_D;     // Grams of panels
+    Acc acc_proj = ACC_D;     // projections / updates
+    Acc acc_fine = ACC_D;     // cancellation-prone products (FP's B_i formula, re-orth coefficients)
+
+    void alloc(Arena& ar, int64_t mn_max) {
+        scr.part_bytes = gemm_scratch_bytes(mn_max);
+        scr.part = ar.get<char>(int64_t(scr.part_bytes));
+        W = ar.get<double>(MAXB * MAXB);
+        R = ar.get<double>(MAXB * MAXB);
+        Rinv = ar.get<double>(MAXB * MAXB);
+        Racc = ar.get<double>(MAXB * MAXB);
+        rn = ar.get<double>(MAXB);
+        state = ar.get<double>(8);
+        part = ar.get<double>(3 * 1024);
+        flags = ar.get<int>(4);
+    }
+    XOp x(const void* p, int64_t ld) const { return XOp{f64 ? X_F64 : X_F32, p, nullptr, ld}; }
+
+    // C (M x N) = alpha * X^T Y + beta C, X (K x M), Y (K x N), work precision, col-major
+    void tn(int64_t M, int64_t N, int64_t K, double alpha, const void* X, int64_t ldx, const void* Y,
+            int64_t ldy, double beta, void* C, int64_t ldc, Acc acc) {
+        if (M <= 0 || N <= 0) return;
+        gemm(st, true, M, N, K, alpha, x(X, ldx), Y, f64, ldy, beta, C, f64, ldc, f64 ? ACC_D : acc, scr);
+    }
+    // C (M x N) = alpha * X Y + beta C, X (M x K), Y (K x N)
+    void nn(int64_t M, int64_t N, int64_t K, double alpha, const void* X, int64_t ldx, const void* Y,
+            int64_t ldy, double beta, void* C, int64_t ldc, Acc acc) {
+        if (M <= 0 || N <= 0) return;
+        gemm(st, false, M, N, K, alpha, x(X, ldx), Y, f64, ldy, beta, C, f64, ldc, f64 ? ACC_D : acc, scr);
+    }
+    void copy_cols_(const void* X, int64_t ldx, int64_t rows, int64_t cols, void* Y, int64_t ldy) {
+        copy_cols(st, f64, X, ldx, rows, cols, Y, ldy);
+    }
+    char* col(void* base, int64_t ld, int64_t j) const {
+        return reinterpret_cast<char*>(base) + size_t(j) * size_t(ld) * es;
+    }
+    const char* col(const void* base, int64_t ld, int64_t j) const {
+        return reinterpret_cast<const char*>(base) + size_t(j) * size_t(ld) * es;
+    }
+
+    // One CholeskyQR pass: W = P^T P (float64 or float32-pair accumulation), W = R^T R,
+    // P <- P R^-1, Racc <- R Racc when acc_r.
+    void cholqr(void* P, int64_t ld, int64_t rows, int bi, bool acc_r) {
+        gemm(st, true, bi, bi, rows, 1.0, x(P, ld), P, f64, ld, 0.0, W, true, MAXB,
+             f64 ? ACC_D : acc_gram, scr);
+        chol_rinv(st, W, bi, tau, R, Rinv, acc_r ? Racc : nullptr, flags);
+        apply_rinv(st, f64, P, ld, rows, bi, Rinv);
+    }
+    // orth(P): CholeskyQR2 (two passes); Racc accumulates R2 R1 when acc_r.
+    void cholqr2(void* P, int64_t ld, int64_t rows, int bi, bool acc_r) {
+        cholqr(P, ld, rows, bi, acc_r);
+        cholqr(P, ld, rows, bi, acc_r);
+    }
+    // P <- P - Qk (Qk^T P), Qk = first k columns of Q (ld ldq); T: k x bi scratch (ld k)
+    void project_out(const void* Q, int64_t ldq, int64_t k, void* P, int64_t ldp, int64_t rows, int bi,
+                     void* T) {
+        if (k <= 0) return;
+        tn(k, bi, rows, 1.0, Q, ldq, P, ldp, 0.0, T, k, acc_fine);
+        nn(rows, bi, k, -1.0, Q, ldq, T, k, 1.0, P, ldp, acc_proj);
+    }
+    // Orthonormalise the rows x w matrix X (column-major) panel by panel: block Gram-Schmidt with
+    // re-orthogonalisation, CholeskyQR2 per panel of width b.  T: w x b scratch.
+    void orth_wide(void* X, int64_t ld, int64_t rows, int64_t w, int b, void* T) {
+        for (int64_t j0 = 0; j0 < w; j0 += b) {
+            const int bj = int(std::min<int64_t>(b, w - j0));
+            char* Pj = col(X, ld, j0);
+            project_out(X, ld, j0, Pj, ld, rows, bj, T);
+            cholqr2(Pj, ld, rows, bj, false);
+            if (j0 > 0) {
+                project_out(X, ld, j0, Pj, ld, rows, bj, T);
+                cholqr2(Pj, ld, rows, bj, false);
+            }
+        }
+    }
+    struct Step { double E; int keep; int stop; };
+    Step indicator_step(const void* Bslot, int64_t ldb, int bi, int64_t n, double eps2, int rbr) {
+        row_norm2(st, f64, Bslot, ldb, bi, n, rn);
+        indicator(st, state, rn, bi, eps2, rbr);
+        double h[3];
+        QB_CUDA(cudaMemcpyAsync(h, state, sizeof h, cudaMemcpyDeviceToHost, st));
+        QB_CUDA(cudaStreamSynchronize(st));
+        return Step{h[0], int(h[1]), int(h[2])};
+    }
+    int read_flags(int* h) {
+        QB_CUDA(cudaMemcpyAsync(h, flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        QB_CUDA(cudaStreamSynchronize(st));
+        return 0;
+    }
+};
+
+// ------------------------------------------------------------------------------------ A operators
+struct AOp {
+    int64_t m = 0, n = 0;
+    virtual ~AOp() = default;
+    virtual void reserve(Arena& ar, const Ctx& c, int64_t wmax) = 0;
+    virtual void prepare(Ctx& c) = 0;
+    // Y (m x w) = A X (X: n x w); sketch passes may use the reduced representation of A
+    virtual void apply(Ctx& c, const void* X, int64_t ldx, int64_t w, void* Y, int64_t ldy) = 0;
+    // Y (n x w) = A^T X (X: m x w); precise = the pass that forms B_i or H
+    virtual void apply_t(Ctx& c, const void* X, int64_t ldx, int64_t w, void* Y, int64_t ldy,
+                         bool precise) = 0;
+    // ||A||_F^2 (float64); non-finite entries raise c.flags[0]
+    virtual double norm2(Ctx& c) = 0;
+    // true when a bounded device-side wait of this operator's kernels ran out
+    virtual bool timed_out(Ctx&) { return false; }
+};
+
+struct DenseOp : AOp {
+    qb_dense d;
+    bool use_tc = false;
+    void* tc_scr = nullptr;
+    size_t tc_bytes = 0;
+    bf16* Xb = nullptr;      // bf16 copy of the sketch operand (tensor-core path)
+    int64_t wmax = 0;
+    explicit DenseOp(const qb_dense& dd) : d(dd) { m = dd.m; n = dd.n; }
+    XOp xa(bool precise) const {
+        switch (d.dtype) {
+            case QB_F64: return XOp{X_F64, d.a, nullptr, d.ld};
+            case QB_F32: return XOp{X_F32, d.a, nullptr, d.ld};
+            case QB_BF16: return XOp{X_BF16, d.a, nullptr, d.ld};
+            default: return precise ? XOp{X_BF16X2, d.a, d.a_lo, d.ld} : XOp{X_BF16, d.a, nullptr, d.ld};
+        }
+    }
+    bool bf16_storage() const { return d.dtype == QB_BF16 || d.dtype == QB_BF16X2; }
+    // The tensor-core path needs TMA-compatible A: 16-byte aligned rows and base, and at least
+    // one full 128-row tile each way.
+    bool tc_ok() const {
+        auto al = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
+        return bf16_storage() && d.ld % 8 == 0 && al(d.a) && (!d.a_lo || al(d.a_lo)) &&
+               m >= 128 && n >= 128;
+    }
+    void reserve(Arena& ar, const Ctx& c, int64_t w) override {
+        wmax = w;
+        use_tc = !c.f64 && tc_ok() && (ar.base == nullptr || tc_available());
+        if (use_tc) {
+            tc_bytes = tc_scratch_bytes(m, n, w);
+            tc_scr = ar.get<char>(int64_t(tc_bytes));
+            Xb = ar.get<bf16>(align_up(n, 8) * w);
+        }
+    }
+    void prepare(Ctx& c) override {
+        if (use_tc) QB_CUDA(cudaMemsetAsync(tc_error_flag(tc_scr), 0, 256, c.st));
+    }
+    bool timed_out(Ctx& c) override {
+        if (!use_tc) return false;
+        int h = 0;
+        QB_CUDA(cudaMemcpyAsync(&h, tc_error_flag(tc_scr), sizeof h, cudaMemcpyDeviceToHost, c.st));
+        QB_CUDA(cudaStreamSynchronize(c.st));
+        return h != 0;
+    }
+    void apply(Ctx& c, const void* X, int64_t ldx, int64_t w, void* Y, int64_t ldy) override {
+        if (use_tc) {
+            const int64_t ldb = align_up(n, 8);
+            to_bf16(c.st, reinterpret_cast<const float*>(X), ldx, n, w, Xb, ldb);
+            tc_sketch(c.st, reinterpret_cast<const bf16*>(d.a), d.ld, m, n, Xb, ldb, w,
+                      reinterpret_cast<float*>(Y), ldy, tc_scr, tc_bytes);
+            return;
+        }
+        // Y = (A viewed column-major n x m)^T X
+        gemm(c.st, true, m, w, n, 1.0, xa(false), X, c.f64, ldx, 0.0, Y, c.f64, ldy,
+             c.f64 ? ACC_D : ACC_F, c.scr);
+    }
+    void apply_t(Ctx& c, const void* X, int64_t ldx, int64_t w, void* Y, int64_t ldy,
+                 bool precise) override {
+        if (use_tc) {
+            tc_trans(c.st, reinterpret_cast<const bf16*>(d.a), reinterpret_cast<const bf16*>(d.a_lo),
+                     d.ld, m, n, reinterpret_cast<const float*>(X), ldx, w,
+                     reinterpret_cast<float*>(Y), ldy, precise && d.dtype == QB_BF16X2, tc_scr,
+                     tc_bytes);
+            return;
+        }
+        gemm(c.st, false, n, w, m, 1.0, xa(precise), X, c.f64, ldx, 0.0, Y, c.f64, ldy,
+             c.f64 ? ACC_D : ACC_F, c.scr);
+    }
+    double norm2(Ctx& c) override {
+        if (!std::isnan(d.src_norm2)) return d.src_norm2;
+        dense_norm2(c.st, xa(true), m, n, c.part, c.state + 4, c.flags);
+        double h = 0;
+        QB_CUDA(cudaMemcpyAsync(&h, c.state + 4, sizeof h, cudaMemcpyDeviceToHost, c.st));
+        QB_CUDA(cudaStreamSynchronize(c.st));
+        return h;
+    }
+};
+
+struct CsrOp : AOp {
+    qb_csr s;
+    int32_t* colptr = nullptr;
+    int32_t* rowind = nullptr;
+    void* cval = nullptr;
+    int32_t* cnt = nullptr;
+    void* stage = nullptr;
+    explicit CsrOp(const qb_csr& ss) : s(ss) { m = ss.m; n = ss.n; }
+    bool f64v() const { return s.dtype == QB_F64; }
+    void reserve(Arena& ar, const Ctx&, int64_t) override {
+        colptr = ar.get<int32_t>(n + 1);
+        rowind = ar.get<int32_t>(s.nnz);
+        cval = ar.get<char>(s.nnz * (f64v() ? 8 : 4));
+        cnt = ar.get<int32_t>(2 * n);
+        stage = ar.get<char>(int64_t(csr_stage_bytes(m, n, f64v())));
+    }
+    void prepare(Ctx& c) override {
+        CsrDev A{m, n, s.nnz, s.rowptr, s.colind, s.val, f64v()};
+        csr_to_csc(c.st, A, colptr, rowind, cval, cnt);
+    }
+    void apply(Ctx& c, const void* X, int64_t ldx, int64_t w, void* Y, int64_t ldy) override {
+        csr_spmm(c.st, f64v(), s.rowptr, s.colind, s.val, m, n, X, ldx, w, Y, ldy, stage);
+    }
+    void apply_t(Ctx& c, const void* X, int64_t ldx, int64_t w, void* Y, int64_t ldy, bool) override {
+        csr_spmm(c.st, f64v(), colptr, rowind, cval, n, m, X, ldx, w, Y, ldy, stage);
+    }
+    double norm2(Ctx& c) override {
+        vec_norm2(c.st, s.val, f64v(), s.nnz, c.part, c.state + 4, c.flags);
+        double h = 0;
+        QB_CUDA(cudaMemcpyAsync(&h, c.state + 4, sizeof h, cudaMemcpyDeviceToHost, c.st));
+        QB_CUDA(cudaStreamSynchronize(c.st));
+        return h;
+    }
+};
+
+// ------------------------------------------------------------------------------------ shared setup
+struct Plan {
+    int64_t m, n, cap, lt;
+    int b, P;
+};
+
+bool valid_opts(const qb_opts* o) {
+    return o && o->b >= 1 && o->b <= MAXB && o->P >= 0 && o->P <= 8 && std::isfinite(o->tol) &&
+           o->tol >= 0.0 && (o->prec == QB_PREC_FP64 || o->prec == QB_PREC_MIXED);
+}
+
+Plan make_plan(int64_t m, int64_t n, const qb_opts& o, bool fp) {
+    Plan p;
+    p.m = m;
+    p.n = n;
+    p.b = o.b;
+    p.P = o.P;
+    p.cap = std::min(m, n);
+    if (o.rank_cap > 0) p.cap = std::min<int64_t>(p.cap, o.rank_cap);
+    p.lt = o.l_tilde > 0 ? o.l_tilde : 50LL * o.b;
+    p.lt = std::max<int64_t>(1, std::min(p.lt, std::max<int64_t>(p.cap, 1)));
+    if (!fp) p.lt = o.b;
+    return p;
+}
+
+void setup_ctx(Ctx& c, bool f64) {
+    c.f64 = f64;
+    c.es = f64 ? 8 : 4;
+    c.tau = f64 ? 1e-14 : 1e-12;
+    c.acc_gram = f64 ? ACC_D : ACC_DF;
+    c.acc_proj = f64 ? ACC_D : ACC_F;
+    c.acc_fine = f64 ? ACC_D : ACC_DF;
+}
+
+struct Bufs {
+    char* Om = nullptr;   // n x lt
+    char* Z = nullptr;    // n x b (EI power) or n x b S (FP)
+    char* G = nullptr;    // m x lt (FP)
+    char* H = nullptr;    // n x lt (FP)
+    char* Ys = nullptr;   // m x b (FP)
+    char* T1 = nullptr;   // cap x lt
+    char* C2 = nullptr;   // cap x b
+    char* Tw = nullptr;   // lt x b (orth_wide)
+};
+
+void reserve_all(Arena& ar, Ctx& c, AOp& A, const Plan& p, bool fp, Bufs& bf) {
+    const int64_t es = int64_t(c.es);
+    const int64_t wmax = fp ? p.lt : p.b;
+    c.alloc(ar, std::max({p.m, p.n, p.cap, wmax}) * std::max<int64_t>(wmax, p.b));
+    bf.Om = ar.get<char>(p.n * wmax * es);
+    bf.Z = ar.get<char>(p.n * p.b * es);
+    bf.T1 = ar.get<char>(std::max<int64_t>(p.cap, 1) * wmax * es);
+    bf.C2 = ar.get<char>(std::max<int64_t>(p.cap, 1) * p.b * es);
+    if (fp) {
+        bf.G = ar.get<char>(p.m * p.lt * es);
+        bf.H = ar.get<char>(p.n * p.lt * es);
+        bf.Ys = ar.get<char>(p.m * p.b * es);
+        bf.Tw = ar.get<char>(p.lt * p.b * es);
+    }
+    A.reserve(ar, c, wmax);
+}
+
+struct RunOut {
+    int64_t rank = 0;
+    double E = 0, normA2 = 0;
+    int64_t passes = 0, omega_cols = 0;
+    int blocks = 0;
+    bool converged = false;
+};
+
+// ------------------------------------------------------------------------------------ randQB_EI
+void run_ei(Ctx& c, AOp& A, const Plan& p, const qb_opts& o, Bufs& bf, void* Q, int64_t ldq,
+            void* B, int64_t ldb, double eps2, RunOut& out) {
+    const int64_t m = p.m, n = p.n;
+    int64_t k = 0;
+    const int omega_dt = c.f64 ? QB_F64 : QB_F32;
+    while (k < p.cap) {
+        const int bi = int(std::min<int64_t>(p.b, p.cap - k));
+        out.omega_cols = k + bi;
+        // Omega_i = randn(n, b), global columns [k, k + bi)
+        omega_gen(c.st, n, k, bi, o.seed, omega_dt, bf.Om, n);
+        // Y = A Omega_i - Q (B Omega_i), computed in the slot of Q_i
+        char* Y = c.col(Q, ldq, k);
+        A.apply(c, bf.Om, n, bi, Y, ldq);
+        out.passes += 1;
+        if (k > 0) {
+            c.tn(k, bi, n, 1.0, B, ldb, bf.Om, n, 0.0, bf.T1, k, c.acc_proj);      // B Omega_i
+            c.nn(m, bi, k, -1.0, Q, ldq, bf.T1, k, 1.0, Y, ldq, c.acc_proj);      // Y -= Q (.)
+        }
+        for (int it = 0; it < p.P; ++it) {
+            c.cholqr2(Y, ldq, m, bi, false);                                      // Y = orth(Y)
+            A.apply_t(c, Y, ldq, bi, bf.Z, n, false);                             // Z = A^T Y
+            out.passes += 1;
+            if (k > 0) {
+                c.tn(k, bi, m, 1.0, Q, ldq, Y, ldq, 0.0, bf.T1, k, c.acc_proj);   // Q^T Y
+                c.nn(n, bi, k, -1.0, B, ldb, bf.T1, k, 1.0, bf.Z, n, c.acc_proj); // Z -= B^T (.)
+            }
+            c.cholqr2(bf.Z, n, n, bi, false);                                     // Z = orth(Z)
+            A.apply(c, bf.Z, n, bi, Y, ldq);                                      // Y = A Z
+            out.passes += 1;
+            if (k > 0) {
+                c.tn(k, bi, n, 1.0, B, ldb, bf.Z, n, 0.0, bf.T1, k, c.acc_proj);  // B Z
+                c.nn(m, bi, k, -1.0, Q, ldq, bf.T1, k, 1.0, Y, ldq, c.acc_proj);  // Y -= Q (.)
+            }
+        }
+        c.cholqr2(Y, ldq, m, bi, false);                                          // Q_i = orth(Y)
+        if (k > 0) {                                                              // re-orthogonalise
+            c.project_out(Q, ldq, k, Y, ldq, m, bi, bf.T1);
+            c.cholqr2(Y, ldq, m, bi, false);
+        }
+        // B_i = Q_i^T A, written as rows k.. of B (= column-major n x bi with ld ldb)
+        char* Bs = c.col(B, ldb, k);
+        A.apply_t(c, Y, ldq, bi, Bs, ldb, true);
+        out.passes += 1;
+        const Ctx::Step s = c.indicator_step(Bs, ldb, bi, n, eps2, o.row_by_row);
+        out.blocks += 1;
+        out.E = s.E;
+        k += s.keep;
+        if (s.stop) { out.converged = true; break; }
+    }
+    out.rank = k;
+}
+
+// ------------------------------------------------------------------------------------ randQB_FP
+void run_fp(Ctx& c, AOp& A, const Plan& p, const qb_opts& o, Bufs& bf, void* Q, int64_t ldq,
+            void* B, int64_t ldb, double eps2, RunOut& out) {
+    const int64_t m = p.m, n = p.n;
+    const int omega_dt = c.f64 ? QB_F64 : QB_F32;
+    int64_t k = 0;
+    int64_t q = 0;
+    bool stop = false;
+    while (k < p.cap && !stop) {
+        const int64_t w = std::min<int64_t>(p.lt, p.cap - k);
+        const int64_t col0 = q * p.lt;
+        out.omega_cols = col0 + w;
+        omega_gen(c.st, n, col0, w, o.seed, omega_dt, bf.Om, n);                 // Omega = randn(n, l~)
+        for (int it = 0; it < p.P; ++it) {                                       // power scheme
+            A.apply(c, bf.Om, n, w, bf.G, m);                                     // G = A Omega
+            out.passes += 1;
+            if (k > 0) {
+                c.tn(k, w, n, 1.0, B, ldb, bf.Om, n, 0.0, bf.T1, k, c.acc_proj);
+                c.nn(m, w, k, -1.0, Q, ldq, bf.T1, k, 1.0, bf.G, m, c.acc_proj);
+            }
+            c.orth_wide(bf.G, m, m, w, p.b, bf.Tw);                               // G = orth(.)
+            A.apply_t(c, bf.G, m, w, bf.Om, n, false);                            // Omega = A^T G
+            out.passes += 1;
+            if (k > 0) {
+                c.tn(k, w, m, 1.0, Q, ldq, bf.G, m, 0.0, bf.T1, k, c.acc_proj);
+                c.nn(n, w, k, -1.0, B, ldb, bf.T1, k, 1.0, bf.Om, n, c.acc_proj);
+            }
+            c.orth_wide(bf.Om, n, n, w, p.b, bf.Tw);                              // Omega = orth(.)
+        }
+        A.apply(c, bf.Om, n, w, bf.G, m);                                         // G = A Omega
+        A.apply_t(c, bf.G, m, w, bf.H, n, true);                                  // H = A^T G
+        out.passes += 1;
+        for (int64_t c0 = 0; c0 < w && !stop; c0 += p.b) {
+            const int bi = int(std::min<int64_t>(p.b, w - c0));
+            const char* Om_i = c.col(bf.Om, n, c0);
+            // Y_i = G_i - Q (B Omega_i), kept for the B_i formula
+            c.copy_cols_(c.col(bf.G, m, c0), m, m, bi, bf.Ys, m);
+            if (k > 0) {
+                c.tn(k, bi, n, 1.0, B, ldb, Om_i, n, 0.0, bf.T1, k, c.acc_proj);
+                c.nn(m, bi, k, -1.0, Q, ldq, bf.T1, k, 1.0, bf.Ys, m, c.acc_proj);
+            }
+            // [Q_i, R_i] = qr(Y_i) in the slot of Q_i; R accumulated in Racc
+            char* Qi = c.col(Q, ldq, k);
+            c.copy_cols_(bf.Ys, m, m, bi, Qi, ldq);
+            set_identity(c.st, c.Racc, bi);
+            c.cholqr2(Qi, ldq, m, bi, true);
+            if (k > 0) {
+                // [Q_i, R~_i] = qr(Q_i - Q (Q^T Q_i)), R_i = R~_i R_i
+                c.project_out(Q, ldq, k, Qi, ldq, m, bi, bf.C2);
+                c.cholqr2(Qi, ldq, m, bi, true);
+            }
+            tri_inv(c.st, c.Racc, bi, c.Rinv);
+            // S^T = H_i - B^T (Q^T Y_i + B Omega_i), i.e. S = H_i^T - Y_i^T Q B - Omega_i^T B^T B
+            char* S = bf.Z;
+            c.copy_cols_(c.col(bf.H, n, c0), n, n, bi, S, n);
+            if (k > 0) {
+                c.copy_cols_(bf.T1, k, k, bi, bf.C2, k);                          // C2 = B Omega_i
+                c.tn(k, bi, m, 1.0, Q, ldq, bf.Ys, m, 1.0, bf.C2, k, c.acc_fine); // += Q^T Y_i
+                c.nn(n, bi, k, -1.0, B, ldb, bf.C2, k, 1.0, S, n, c.acc_fine);    // S^T -= B^T C2
+            }
+            // B_i = R_i^-T S  <=>  B_i^T = S^T R_i^-1
+            apply_rinv(c.st, c.f64, S, n, n, bi, c.Rinv);
+            char* Bs = c.col(B, ldb, k);
+            c.copy_cols_(S, n, n, bi, Bs, ldb);
+            const Ctx::Step s = c.indicator_step(Bs, ldb, bi, n, eps2, o.row_by_row);
+            out.blocks += 1;
+            out.E = s.E;
+            k += s.keep;
+            if (s.stop) { stop = true; out.converged = true; }
+        }
+        ++q;
+    }
+    out.rank = k;
+}
+
+// ------------------------------------------------------------------------------------ common entry
+int32_t run_common(AOp& A, const qb_opts* opts, bool fp, void* Q, int64_t ldq, void* B,
+                   int64_t ldb, void* ws, size_t ws_bytes, qb_info* info, void* stream,
+                   size_t* measure) {
+    if (!valid_opts(opts)) return QB_ERR_INVALID_ARG;
+    const qb_opts& o = *opts;
+    if (A.m < 0 || A.n < 0) return QB_ERR_INVALID_ARG;
+    const Plan p = make_plan(A.m, A.n, o, fp);
+    Ctx c;
+    setup_ctx(c, o.prec == QB_PREC_FP64);
+    c.st = reinterpret_cast<cudaStream_t>(stream);
+    Bufs bf;
+    Arena ar;
+    if (measure) {
+        reserve_all(ar, c, A, p, fp, bf);
+        *measure = ar.used + 4096;
+        return QB_OK;
+    }
+    if (!Q || !B || ldq < A.m || ldb < A.n) return QB_ERR_INVALID_ARG;
+    ar.base = reinterpret_cast<char*>(ws);
+    ar.cap = ws_bytes;
+    const int64_t l0 = launches_total();
+    reserve_all(ar, c, A, p, fp, bf);
+    QB_CUDA(cudaMemsetAsync(c.flags, 0, 4 * sizeof(int), c.st));
+    A.prepare(c);
+    const double normA2 = A.norm2(c);
+    int hf[4];
+    c.read_flags(hf);
+    RunOut out;
+    out.normA2 = normA2;
+    auto fill_info = [&](int32_t bits) {
+        if (!info) return;
+        info->rank = out.rank;
+        info->err2_est = out.E;
+        info->err_est = std::sqrt(std::max(out.E, 0.0));
+        info->normA2 = out.normA2;
+        info->passes = out.passes;
+        info->omega_cols = out.omega_cols;
+        info->status_bits = bits;
+        info->blocks = out.blocks;
+        info->launches = launches_total() - l0;
+    };
+    if (hf[0] || !std::isfinite(normA2)) {
+        fill_info(0);
+        return QB_ERR_NONFINITE;
+    }
+    const double eps = o.relative ? o.tol * std::sqrt(normA2) : o.tol;
+    const double eps2 = eps * eps;
+    if (normA2 == 0.0 || p.cap == 0) {
+        out.E = normA2;
+        out.converged = normA2 < eps2 || normA2 == 0.0;
+        fill_info(out.converged ? 0 : QB_BIT_NOT_CONVERGED);
+        return out.converged ? QB_OK : QB_NOT_CONVERGED;
+    }
+    double st0[4] = {normA2, 0, 0, normA2};
+    QB_CUDA(cudaMemcpyAsync(c.state, st0, sizeof st0, cudaMemcpyHostToDevice, c.st));
+    if (fp) run_fp(c, A, p, o, bf, Q, ldq, B, ldb, eps2, out);
+    else run_ei(c, A, p, o, bf, Q, ldq, B, ldb, eps2, out);
+    if (A.timed_out(c)) {
+        fill_info(0);
+        return QB_ERR_TIMEOUT;
+    }
+    c.read_flags(hf);
+    int32_t bits = 0;
+    if (hf[1]) bits |= QB_BIT_BREAKDOWN;
+    const double floor = std::sqrt(4.0 * U64 / THM3_DELTA) * std::sqrt(normA2);
+    int32_t status = QB_OK;
+    if (!out.converged) {
+        bits |= QB_BIT_NOT_CONVERGED;
+        status = QB_NOT_CONVERGED;
+    } else if (eps <= floor) {
+        bits |= QB_BIT_TOL_FLOOR;
+        status = QB_WARN_TOL_FLOOR;
+    }
+    fill_info(bits);
+    return status;
+}
+
+template <class F>
+int32_t guarded(F&& f) {
+    try {
+        return f();
+    } catch (const Error& e) {
+        return e.code;
+    } catch (...) {
+        return QB_ERR_CUDA;
+    }
+}
+
+bool valid_dense(const qb_dense* A, const qb_opts* o) {
+    if (!A || !o || A->m < 0 || A->n < 0 || A->ld < A->n || !A->a) return false;
+    if (A->dtype == QB_BF16X2 && !A->a_lo) return false;
+    if (o->prec == QB_PREC_FP64 && A->dtype != QB_F64) return false;
+    if (o->prec == QB_PREC_MIXED && A->dtype == QB_F64) return false;
+    return A->dtype >= QB_F64 && A->dtype <= QB_BF16X2;
+}
+
+bool valid_csr(const qb_csr* A, const qb_opts* o) {
+    if (!A || !o || A->m < 0 || A->n < 0 || A->nnz < 0 || A->nnz > INT32_MAX) return false;
+    if (!A->rowptr || (A->nnz > 0 && (!A->colind || !A->val))) return false;
+    if (A->dtype != QB_F64 && A->dtype != QB_F32) return false;
+    if (o->prec == QB_PREC_FP64 && A->dtype != QB_F64) return false;
+    if (o->prec == QB_PREC_MIXED && A->dtype != QB_F32) return false;
+    return true;
+}
+
+}  // namespace
+
+}  // namespace qb
+
+// ======================================================================================== C ABI
+using namespace qb;
+
+extern "C" {
+
+const char* qb_status_str(int32_t s) {
+    switch (s) {
+        case QB_OK: return "QB_OK";
+        case QB_NOT_CONVERGED: return "QB_NOT_CONVERGED";
+        case QB_WARN_TOL_FLOOR: return "QB_WARN_TOL_FLOOR";
+        case QB_ERR_INVALID_ARG: return "QB_ERR_INVALID_ARG";
+        case QB_ERR_NONFINITE: return "QB_ERR_NONFINITE";
+        case QB_ERR_CUDA: return "QB_ERR_CUDA";
+        case QB_ERR_BREAKDOWN: return "QB_ERR_BREAKDOWN";
+        case QB_ERR_WORKSPACE: return "QB_ERR_WORKSPACE";
+        case QB_ERR_TIMEOUT: return "QB_ERR_TIMEOUT";
+        case QB_ERR_UNSUPPORTED: return "QB_ERR_UNSUPPORTED";
+        default: return "QB_UNKNOWN_STATUS";
+    }
+}
+
+const char* qb_last_cuda_error(void) { return g_last_err; }
+
+int64_t qb_launch_count(void) { return launches_total(); }
+
+size_t qb_dense_workspace(const qb_dense* A, const qb_opts* opts, int32_t algo) {
+    if (!valid_dense(A, opts) || !valid_opts(opts) || (algo != 0 && algo != 1)) return 0;
+    size_t bytes = 0;
+    DenseOp op(*A);
+    int32_t rc = guarded([&] {
+        return run_common(op, opts, algo == 1, nullptr, 0, nullptr, 0, nullptr, 0, nullptr,
+                          nullptr, &bytes);
+    });
+    return rc == QB_OK ? bytes : 0;
+}
+
+int32_t qb_ei_dense(const qb_dense* A, const qb_opts* opts, void* Q, int64_t ldq, void* B,
+                    int64_t ldb, void* ws, size_t ws_bytes, qb_info* info, void* stream) {
+    if (!valid_dense(A, opts)) return QB_ERR_INVALID_ARG;
+    DenseOp op(*A);
+    return guarded([&] {
+        return run_common(op, opts, false, Q, ldq, B, ldb, ws, ws_bytes, info, stream, nullptr);
+    });
+}
+
+int32_t qb_fp_dense(const qb_dense* A, const qb_opts* opts, void* Q, int64_t ldq, void* B,
+                    int64_t ldb, void* ws, size_t ws_bytes, qb_info* info, void* stream) {
+    if (!valid_dense(A, opts)) return QB_ERR_INVALID_ARG;
+    DenseOp op(*A);
+    return guarded([&] {
+        return run_common(op, opts, true, Q, ldq, B, ldb, ws, ws_bytes, info, stream, nullptr);
+    });
+}
+
+size_t qb_csr_workspace(const qb_csr* A, const qb_opts* opts, int32_t algo) {
+    if (!valid_csr(A, opts) || !valid_opts(opts) || (algo != 0 && algo != 1)) return 0;
+    size_t bytes = 0;
+    CsrOp op(*A);
+    int32_t rc = guarded([&] {
+        return run_common(op, opts, algo == 1, nullptr, 0, nullptr, 0, nullptr, 0, nullptr,
+                          nullptr, &bytes);
+    });
+    return rc == QB_OK ? bytes : 0;
+}
+
+int32_t qb_ei_csr(const qb_csr* A, const qb_opts* opts, void* Q, int64_t ldq, void* B,
+                  int64_t ldb, void* ws, size_t ws_bytes, qb_info* info, void* stream) {
+    if (!valid_csr(A, opts)) return QB_ERR_INVALID_ARG;
+    CsrOp op(*A);
+    return guarded([&] {
+        return run_common(op, opts, false, Q, ldq, B, ldb, ws, ws_bytes, info, stream, nullptr);
+    });
+}
+
+int32_t qb_fp_csr(const qb_csr* A, const qb_opts* opts, void* Q, int64_t ldq, void* B,
+                  int64_t ldb, void* ws, size_t ws_bytes, qb_info* info, void* stream) {
+    if (!valid_csr(A, opts)) return QB_ERR_INVALID_ARG;
+    CsrOp op(*A);
+    return guarded([&] {
+        return run_common(op, opts, true, Q, ldq, B, ldb, ws, ws_bytes, info, stream, nullptr);
+    });
+}
+
+int32_t qb_omega(int64_t n, int64_t col0, int64_t w, uint64_t seed, int32_t dtype, void* out,
+                 int64_t ld, void* stream) {
+    if (n < 0 || col0 < 0 || w < 0 || ld < n || (n > 0 && w > 0 && !out)) return QB_ERR_INVALID_ARG;
+    if (dtype != QB_F64 && dtype != QB_F32 && dtype != QB_BF16) return QB_ERR_INVALID_ARG;
+    return guarded([&] {
+        omega_gen(reinterpret_cast<cudaStream_t>(stream), n, col0, w, seed, dtype, out, ld);
+        return int32_t(QB_OK);
+    });
+}
+
+size_t qb_apass_workspace(const qb_dense* A, int64_t w) {
+    if (!A || A->m < 0 || A->n < 0 || w < 0) return 0;
+    qb_opts o{};
+    o.b = 1;
+    o.prec = A->dtype == QB_F64 ? QB_PREC_FP64 : QB_PREC_MIXED;
+    if (!valid_dense(A, &o)) return 0;
+    try {
+        Ctx c;
+        setup_ctx(c, o.prec == QB_PREC_FP64);
+        Arena ar;   // measuring arena
+        c.alloc(ar, std::max(A->m, A->n) * std::max<int64_t>(w, 1));
+        DenseOp op(*A);
+        op.reserve(ar, c, std::max<int64_t>(w, 1));
+        return ar.used + 4096;
+    } catch (...) {
+        return 0;
+    }
+}
+
+static int32_t apass(const qb_dense* A, bool trans, const void* V, int64_t ldv, int64_t w,
+                     int32_t precise, void* Y, int64_t ldy, void* ws, size_t ws_bytes,
+                     void* stream) {
+    qb_opts o{};
+    o.b = 1;
+    o.prec = (A && A->dtype == QB_F64) ? QB_PREC_FP64 : QB_PREC_MIXED;
+    if (!valid_dense(A, &o) || w < 0 || !V || !Y) return QB_ERR_INVALID_ARG;
+    const int64_t rows_in = trans ? A->m : A->n, rows_out = trans ? A->n : A->m;
+    if (ldv < rows_in || ldy < rows_out) return QB_ERR_INVALID_ARG;
+    return guarded([&] {
+        Ctx c;
+        setup_ctx(c, o.prec == QB_PREC_FP64);
+        c.st = reinterpret_cast<cudaStream_t>(stream);
+        Arena ar;
+        ar.base = reinterpret_cast<char*>(ws);
+        ar.cap = ws_bytes;
+        c.alloc(ar, std::max(A->m, A->n) * std::max<int64_t>(w, 1));
+        DenseOp op(*A);
+        op.reserve(ar, c, std::max<int64_t>(w, 1));
+        op.prepare(c);
+        if (trans) op.apply_t(c, V, ldv, w, Y, ldy, precise != 0);
+        else op.apply(c, V, ldv, w, Y, ldy);
+        if (op.timed_out(c)) return int32_t(QB_ERR_TIMEOUT);
+        return int32_t(QB_OK);
+    });
+}
+
+int32_t qb_apass_sketch(const qb_dense* A, const void* V, int64_t ldv, int64_t w, void* Y,
+                        int64_t ldy, void* ws, size_t ws_bytes, void* stream) {
+    return apass(A, false, V, ldv, w, 0, Y, ldy, ws, ws_bytes, stream);
+}
+
+int32_t qb_apass_trans(const qb_dense* A, const void* V, int64_t ldv, int64_t w, int32_t precise,
+                       void* Z, int64_t ldz, void* ws, size_t ws_bytes, void* stream) {
+    return apass(A, true, V, ldv, w, precise, Z, ldz, ws, ws_bytes, stream);
+}
+
+size_t qb_quantize_workspace(int64_t, int64_t) { return (3 * 1024 + 8) * sizeof(double); }
+
+int32_t qb_quantize_bf16x2(const double* src, int64_t m, int64_t n, int64_t ld_src, void* hi,
+                           void* lo, int64_t ld, double* norms, void* ws, size_t ws_bytes,
+                           void* stream) {
+    if (m < 0 || n < 0 || ld_src < n || ld < n || !norms) return QB_ERR_INVALID_ARG;
+    if (m > 0 && n > 0 && (!src || !hi || !lo)) return QB_ERR_INVALID_ARG;
+    if (!ws || ws_bytes < qb_quantize_workspace(m, n)) return QB_ERR_WORKSPACE;
+    return guarded([&] {
+        cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+        double* part = reinterpret_cast<double*>(ws);   // 3 x 1024 partial sums
+        double* res = part + 3 * 1024;                 // 3 results
+        quantize_bf16x2(st, src, m, n, ld_src, reinterpret_cast<bf16*>(hi),
+                        reinterpret_cast<bf16*>(lo), ld, part, res);
+        QB_CUDA(cudaMemcpyAsync(norms, res, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        QB_CUDA(cudaStreamSynchronize(st));
+        return int32_t(QB_OK);
+    });
+}
+
+}  // extern "C"

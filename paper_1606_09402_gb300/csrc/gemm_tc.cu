@@ -1,0 +1,620 @@
+// BF16 tensor-core passes over a dense row-major A on sm_103a: TMA (cp.async.bulk.tensor) tiles
+// into 128-byte-swizzled shared memory, tcgen05.mma with the float32 accumulator in tensor memory,
+// tcgen05.ld for the epilogue.
+//
+//   sketch (G = A Omega, Y = A Z):  D (m x w) = A (m x n) * V (n x w)
+//       A operand: A row tile [128 rows x 64 k] (K-major)
+//       B operand: V^T tile [BN x 64 k] from V column-major (K-major)
+//   trans  (B_i^T = A^T Q_i, H = A^T G, Z = A^T Y):  D (n x w) = A^T (n x m) * V (m x w)
+//       A operand: column slab of A [64 k rows x 128 n] as two 64-column boxes (MN-major)
+//       B operand: V^T tile [BN x 64 k] (K-major)
+//   Up to three products accumulate into one tile: A_hi V_hi, A_hi V_lo, A_lo V_hi, where
+//   A = A_hi + A_lo and V = V_hi + V_lo are bf16 pairs (float32-like operands).
+//
+// Persistent CTAs (one per SM).  Work is the list of (row tile, column tile) units x the k-blocks
+// of each unit.  With several column tiles every CTA takes whole units in raster order (row tile
+// outer) so CTAs running together share the A tile through L2.  With one column tile (the
+// narrow passes of randQB_EI) the flattened k-block range is split evenly across CTAs
+// ("stream-K"): A is read exactly once and no SM idles on a partial wave; units cut between CTAs
+// leave float32 partials that a fix-up kernel adds in CTA order (deterministic).
+//
+// Warp roles: warp 0 issues TMA, warp 1 owns tensor memory and issues MMAs, warps 2-5 drain the
+// accumulator (double-buffered in tensor memory, so the epilogue of one unit overlaps the main
+// loop of the next).  Every mbarrier wait is bounded: on timeout the kernel records an error flag
+// and leaves the loop instead of spinning.
+#include "qb_internal.cuh"
+
+#include <cuda.h>
+
+namespace qb {
+namespace {
+
+constexpr int BM = 128;      // rows of the accumulator tile (MMA M)
+constexpr int BK = 64;       // k per stage: one 128-byte swizzle row of bf16
+constexpr int UMMA_K = 16;   // k per tcgen05.mma (kind::f16)
+constexpr int NUM_THREADS = 192;
+constexpr uint64_t WAIT_NS = 2000000000ull;   // bounded waits: 2 s
+constexpr int MAX_SK_CTAS = 160;              // stream-K launches use at most this many CTAs
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait; false (and err flag set) after WAIT_NS.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+    if (mbar_try(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    while (true) {
+        for (int i = 0; i < 64; ++i)
+            if (mbar_try(bar, parity)) return true;
+        if (globaltimer() - t0 > WAIT_NS) {
+            atomicOr(err, 1);
+            return false;
+        }
+    }
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
+                                            int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                       uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+// 32 lanes x 32 columns of 32-bit words: thread t of the warp gets row (lane base + t)
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor (tcgen05): start address, leading / stride byte offsets,
+// descriptor version 1, 128-byte swizzle.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= uint64_t((saddr >> 4) & 0x3FFFu);
+    d |= uint64_t((lbo >> 4) & 0x3FFFu) << 16;
+    d |= uint64_t((sbo >> 4) & 0x3FFFu) << 32;
+    d |= uint64_t(1) << 46;
+    d |= uint64_t(2) << 61;
+    return d;
+}
+// Instruction descriptor, kind::f16: bf16 A and B, float32 D, M = 128, N = bn.
+__host__ __device__ constexpr uint32_t idesc_bf16(int bn, bool a_mn) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn ? 1u : 0u) << 15) |
+           (uint32_t(bn >> 3) << 17) | (uint32_t(BM >> 4) << 24);
+}
+
+// ---------------------------------------------------------------- schedule
+struct Sched {
+    int tiles_m, tiles_n, kb;   // units = tiles_m * tiles_n, k-blocks per unit
+    int streamk;                // 1: split flattened k-blocks evenly across CTAs
+};
+// Segment of CTA c: unit u, k-blocks [k0, k1), slot = partial slot (-1 = whole unit)
+struct Seg {
+    int u, k0, k1, slot;
+};
+__host__ __device__ __forceinline__ int64_t sk_begin(int64_t total, int64_t c, int64_t G) {
+    return (total * c) / G;
+}
+
+// ---------------------------------------------------------------- kernel
+struct Params {
+    int M, N, K;                 // D is M x N, reduction length K
+    int nprod;                   // 1..3 products
+    Sched s;
+    float* D;
+    int64_t ldd;
+    float* part;                 // stream-K partial slots: [G][2][BN][BM]
+    int* err;
+};
+
+template <int BN, bool TRANS, int NA, int NB>
+struct Cfg {
+    static constexpr int A_TILE = BM * BK * 2;         // 16 KB per A array
+    static constexpr int B_TILE = BN * BK * 2;
+    static constexpr int STAGE = NA * A_TILE + NB * B_TILE;
+    static constexpr int STAGES = (200 * 1024) / STAGE < 8 ? (200 * 1024) / STAGE : 8;
+    static constexpr int SMEM = STAGES * STAGE + 1024 /*align*/ + 256 /*barriers*/;
+    static constexpr int TMEM_COLS = 2 * BN;           // double-buffered accumulator
+};
+
+template <int BN, bool TRANS, int NA, int NB>
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
+          const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1,
+          Params p) {
+    using C = Cfg<BN, TRANS, NA, NB>;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE);
+    uint64_t* empty = full + C::STAGES;
+    uint64_t* tfull = empty + C::STAGES;   // [2]
+    uint64_t* tempty = tfull + 2;          // [2]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int G = gridDim.x, cta = blockIdx.x;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < C::STAGES; ++s) {
+            mbar_init(full + s, 1);
+            mbar_init(empty + s, 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(tfull + b, 1);
+            mbar_init(tempty + b, 128);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(C::TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    // this CTA's segments
+    const Sched& sc = p.s;
+    const int64_t units = int64_t(sc.tiles_m) * sc.tiles_n;
+    int64_t beg, end;   // in k-blocks (stream-K) or units (raster)
+    if (sc.streamk) {
+        beg = sk_begin(units * sc.kb, cta, G);
+        end = sk_begin(units * sc.kb, cta + 1, G);
+    } else {
+        beg = cta;
+        end = units;
+    }
+    auto next_seg = [&](int64_t& pos, Seg& sg, bool& first) -> bool {
+        if (sc.streamk) {
+            if (pos >= end) return false;
+            const int64_t u = pos / sc.kb;
+            const int k0 = int(pos - u * sc.kb);
+            const int64_t rem = end - u * sc.kb;
+            const int k1 = int(rem < sc.kb ? rem : int64_t(sc.kb));
+            const bool whole = (k0 == 0 && k1 == sc.kb);
+            sg = Seg{int(u), k0, k1, whole ? -1 : (first ? 0 : 1)};
+            pos = u * sc.kb + k1;
+        } else {
+            if (pos >= end) return false;
+            sg = Seg{int(pos), 0, sc.kb, -1};
+            pos += G;
+        }
+        first = false;
+        return true;
+    };
+    auto unit_rc = [&](int u, int& r0, int& c0) {
+        r0 = (u / sc.tiles_n) * BM;
+        c0 = (u % sc.tiles_n) * BN;
+    };
+
+    bool ok = true;
+    if (warp == 0 && lane == 0) {
+        // ---------------------------------------------------------- TMA producer
+        int stage = 0;
+        uint32_t phase = 0;
+        int64_t pos = beg;
+        bool first = true;
+        Seg sg;
+        constexpr uint32_t bytes = uint32_t(C::STAGE);
+        while (ok && next_seg(pos, sg, first)) {
+            int r0, c0;
+            unit_rc(sg.u, r0, c0);
+            for (int kb = sg.k0; kb < sg.k1 && ok; ++kb) {
+                ok = mbar_wait(empty + stage, phase ^ 1, p.err);
+                if (!ok) break;
+                mbar_expect_tx(full + stage, bytes);
+                unsigned char* st = smem + stage * C::STAGE;
+                const int k = kb * BK;
+                if (!TRANS) {
+                    tma_load_2d(st, &mA0, full + stage, k, r0);
+                    if (NA > 1) tma_load_2d(st + C::A_TILE, &mA1, full + stage, k, r0);
+                } else {
+                    tma_load_2d(st, &mA0, full + stage, r0, k);
+                    tma_load_2d(st + C::A_TILE / 2, &mA0, full + stage, r0 + 64, k);
+                    if (NA > 1) {
+                        tma_load_2d(st + C::A_TILE, &mA1, full + stage, r0, k);
+                        tma_load_2d(st + C::A_TILE + C::A_TILE / 2, &mA1, full + stage, r0 + 64, k);
+                    }
+                }
+                unsigned char* sb = st + NA * C::A_TILE;
+                tma_load_2d(sb, &mB0, full + stage, k, c0);
+                if (NB > 1) tma_load_2d(sb + C::B_TILE, &mB1, full + stage, k, c0);
+                if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---------------------------------------------------------- MMA issuer
+        constexpr uint32_t idesc = idesc_bf16(BN, TRANS);
+        int stage = 0;
+        uint32_t phase = 0;
+        int64_t pos = beg;
+        bool first = true;
+        Seg sg;
+        int buf = 0;
+        uint32_t tphase[2] = {0, 0};
+        while (ok && next_seg(pos, sg, first)) {
+            ok = mbar_wait(tempty + buf, tphase[buf] ^ 1, p.err);
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t acc = tmem + uint32_t(buf * BN);
+            for (int kb = sg.k0; kb < sg.k1 && ok; ++kb) {
+                ok = mbar_wait(full + stage, phase, p.err);
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t sa = smem_u32(smem + stage * C::STAGE);
+                const uint32_t sbb = sa + NA * C::A_TILE;
+#pragma unroll
+                for (int kk = 0; kk < BK / UMMA_K; ++kk) {
+                    uint64_t da[2], db[2];
+#pragma unroll
+                    for (int q = 0; q < NA; ++q) {
+                        const uint32_t base = sa + q * C::A_TILE;
+                        da[q] = TRANS ? sdesc(base + kk * (UMMA_K * 128), C::A_TILE / 2, 1024)
+                                      : sdesc(base + kk * (UMMA_K * 2), 16, 1024);
+                    }
+#pragma unroll
+                    for (int q = 0; q < NB; ++q)
+                        db[q] = sdesc(sbb + q * C::B_TILE + kk * (UMMA_K * 2), 16, 1024);
+                    const uint32_t accum = (kb > sg.k0 || kk > 0) ? 1u : 0u;
+                    tc_mma(acc, da[0], db[0], idesc, accum);                  // hi * hi
+                    if (p.nprod > 1) tc_mma(acc, da[0], db[NB - 1], idesc, 1u);  // hi * V_lo
+                    if (p.nprod > 2) tc_mma(acc, da[NA - 1], db[0], idesc, 1u);  // A_lo * hi
+                }
+                tc_commit(empty + stage);
+                if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
+            }
+            tc_commit(tfull + buf);
+            tphase[buf] ^= 1;
+            buf ^= 1;
+        }
+    } else if (warp >= 2) {
+        // ---------------------------------------------------------- epilogue
+        const int q = warp & 3;                 // tensor-memory lane quarter of this warp
+        const int row = q * 32 + lane;
+        int64_t pos = beg;
+        bool first = true;
+        Seg sg;
+        int buf = 0;
+        uint32_t tphase[2] = {0, 0};
+        while (ok && next_seg(pos, sg, first)) {
+            ok = mbar_wait(tfull + buf, tphase[buf], p.err);
+            if (!ok) break;
+            tc_fence_after();
+            int r0, c0;
+            unit_rc(sg.u, r0, c0);
+            const int64_t gr = int64_t(r0) + row;
+            float* slot = sg.slot >= 0
+                              ? p.part + ((int64_t(cta) * 2 + sg.slot) * BN) * BM
+                              : nullptr;
+#pragma unroll 1
+            for (int cc = 0; cc < BN; cc += 32) {
+                float v[32];
+                tmem_ld32(tmem + (uint32_t(q * 32) << 16) + uint32_t(buf * BN + cc), v);
+                if (slot) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) slot[int64_t(cc + j) * BM + row] = v[j];
+                } else if (gr < p.M) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int gc = c0 + cc + j;
+                        if (gc < p.N) p.D[gr + int64_t(gc) * p.ldd] = v[j];
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(tempty + buf);
+            tphase[buf] ^= 1;
+            buf ^= 1;
+        }
+    }
+    __syncwarp();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(C::TMEM_COLS));
+    }
+}
+
+// Stream-K fix-up: D tile of unit u = sum of the partial slots of the CTAs that share it, in CTA
+// order.  A unit covered by one CTA was written directly and is skipped.
+template <int BN>
+__global__ void k_tc_fixup(Params p, int G) {
+    const Sched& sc = p.s;
+    const int u = blockIdx.x;
+    const int64_t total = int64_t(sc.tiles_m) * sc.tiles_n * sc.kb;
+    const int64_t f = int64_t(u) * sc.kb, l = f + sc.kb - 1;
+    auto owner = [&](int64_t x) {
+        int64_t c = (x * G) / total;
+        while (c + 1 < G && sk_begin(total, c + 1, G) <= x) ++c;
+        while (c > 0 && sk_begin(total, c, G) > x) --c;
+        return c;
+    };
+    const int64_t c_first = owner(f), c_last = owner(l);
+    if (c_first == c_last) return;
+    const int r0 = (u / sc.tiles_n) * BM, c0 = (u % sc.tiles_n) * BN;
+    for (int e = threadIdx.x; e < BM * BN; e += blockDim.x) {
+        const int row = e % BM, col = e / BM;
+        float s = 0.f;
+        for (int64_t c = c_first; c <= c_last; ++c) {
+            const int64_t b = sk_begin(total, c, G);
+            const int slot = (b / sc.kb == u) ? 0 : 1;
+            s += p.part[((c * 2 + slot) * BN + col) * BM + row];
+        }
+        const int64_t gr = int64_t(r0) + row;
+        const int gc = c0 + col;
+        if (gr < p.M && gc < p.N) p.D[gr + int64_t(gc) * p.ldd] = s;
+    }
+}
+
+// V (rows x w float, col-major ld) -> hi, lo bf16 (col-major, ld ldo)
+__global__ void k_split_bf16(const float* __restrict__ V, int64_t ldv, int64_t rows, int64_t w,
+                             bf16* __restrict__ hi, bf16* __restrict__ lo, int64_t ldo) {
+    const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (idx >= rows * w) return;
+    const int64_t i = idx % rows, j = idx / rows;
+    const float v = V[i + j * ldv];
+    const bf16 h = __float2bfloat16_rn(v);
+    hi[i + j * ldo] = h;
+    if (lo) lo[i + j * ldo] = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
+// ---------------------------------------------------------------- host side
+typedef CUresult (*EncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encoder() {
+    static EncodeTiled fn = nullptr;
+    if (!fn) {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        QB_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000,
+                                                 cudaEnableDefault, &q));
+        if (q != cudaDriverEntryPointSuccess || !f)
+            throw Error{QB_ERR_CUDA, "cuTensorMapEncodeTiled unavailable"};
+        fn = reinterpret_cast<EncodeTiled>(f);
+    }
+    return fn;
+}
+
+// 2-D bf16 tensor: inner extent `inner` (contiguous), `outer` rows of `ld` elements
+CUtensorMap make_map(const void* ptr, int64_t inner, int64_t outer, int64_t ld, int box_inner,
+                     int box_outer) {
+    CUtensorMap m;
+    const cuuint64_t dims[2] = {cuuint64_t(inner), cuuint64_t(outer)};
+    const cuuint64_t strides[1] = {cuuint64_t(ld) * 2};
+    const cuuint32_t box[2] = {cuuint32_t(box_inner), cuuint32_t(box_outer)};
+    const cuuint32_t es[2] = {1, 1};
+    CUresult r = encoder()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims,
+                           strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) throw Error{QB_ERR_CUDA, "cuTensorMapEncodeTiled failed"};
+    return m;
+}
+
+// Column tile: the narrowest of 64 / 128 / 256 that holds w; the three-product passes stop at 128
+// so that three pipeline stages (64 KB each) fit in shared memory.
+int pick_bn(int64_t w, bool precise) {
+    if (w <= 64) return 64;
+    if (w <= 128 || precise) return 128;
+    return 256;
+}
+
+template <int BN, bool TRANS, int NA, int NB>
+void run(cudaStream_t st, const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& b0,
+         const CUtensorMap& b1, Params p, int G) {
+    using C = Cfg<BN, TRANS, NA, NB>;
+    auto kern = k_tc_gemm<BN, TRANS, NA, NB>;
+    QB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+    kern<<<G, NUM_THREADS, C::SMEM, st>>>(a0, a1, b0, b1, p);
+    QB_LAUNCHED();
+    if (p.s.streamk) {
+        k_tc_fixup<BN><<<p.s.tiles_m * p.s.tiles_n, 256, 0, st>>>(p, G);
+        QB_LAUNCHED();
+    }
+}
+
+template <bool TRANS, int NA, int NB>
+void run_bn(int bn, cudaStream_t st, const CUtensorMap& a0, const CUtensorMap& a1,
+            const CUtensorMap& b0, const CUtensorMap& b1, Params p, int G) {
+    if (bn == 64) run<64, TRANS, NA, NB>(st, a0, a1, b0, b1, p, G);
+    else if (bn == 128) run<128, TRANS, NA, NB>(st, a0, a1, b0, b1, p, G);
+    else run<256, TRANS, NA, NB>(st, a0, a1, b0, b1, p, G);
+}
+
+struct Scratch {
+    float* part;
+    int* err;
+    bf16* vhi;
+    bf16* vlo;
+    size_t part_bytes;
+};
+
+Scratch carve(void* scratch, size_t bytes, int64_t rows, int64_t w) {
+    // [err 256 B][V hi][V lo][partials]
+    char* p = reinterpret_cast<char*>(scratch);
+    Scratch s;
+    s.err = reinterpret_cast<int*>(p);
+    const int64_t ldv = align_up(rows, 8);
+    const size_t vb = size_t(align_up(ldv * w * 2, 256));
+    s.vhi = reinterpret_cast<bf16*>(p + 256);
+    s.vlo = reinterpret_cast<bf16*>(p + 256 + vb);
+    s.part = reinterpret_cast<float*>(p + 256 + 2 * vb);
+    if (256 + 2 * vb > bytes) throw Error{QB_ERR_WORKSPACE, "tensor-core scratch too small"};
+    s.part_bytes = bytes - 256 - 2 * vb;
+    return s;
+}
+
+Sched make_sched(int64_t M, int64_t N, int64_t K, int bn, int G) {
+    Sched s;
+    s.tiles_m = int(cdiv(M, BM));
+    s.tiles_n = int(cdiv(N, bn));
+    s.kb = int(cdiv(K, BK));
+    const int64_t units = int64_t(s.tiles_m) * s.tiles_n;
+    // raster when there are enough units for ~8 waves; stream-K otherwise
+    s.streamk = units < 8LL * G ? 1 : 0;
+    return s;
+}
+
+// CTAs to launch: never more than there are k-blocks (stream-K) or units (raster), so that every
+// CTA of a stream-K launch owns a non-empty range.
+int grid_size(const Sched& s, int sms) {
+    const int64_t units = int64_t(s.tiles_m) * s.tiles_n;
+    const int64_t work = s.streamk ? units * s.kb : units;
+    const int64_t cap = s.streamk ? std::min(sms, MAX_SK_CTAS) : sms;
+    return int(std::max<int64_t>(1, std::min<int64_t>(cap, work)));
+}
+
+}  // namespace
+
+int* tc_error_flag(void* scratch) { return reinterpret_cast<int*>(scratch); }
+
+bool tc_available() {
+    static int cached = -1;
+    if (cached < 0) {
+        int dev = 0, major = 0, minor = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return false;
+        cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+        cached = (major == 10 && minor == 3) ? 1 : 0;
+    }
+    return cached == 1;
+}
+
+size_t tc_scratch_bytes(int64_t m, int64_t n, int64_t w) {
+    const int64_t rows = std::max(m, n);
+    const size_t vb = size_t(align_up(align_up(rows, 8) * w * 2, 256));
+    const size_t part = size_t(MAX_SK_CTAS) * 2 * pick_bn(w, false) * BM * sizeof(float);
+    return 256 + 2 * vb + part;
+}
+
+void tc_sketch(cudaStream_t st, const bf16* A, int64_t lda, int64_t m, int64_t n, const bf16* Vt,
+               int64_t ldv, int64_t w, float* Y, int64_t ldy, void* scratch, size_t scratch_bytes) {
+    if (m <= 0 || w <= 0) return;
+    Scratch s = carve(scratch, scratch_bytes, 0, 0);
+    const int bn = pick_bn(w, false);
+    Params p{};
+    p.M = int(m);
+    p.N = int(w);
+    p.K = int(n);
+    p.nprod = 1;
+    int G = num_sms();
+    p.s = make_sched(m, w, n, bn, G);
+    G = grid_size(p.s, G);
+    p.D = Y;
+    p.ldd = ldy;
+    p.part = s.part;
+    p.err = s.err;
+    if (p.s.streamk && size_t(G) * 2 * bn * BM * sizeof(float) > s.part_bytes)
+        throw Error{QB_ERR_WORKSPACE, "tensor-core partials"};
+    const CUtensorMap a = make_map(A, n, m, lda, BK, BM);
+    const CUtensorMap b = make_map(Vt, n, w, ldv, BK, bn);
+    run_bn<false, 1, 1>(bn, st, a, a, b, b, p, G);
+}
+
+void tc_trans(cudaStream_t st, const bf16* A_hi, const bf16* A_lo, int64_t lda, int64_t m,
+              int64_t n, const float* V, int64_t ldv, int64_t w, float* Z, int64_t ldz,
+              bool precise, void* scratch, size_t scratch_bytes) {
+    if (n <= 0 || w <= 0) return;
+    Scratch s = carve(scratch, scratch_bytes, m, w);
+    const int64_t ldo = align_up(m, 8);
+    k_split_bf16<<<unsigned(cdiv(m * w, 256)), 256, 0, st>>>(V, ldv, m, w, s.vhi,
+                                                             precise ? s.vlo : nullptr, ldo);
+    QB_LAUNCHED();
+    const int bn = pick_bn(w, precise);
+    Params p{};
+    p.M = int(n);
+    p.N = int(w);
+    p.K = int(m);
+    p.nprod = precise ? 3 : 1;
+    int G = num_sms();
+    p.s = make_sched(n, w, m, bn, G);
+    G = grid_size(p.s, G);
+    p.D = Z;
+    p.ldd = ldz;
+    p.part = s.part;
+    p.err = s.err;
+    if (p.s.streamk && size_t(G) * 2 * bn * BM * sizeof(float) > s.part_bytes)
+        throw Error{QB_ERR_WORKSPACE, "tensor-core partials"};
+    // A as an (n inner, m outer) tensor; boxes of 64 columns x 64 rows
+    const CUtensorMap a0 = make_map(A_hi, n, m, lda, 64, BK);
+    const CUtensorMap b0 = make_map(s.vhi, m, w, ldo, BK, bn);
+    if (precise) {
+        const CUtensorMap a1 = make_map(A_lo, n, m, lda, 64, BK);
+        const CUtensorMap b1 = make_map(s.vlo, m, w, ldo, BK, bn);
+        run_bn<true, 2, 2>(bn, st, a0, a1, b0, b1, p, G);
+    } else {
+        run_bn<true, 1, 1>(bn, st, a0, a0, b0, b0, p, G);
+    }
+}
+
+}  // namespace qb

@@ -1,0 +1,251 @@
+// Omega generation (Philox4x32-10 + Box-Muller), norms, quantisation, copies.
+#include "qb_internal.cuh"
+
+namespace qb {
+namespace {
+
+// Philox4x32-10 (Salmon et al., SC'11): two 32x32->64 multiplications per round, key bumped by
+// the Weyl constants before every round but the first.
+struct U4 { uint32_t x, y, z, w; };
+
+__device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = U4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+    }
+    return c;
+}
+
+// One thread per (row j, column pair): both Box-Muller outputs of one counter are written.
+template <int KIND>  // 0 = f64, 1 = f32, 2 = bf16
+__global__ void k_omega(int64_t n, int64_t col0, int64_t w, uint32_t k0, uint32_t k1, void* out,
+                        int64_t ld) {
+    const int64_t pairs = (col0 + w + 1) / 2 - col0 / 2;
+    const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (idx >= n * pairs) return;
+    const int64_t j = idx % n;
+    const int64_t pc = col0 / 2 + idx / n;  // counter word 1 = c / 2
+    const U4 r = philox4x32_10(U4{uint32_t(j), uint32_t(pc), 0u, 0u}, k0, k1);
+    double z0, z1;
+    float f0, f1;
+    if (KIND == 0) {
+        const uint64_t a = ((uint64_t(r.x) << 32) | r.y) >> 11;
+        const uint64_t b = ((uint64_t(r.z) << 32) | r.w) >> 11;
+        const double u1 = (double(a) + 0.5) * 0x1.0p-53;
+        const double u2 = (double(b) + 0.5) * 0x1.0p-53;
+        const double rho = sqrt(-2.0 * log(u1));
+        double s, c;
+        sincospi(2.0 * u2, &s, &c);
+        z0 = rho * c;
+        z1 = rho * s;
+    } else {
+        const float u1 = (float(r.x >> 8) + 0.5f) * 0x1.0p-24f;
+        const float u2 = (float(r.z >> 8) + 0.5f) * 0x1.0p-24f;
+        const float rho = sqrtf(-2.0f * logf(u1));
+        float s, c;
+        sincospif(2.0f * u2, &s, &c);
+        f0 = rho * c;
+        f1 = rho * s;
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int64_t c = 2 * pc + h;
+        if (c < col0 || c >= col0 + w) continue;
+        const int64_t o = j + (c - col0) * ld;
+        if (KIND == 0) reinterpret_cast<double*>(out)[o] = h ? z1 : z0;
+        else if (KIND == 1) reinterpret_cast<float*>(out)[o] = h ? f1 : f0;
+        else reinterpret_cast<bf16*>(out)[o] = __float2bfloat16_rn(h ? f1 : f0);
+    }
+}
+
+__global__ void k_to_bf16(const float* X, int64_t ldx, int64_t rows, int64_t cols, bf16* Y,
+                          int64_t ldy) {
+    const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (idx >= rows * cols) return;
+    const int64_t i = idx % rows, j = idx / rows;
+    Y[i + j * ldy] = __float2bfloat16_rn(X[i + j * ldx]);
+}
+
+template <class T>
+__global__ void k_copy_cols(const T* X, int64_t ldx, int64_t rows, int64_t cols, T* Y,
+                            int64_t ldy) {
+    const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (idx >= rows * cols) return;
+    const int64_t i = idx % rows, j = idx / rows;
+    Y[i + j * ldy] = X[i + j * ldx];
+}
+
+// Block-level float64 sum, result in thread 0.
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double sh[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    v = 0.0;
+    if (wid == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        v = lane < nw ? sh[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    }
+    return v;
+}
+
+constexpr int NPART = 1024;
+
+template <int KIND>  // XKind
+__global__ void k_dense_norm2(const void* p, const void* lo, int64_t ld, int64_t m, int64_t n,
+                              double* part, int* flags) {
+    double s = 0.0;
+    bool bad = false;
+    for (int64_t i = blockIdx.x; i < m; i += gridDim.x) {
+        for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+            double v;
+            const int64_t o = i * ld + j;
+            if (KIND == X_F64) v = reinterpret_cast<const double*>(p)[o];
+            else if (KIND == X_F32) v = reinterpret_cast<const float*>(p)[o];
+            else if (KIND == X_BF16) v = __bfloat162float(reinterpret_cast<const bf16*>(p)[o]);
+            else v = double(__bfloat162float(reinterpret_cast<const bf16*>(p)[o])) +
+                     double(__bfloat162float(reinterpret_cast<const bf16*>(lo)[o]));
+            bad |= !isfinite(v);
+            s = fma(v, v, s);
+        }
+    }
+    s = block_sum(s);
+    if (bad) atomicOr(flags, 1);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+template <bool F64>
+__global__ void k_vec_norm2(const void* v, int64_t count, double* part, int* flags) {
+    double s = 0.0;
+    bool bad = false;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < count;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        const double x = F64 ? reinterpret_cast<const double*>(v)[i]
+                             : double(reinterpret_cast<const float*>(v)[i]);
+        bad |= !isfinite(x);
+        s = fma(x, x, s);
+    }
+    s = block_sum(s);
+    if (bad) atomicOr(flags, 1);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void k_sum_parts(const double* part, int count, int stride, double* out, int nout) {
+    for (int q = 0; q < nout; ++q) {
+        double s = 0.0;
+        for (int i = threadIdx.x; i < count; i += blockDim.x) s += part[q * stride + i];
+        s = block_sum(s);
+        if (threadIdx.x == 0) out[q] = s;
+        __syncthreads();
+    }
+}
+
+// A = hi + lo: hi = bf16(a), lo = bf16(a - hi); float64 partial sums of a^2, (a-hi-lo)^2, (a-hi)^2
+__global__ void k_quant(const double* src, int64_t lds, int64_t m, int64_t n, bf16* hi, bf16* lo,
+                        int64_t ld, double* part) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int64_t i = blockIdx.x; i < m; i += gridDim.x) {
+        for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+            const double a = src[i * lds + j];
+            const bf16 h = __double2bfloat16(a);
+            const double r = a - double(__bfloat162float(h));
+            const bf16 l = __double2bfloat16(r);
+            const double d = r - double(__bfloat162float(l));
+            hi[i * ld + j] = h;
+            lo[i * ld + j] = l;
+            s0 = fma(a, a, s0);
+            s1 = fma(d, d, s1);
+            s2 = fma(r, r, s2);
+        }
+    }
+    s0 = block_sum(s0);
+    s1 = block_sum(s1);
+    s2 = block_sum(s2);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = s0;
+        part[NPART + blockIdx.x] = s1;
+        part[2 * NPART + blockIdx.x] = s2;
+    }
+}
+
+}  // namespace
+
+void omega_gen(cudaStream_t st, int64_t n, int64_t col0, int64_t w, uint64_t seed, int dtype,
+               void* out, int64_t ld) {
+    if (n <= 0 || w <= 0) return;
+    const int64_t pairs = (col0 + w + 1) / 2 - col0 / 2;
+    const int64_t tot = n * pairs;
+    const uint32_t k0 = uint32_t(seed & 0xffffffffu), k1 = uint32_t(seed >> 32);
+    const unsigned grid = unsigned(cdiv(tot, 256));
+    if (dtype == QB_F64) k_omega<0><<<grid, 256, 0, st>>>(n, col0, w, k0, k1, out, ld);
+    else if (dtype == QB_F32) k_omega<1><<<grid, 256, 0, st>>>(n, col0, w, k0, k1, out, ld);
+    else k_omega<2><<<grid, 256, 0, st>>>(n, col0, w, k0, k1, out, ld);
+    QB_LAUNCHED();
+}
+
+void to_bf16(cudaStream_t st, const float* X, int64_t ldx, int64_t rows, int64_t cols, bf16* Y,
+             int64_t ldy) {
+    if (rows <= 0 || cols <= 0) return;
+    k_to_bf16<<<unsigned(cdiv(rows * cols, 256)), 256, 0, st>>>(X, ldx, rows, cols, Y, ldy);
+    QB_LAUNCHED();
+}
+
+void copy_cols(cudaStream_t st, bool f64, const void* X, int64_t ldx, int64_t rows, int64_t cols,
+               void* Y, int64_t ldy) {
+    if (rows <= 0 || cols <= 0) return;
+    const unsigned g = unsigned(cdiv(rows * cols, 256));
+    if (f64)
+        k_copy_cols<double><<<g, 256, 0, st>>>(reinterpret_cast<const double*>(X), ldx, rows,
+                                               cols, reinterpret_cast<double*>(Y), ldy);
+    else
+        k_copy_cols<float><<<g, 256, 0, st>>>(reinterpret_cast<const float*>(X), ldx, rows, cols,
+                                              reinterpret_cast<float*>(Y), ldy);
+    QB_LAUNCHED();
+}
+
+void fill_zero(cudaStream_t st, void* p, size_t bytes) {
+    if (bytes) QB_CUDA(cudaMemsetAsync(p, 0, bytes, st));
+}
+
+void dense_norm2(cudaStream_t st, XOp A, int64_t m, int64_t n, double* part, double* out,
+                 int* flags) {
+    const unsigned g = unsigned(std::max<int64_t>(1, std::min<int64_t>(m, NPART)));
+    switch (A.kind) {
+        case X_F64: k_dense_norm2<X_F64><<<g, 256, 0, st>>>(A.p, A.lo, A.ld, m, n, part, flags); break;
+        case X_F32: k_dense_norm2<X_F32><<<g, 256, 0, st>>>(A.p, A.lo, A.ld, m, n, part, flags); break;
+        case X_BF16: k_dense_norm2<X_BF16><<<g, 256, 0, st>>>(A.p, A.lo, A.ld, m, n, part, flags); break;
+        case X_BF16X2: k_dense_norm2<X_BF16X2><<<g, 256, 0, st>>>(A.p, A.lo, A.ld, m, n, part, flags); break;
+    }
+    QB_LAUNCHED();
+    k_sum_parts<<<1, 256, 0, st>>>(part, int(g), 0, out, 1);
+    QB_LAUNCHED();
+}
+
+void vec_norm2(cudaStream_t st, const void* v, bool f64, int64_t count, double* part,
+               double* out, int* flags) {
+    const unsigned g = unsigned(std::max<int64_t>(1, std::min<int64_t>(cdiv(count, 256), NPART)));
+    if (f64) k_vec_norm2<true><<<g, 256, 0, st>>>(v, count, part, flags);
+    else k_vec_norm2<false><<<g, 256, 0, st>>>(v, count, part, flags);
+    QB_LAUNCHED();
+    k_sum_parts<<<1, 256, 0, st>>>(part, int(g), 0, out, 1);
+    QB_LAUNCHED();
+}
+
+void quantize_bf16x2(cudaStream_t st, const double* src, int64_t m, int64_t n, int64_t lds,
+                     bf16* hi, bf16* lo, int64_t ld, double* part, double* out3) {
+    const unsigned g = unsigned(std::max<int64_t>(1, std::min<int64_t>(m, NPART)));
+    k_quant<<<g, 256, 0, st>>>(src, lds, m, n, hi, lo, ld, part);
+    QB_LAUNCHED();
+    k_sum_parts<<<1, 256, 0, st>>>(part, int(g), NPART, out3, 3);
+    QB_LAUNCHED();
+}
+
+}  // namespace qb

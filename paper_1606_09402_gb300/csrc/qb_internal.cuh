@@ -1,0 +1,169 @@
+// Internal declarations shared by the translation units of libqb.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstddef>
+#include <atomic>
+#include <stdexcept>
+#include <string>
+
+#include "qb.h"
+
+namespace qb {
+
+using bf16 = __nv_bfloat16;
+
+// ------------------------------------------------------------------------------------ errors
+struct Error {
+    int32_t code;
+    std::string what;
+};
+
+void record_cuda_error(cudaError_t e, const char* where);
+void count_launch();
+int64_t launches_total();
+
+#define QB_CUDA(call)                                                        \
+    do {                                                                     \
+        cudaError_t e__ = (call);                                            \
+        if (e__ != cudaSuccess) {                                            \
+            ::qb::record_cuda_error(e__, #call);                             \
+            throw ::qb::Error{QB_ERR_CUDA, cudaGetErrorString(e__)};         \
+        }                                                                    \
+    } while (0)
+
+#define QB_LAUNCHED()                                                        \
+    do {                                                                     \
+        ::qb::count_launch();                                                \
+        cudaError_t e__ = cudaGetLastError();                                \
+        if (e__ != cudaSuccess) {                                            \
+            ::qb::record_cuda_error(e__, __func__);                          \
+            throw ::qb::Error{QB_ERR_CUDA, cudaGetErrorString(e__)};         \
+        }                                                                    \
+    } while (0)
+
+inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline int64_t align_up(int64_t a, int64_t b) { return cdiv(a, b) * b; }
+
+int num_sms();
+
+// ------------------------------------------------------------------------------------ workspace
+// Bump allocator over the caller's workspace.  With base == nullptr it only measures.
+struct Arena {
+    char* base = nullptr;
+    size_t cap = 0;
+    size_t used = 0;
+    template <class T>
+    T* get(int64_t count) {
+        size_t off = (used + 255) & ~size_t(255);
+        size_t bytes = size_t(count > 0 ? count : 1) * sizeof(T);
+        used = off + bytes;
+        if (base == nullptr) return nullptr;
+        if (used > cap) throw Error{QB_ERR_WORKSPACE, "workspace too small"};
+        return reinterpret_cast<T*>(base + off);
+    }
+};
+
+// ------------------------------------------------------------------------------------ GEMM
+// C (M x N, column-major, ldc) = alpha * op(X) * Y + beta * C, Y is K x N column-major (ldy).
+//   xt == true : op(X) = X^T with X column-major K x M (ldx)   ("TN": both operands K-contiguous)
+//   xt == false: op(X) = X   with X column-major M x K (ldx)   ("NN")
+// Accumulation: ACC_D float64, ACC_F float32, ACC_DF float32 pair (exact products, ~48-bit sums).
+enum Acc { ACC_D = 0, ACC_F = 1, ACC_DF = 2 };
+enum XKind { X_F64 = 0, X_F32 = 1, X_BF16 = 2, X_BF16X2 = 3 };
+
+struct GemmScratch {
+    void* part = nullptr;   // split-K partials
+    size_t part_bytes = 0;
+};
+
+// X given as a typed pointer pair (lo only for X_BF16X2).
+struct XOp {
+    XKind kind;
+    const void* p;
+    const void* lo;
+    int64_t ld;
+};
+
+void gemm(cudaStream_t st, bool xt, int64_t M, int64_t N, int64_t K, double alpha, XOp X,
+          const void* Y, bool y_f64, int64_t ldy, double beta, void* C, bool c_f64, int64_t ldc,
+          Acc acc, const GemmScratch& scr);
+// bytes of split-K partial storage needed by gemm() for any (M, N) with M * N <= mn_max
+size_t gemm_scratch_bytes(int64_t mn_max);
+
+// ------------------------------------------------------------------------------------ tcgen05
+// BF16 tensor-core passes over dense A (row-major m x n, bf16 hi [+ lo]).
+//   sketch: Y (m x w, col-major, float) = A_hi * V, V given as bf16 column-major n x w
+//   trans : Z (n x w, col-major, float) = (A_hi + A_lo)^T * (V_hi + V_lo)  (3 products) or
+//           A_hi^T * V_hi (1 product); V float column-major m x w, split on the fly.
+bool tc_available();
+// scratch layout starts with a 256-byte error area: word 0 is set when a bounded wait timed out
+size_t tc_scratch_bytes(int64_t m, int64_t n, int64_t w);
+int* tc_error_flag(void* scratch);
+void tc_sketch(cudaStream_t st, const bf16* A, int64_t lda, int64_t m, int64_t n,
+               const bf16* Vt, int64_t ldv, int64_t w, float* Y, int64_t ldy, void* scratch,
+               size_t scratch_bytes);
+void tc_trans(cudaStream_t st, const bf16* A_hi, const bf16* A_lo, int64_t lda, int64_t m,
+              int64_t n, const float* V, int64_t ldv, int64_t w, float* Z, int64_t ldz,
+              bool precise, void* scratch, size_t scratch_bytes);
+
+// ------------------------------------------------------------------------------------ misc kernels
+void omega_gen(cudaStream_t st, int64_t n, int64_t col0, int64_t w, uint64_t seed, int dtype,
+               void* out, int64_t ld);
+void to_bf16(cudaStream_t st, const float* X, int64_t ldx, int64_t rows, int64_t cols, bf16* Y,
+             int64_t ldy);
+// ||A||^2 of a dense row-major A; flags[0] |= 1 on a non-finite entry.  part: >= 1024 doubles
+void dense_norm2(cudaStream_t st, XOp A, int64_t m, int64_t n, double* part, double* out,
+                 int* flags);
+void vec_norm2(cudaStream_t st, const void* v, bool f64, int64_t count, double* part,
+               double* out, int* flags);
+void quantize_bf16x2(cudaStream_t st, const double* src, int64_t m, int64_t n, int64_t lds,
+                     bf16* hi, bf16* lo, int64_t ld, double* part, double* out3);
+// copy a column-major rows x cols block (f64 or f32)
+void copy_cols(cudaStream_t st, bool f64, const void* X, int64_t ldx, int64_t rows,
+               int64_t cols, void* Y, int64_t ldy);
+void fill_zero(cudaStream_t st, void* p, size_t bytes);
+
+// ------------------------------------------------------------------------------------ panel
+// Small b x b float64 matrices are column-major with ld = 64.
+constexpr int MAXB = 64;
+// W (bi x bi Gram, col-major ld 64) -> R (upper, W = R^T R) and Rinv; breakdown clamps the pivot
+// and sets flags[1]; R_acc <- R * R_acc if R_acc != nullptr (R_acc starts as identity).
+void chol_rinv(cudaStream_t st, const double* W, int bi, double tau_rel, double* R,
+               double* Rinv, double* R_acc, int* flags);
+void set_identity(cudaStream_t st, double* R, int bi);
+// R_out = Rinv of an upper-triangular R (bi x bi)
+void tri_inv(cudaStream_t st, const double* R, int bi, double* Rinv);
+// P (m x bi, col-major, f32/f64) <- P * Rinv (upper triangular)
+void apply_rinv(cudaStream_t st, bool f64, void* P, int64_t ldp, int64_t m, int bi,
+                const double* Rinv);
+// rn[j] = ||B(j, :)||^2 for rows j < rows of a row-major B (ld), float64 sums
+void row_norm2(cudaStream_t st, bool f64, const void* B, int64_t ldb, int rows, int64_t n,
+               double* rn);
+// state = {E, keep, stop, ...}: E -= rn[j] row by row until E < eps2 (see Sect. 3.1)
+void indicator(cudaStream_t st, double* state, const double* rn, int rows, double eps2,
+               int row_by_row);
+
+// ------------------------------------------------------------------------------------ CSR
+struct CsrDev {
+    int64_t m, n, nnz;
+    const int32_t* rowptr;
+    const int32_t* colind;
+    const void* val;
+    bool f64;
+};
+// staging bytes for csr_spmm on an m x n matrix (either orientation)
+size_t csr_stage_bytes(int64_t m, int64_t n, bool f64);
+// CSC copy of A: colptr[n+1], rowind[nnz], cval[nnz]; cnt: 2 n int32 scratch.  Entries inside a
+// column come in no particular order (atomic scatter).
+void csr_to_csc(cudaStream_t st, const CsrDev& A, int32_t* colptr, int32_t* rowind, void* cval,
+                int32_t* cnt);
+// Y (rows x w, col-major) = S X, S given by (ptr, idx, val) compressed along its rows,
+// X (cols x w, col-major)
+void csr_spmm(cudaStream_t st, bool f64, const int32_t* ptr, const int32_t* idx, const void* val,
+              int64_t rows, int64_t cols, const void* X, int64_t ldx, int64_t w, void* Y,
+              int64_t ldy, void* stage);
+
+}  // namespace qb

@@ -1,0 +1,82 @@
+"""The tensor-core passes over dense A (tcgen05 + TMA), through the C ABI, against float64
+products computed on the CPU.  Covers the stream-K schedule (one column tile), the raster
+schedule (many units), ragged tails in every dimension, and the three-product hi/lo pass."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1606_09402_gb300 as qb  # noqa: E402
+
+
+def _bf16(x):
+    return torch.tensor(x, dtype=torch.float32).to(torch.bfloat16)
+
+
+def _rel_err(got, ref, scale):
+    return float(np.max(np.abs(got - ref) / scale))
+
+
+@pytest.mark.parametrize("m,n,w", [
+    (1000, 776, 64),     # stream-K, ragged m
+    (777, 1000, 20),     # w below one column tile
+    (4099, 2048, 200),   # two column tiles, ragged
+    (16384, 1024, 2560), # raster schedule (>= 8 units per SM)
+    (300, 136, 1),       # single column
+])
+def test_sketch_bf16(m, n, w):
+    rng = np.random.default_rng(m + n + w)
+    A = rng.standard_normal((m, n)).astype(np.float32)
+    V = rng.standard_normal((n, w)).astype(np.float32)
+    Ad = _bf16(A).cuda()
+    Y = qb.qb_apass_sketch(Ad, torch.tensor(V).cuda()).cpu().numpy().astype(np.float64)
+    Ah = Ad.double().cpu().numpy()
+    Vh = _bf16(V).double().numpy()              # the kernel rounds V to bf16
+    ref = Ah @ Vh
+    scale = np.abs(Ah) @ np.abs(Vh) + 1e-30
+    assert _rel_err(Y, ref, scale) < 1e-5
+
+
+@pytest.mark.parametrize("m,n,w,precise", [
+    (2000, 1000, 64, True),
+    (2000, 1000, 64, False),
+    (1500, 777 + 7, 33, True),     # ragged n (multiple of 8 for TMA rows), ragged w
+    (1024, 16384, 2560, True),     # raster schedule
+    (40000, 256, 64, True),        # long reduction split across many CTAs
+])
+def test_trans_bf16(m, n, w, precise):
+    rng = np.random.default_rng(m * 3 + n + w)
+    A = rng.standard_normal((m, n))
+    V = rng.standard_normal((m, w)).astype(np.float32)
+    Ad = torch.tensor(A).cuda()
+    hi, lo, _ = qb.quantize_bf16x2(Ad)
+    Z = qb.qb_apass_trans(hi, torch.tensor(V).cuda(), precise=precise, a_lo=lo)
+    Z = Z.cpu().numpy().astype(np.float64)
+    Vd = V.astype(np.float64)
+    if precise:
+        ref = A.T @ Vd                           # hi/lo products reach ~2^-16 per operand
+        scale = np.abs(A.T) @ np.abs(Vd) + 1e-30
+        assert _rel_err(Z, ref, scale) < 1e-4
+        err_frob = np.linalg.norm(Z - ref) / np.linalg.norm(ref)
+        assert err_frob < 2e-5
+    else:
+        Ah = hi.double().cpu().numpy()
+        ref = Ah.T @ _bf16(V).double().numpy()
+        scale = np.abs(Ah.T) @ np.abs(_bf16(V).double().numpy()) + 1e-30
+        assert _rel_err(Z, ref, scale) < 1e-5
+
+
+def test_fp64_apass_matches_numpy():
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((333, 211))
+    V = rng.standard_normal((211, 17))
+    W = rng.standard_normal((333, 9))
+    Ad = torch.tensor(A).cuda()
+    Y = qb.qb_apass_sketch(Ad, torch.tensor(V).cuda()).cpu().numpy()
+    Z = qb.qb_apass_trans(Ad, torch.tensor(W).cuda()).cpu().numpy()
+    np.testing.assert_allclose(Y, A @ V, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(Z, A.T @ W, rtol=1e-12, atol=1e-12)

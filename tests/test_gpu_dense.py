@@ -1,0 +1,184 @@
+"""GPU parity of the dense paths against the float64 CPU oracle, through the C ABI.
+
+Float64 path: ||QB_gpu - QB_cpu||_F / ||A||_F <= 1e-10 and the same rank (the rank may differ by
+one only where E sits within 1e-12 ||A||^2 of eps^2).  Mixed path: the achieved error
+||A - QB||_F / ||A||_F (float64, on the CPU) is below the tolerance and the rank is close to the
+oracle's.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1606_09402_gb300 as qb  # noqa: E402
+
+PARITY = 1e-10
+U64 = 2.0 ** -53
+
+
+def fp_parity_bound(sigma, rank):
+    """randQB_FP forms B_i from H_i = A^T G_i and B^T B (Sect. 4.2); rounding there is amplified by
+    (sigma_1 / sigma_k)^2 (Remark 4.1), so two correct float64 evaluations in different orders
+    agree to about u (sigma_1 / sigma_k)^2.  The bound is that, with a factor 100 of headroom,
+    and never below the 1e-10 parity target."""
+    s = np.sort(np.asarray(sigma))[::-1]
+    k = max(1, min(rank, len(s)))
+    return max(PARITY, 100 * U64 * (s[0] / s[k - 1]) ** 2)
+
+
+def _qb(Q, B):
+    return (Q.double() @ B.double()).cpu().numpy()
+
+
+def _check_parity(A, res, ref, tol_rel, label="", bound=PARITY):
+    Q, B, info = res
+    normA = np.linalg.norm(A)
+    if info.rank != ref.rank:
+        # allowed only at a numerical tie of E with eps^2
+        eps2 = (tol_rel ** 2) * ref.normA2
+        near = min(abs(e - eps2) for e in ref.E_hist[max(0, min(info.rank, ref.rank) - 2):])
+        assert near <= 1e-12 * ref.normA2, (label, info.rank, ref.rank)
+        return
+    diff = np.linalg.norm(_qb(Q, B) - ref.Q @ ref.B) / normA
+    assert diff <= bound, (label, diff, bound)
+    assert abs(info.err2_est - ref.E) <= max(1e-10, bound) * ref.normA2, (label, info.err2_est, ref.E)
+
+
+# ----------------------------------------------------------------------------- Omega
+def test_omega_f64_matches_oracle():
+    for (n, c0, w, seed) in [(1000, 0, 37, 9402), (777, 13, 20, (1 << 40) + 3), (5, 3, 1, 0)]:
+        g = qb.qb_omega(n, c0, w, seed, dtype=torch.float64).cpu().numpy()
+        r = oracle.omega(n, c0, w, seed)
+        np.testing.assert_allclose(g, r, rtol=1e-13, atol=1e-13)
+
+
+def test_omega_f32_and_bf16():
+    n, c0, w, seed = 3000, 5, 24, 77
+    g = qb.qb_omega(n, c0, w, seed, dtype=torch.float32).cpu().numpy().astype(np.float64)
+    r = oracle.omega_f32(n, c0, w, seed).astype(np.float64)
+    err = np.abs(g - r) / (1 + np.abs(r))
+    assert np.quantile(err, 0.999) < 1e-5 and err.max() < 1e-3
+    gb = qb.qb_omega(n, c0, w, seed, dtype=torch.bfloat16).float().cpu().numpy()
+    assert np.max(np.abs(gb - g) / (1 + np.abs(g))) < 2.0 ** -8
+
+
+# ----------------------------------------------------------------------------- 2000 x 2000 workload
+@pytest.fixture(scope="module")
+def A2000():
+    return synth.dense_from_spectrum(2000, 2000, synth.sigma_pow(2000, 1.5), seed=1606)
+
+
+@pytest.mark.parametrize("alg", ["ei", "fp"])
+@pytest.mark.parametrize("P", [0, 1])
+@pytest.mark.parametrize("tol", [0.05, 2e-3])
+def test_fp64_parity_2000(A2000, alg, P, tol):
+    Ad = torch.tensor(A2000, device="cuda")
+    f = qb.qb_ei_dense if alg == "ei" else qb.qb_fp_dense
+    g = oracle.randqb_ei if alg == "ei" else oracle.randqb_fp
+    res = f(Ad, tol, 20, P=P, seed=9402)
+    ref = g(A2000, tol, 20, seed=9402, P=P)
+    assert res[2].status == ref.status
+    _check_parity(A2000, res, ref, tol, f"{alg} P={P} tol={tol}")
+
+
+# ----------------------------------------------------------------------------- ragged shapes, edge cases
+@pytest.mark.parametrize("alg", ["ei", "fp"])
+@pytest.mark.parametrize("m,n,b,P,tol,cap,lt", [
+    (517, 389, 7, 1, 1e-3, None, None),     # ragged tiles, b not a power of two
+    (389, 517, 64, 0, 1e-4, None, 100),      # wide A, full-width blocks, several FP batches
+    (130, 70, 16, 2, 1e-6, 40, None),        # rank cap reached -> not converged
+    (65, 1, 3, 0, 1e-2, None, None),         # single column
+])
+def test_fp64_parity_ragged(alg, m, n, b, P, tol, cap, lt):
+    k = min(m, n)
+    sigma = synth.sigma_exp(k, max(k / 8.0, 1.0))
+    A = synth.dense_from_spectrum(m, n, sigma, seed=m * 7 + n)
+    Ad = torch.tensor(A, device="cuda")
+    if alg == "ei":
+        res = qb.qb_ei_dense(Ad, tol, b, P=P, seed=5, rank_cap=cap)
+        ref = oracle.randqb_ei(A, tol, b, seed=5, P=P, rank_cap=cap)
+    else:
+        res = qb.qb_fp_dense(Ad, tol, b, P=P, seed=5, rank_cap=cap, l_tilde=lt)
+        ref = oracle.randqb_fp(A, tol, b, seed=5, P=P, rank_cap=cap, l_tilde=lt)
+    assert res[2].status == ref.status
+    bound = PARITY if alg == "ei" else fp_parity_bound(sigma, ref.rank)
+    _check_parity(A, res, ref, tol, f"{alg} {m}x{n}", bound)
+
+
+@pytest.mark.parametrize("alg", ["ei", "fp"])
+@pytest.mark.parametrize("r_true", [30, 27])
+def test_exact_low_rank(alg, r_true):
+    A = synth.dense_low_rank(300, 200, r_true, seed=r_true)
+    f = qb.qb_ei_dense if alg == "ei" else qb.qb_fp_dense
+    Q, B, info = f(torch.tensor(A, device="cuda"), 1e-6, 10, seed=3)
+    assert info.rank == r_true
+    assert abs(info.err2_est) <= 4 * 1.11e-16 * info.normA2 * 10
+    assert np.linalg.norm(A - _qb(Q, B)) ** 2 <= 1e-18 * info.normA2
+
+
+@pytest.mark.parametrize("alg", ["ei", "fp"])
+def test_zero_and_loose_and_nonfinite(alg):
+    f = qb.qb_ei_dense if alg == "ei" else qb.qb_fp_dense
+    Z = torch.zeros(50, 40, dtype=torch.float64, device="cuda")
+    Q, B, info = f(Z, 0.1, 8, seed=1)
+    assert info.rank == 0 and info.status == 0
+    A = synth.dense_from_spectrum(50, 40, synth.sigma_pow(40, 1.0), seed=1)
+    Q, B, info = f(torch.tensor(A, device="cuda"), 1.5, 8, seed=1)
+    assert info.rank == 1
+    A[3, 4] = np.nan
+    with pytest.raises(qb.QBError) as e:
+        f(torch.tensor(A, device="cuda"), 0.1, 8, seed=1)
+    assert e.value.code == -2
+
+
+def test_indicator_matches_direct_residual():
+    A = synth.dense_from_spectrum(400, 300, synth.sigma_exp(300, 30.0), seed=4)
+    for f in (qb.qb_ei_dense, qb.qb_fp_dense):
+        Q, B, info = f(torch.tensor(A, device="cuda"), 1e-5, 16, P=1, seed=2)
+        direct = np.linalg.norm(A - _qb(Q, B)) ** 2
+        assert abs(info.err2_est - direct) <= 1e-12 * info.normA2
+        Qh = Q.cpu().numpy()
+        assert oracle.orth_loss(Qh) <= 1e-12
+
+
+# ----------------------------------------------------------------------------- mixed precision
+@pytest.fixture(scope="module")
+def A_mixed():
+    return synth.dense_from_spectrum(3000, 2000, synth.sigma_exp(2000, 60.0, 1e-6), seed=7)
+
+
+@pytest.mark.parametrize("alg", ["ei", "fp"])
+def test_mixed_reaches_tolerance(A_mixed, alg):
+    A = A_mixed
+    tol = 1e-3
+    Ad = torch.tensor(A, device="cuda")
+    hi, lo, norms = qb.quantize_bf16x2(Ad)
+    assert abs(norms[0] - oracle.frob2(A)) <= 1e-12 * norms[0]
+    assert norms[1] <= 1e-9 * norms[0]
+    f = qb.qb_ei_dense if alg == "ei" else qb.qb_fp_dense
+    Q, B, info = f(hi, tol, 32, P=1, seed=11, a_lo=lo, src_norm2=norms[0], prec="mixed")
+    assert info.status == 0
+    err = np.linalg.norm(A - _qb(Q, B)) / np.linalg.norm(A)
+    assert err < tol
+    ref = (oracle.randqb_ei if alg == "ei" else oracle.randqb_fp)(A, tol, 32, seed=11, P=1)
+    assert abs(info.rank - ref.rank) <= max(3, 0.02 * ref.rank)
+    # the indicator tracks the true error (Theorem 1) within the mixed-precision budget
+    assert abs(info.err2_est - (err ** 2) * info.normA2) <= 0.05 * (tol ** 2) * info.normA2
+
+
+def test_quantize_bf16x2_split():
+    A = np.random.default_rng(0).standard_normal((300, 257))
+    Ad = torch.tensor(A, device="cuda")
+    hi, lo, norms = qb.quantize_bf16x2(Ad)
+    rec = hi.double() + lo.double()
+    rel = np.abs(rec.cpu().numpy() - A) / np.abs(A)
+    assert rel.max() <= 2.0 ** -16
+    assert abs(norms[0] - np.sum(A * A)) <= 1e-12 * norms[0]
+    assert abs(norms[2] - np.sum((A - hi.double().cpu().numpy()) ** 2)) <= 1e-9 * norms[2]
