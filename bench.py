@@ -1,0 +1,426 @@
+"""Benchmark: time-to-tolerance of mixed-precision randQB_FP on one GB300, next to the float64
+randQB_FP path, the narrow A-pass bandwidth and the float64 CPU oracle.
+
+Workload (one "step" = one complete fixed-precision factorisation, inputs resident in HBM):
+  A = U diag(sigma) V^T, 40000 x 20000, sigma_j = exp(-j/200) + 1e-6 (j <= 4096; the omitted
+  tail carries 1.6e-8 of the energy of ||A||^2 = 99.5, far below eps^2 = 1e-6 ||A||^2), U, V from
+  the QR of seeded N(0,1) matrices; b = 64, P = 1, relative tolerance 1e-3, Omega seed 9402,
+  l~ = 50 b = 3200.  Mixed path: A stored as bf16 hi + lo (quantised once from float64, not
+  timed), BF16 tensor-core passes, float32 Q/B, float64 indicator and b x b Cholesky.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                       [--no-fp64] [--quick]
+N > 1 runs N independent replicas (the factorisation of one matrix does not shard across GPUs
+here), one per rank under torchrun.  Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "time-to-tolerance (s) and A-pass HBM GB/s, mixed-precision vs FP64 randQB_FP"
+M, N = 40000, 20000
+RANK_SPECTRUM = 4096
+TOL, B, P, SEED_A, SEED_OMEGA = 1e-3, 64, 1, 1606, 9402
+L_TILDE = 50 * B
+RANK_CAP = 4096
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the float64 comparison run")
+    ap.add_argument("--quick", action="store_true", help="smaller workload (smoke only)")
+    ap.add_argument("--steps-only", action="store_true",
+                    help="time the mixed randQB_FP steps only (no side measurements); for profiling")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampler for the timed region (SM clock, throttle reasons)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- inputs
+def make_inputs(torch, dev, quick):
+    import synth
+    m, n = (8000, 4000) if quick else (M, N)
+    r = min(RANK_SPECTRUM, n)
+    sigma = synth.sigma_exp(r, 200.0, 1e-6)
+    A64 = synth.dense_from_spectrum_torch(m, n, sigma, SEED_A, dev, dtype=torch.float64)
+    return A64, sigma
+
+
+def timed(torch, fn, steps, warmup, ws, stream):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        fn()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    return ev0.elapsed_time(ev1) / 1e3 / steps
+
+
+def event_time(torch, fn, reps, stream):
+    """Average device time of fn() over reps launches, CUDA events on the launching stream."""
+    fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3 / reps
+
+
+def cpu_baseline(A_rows, m_full):
+    """The float64 oracle's randQB_FP on a row sample of the same A, scaled to the full workload
+    by m_full / rows (every dominant cost of randQB_FP is linear in m)."""
+    import numpy as np
+
+    import oracle
+    m_s = A_rows.shape[0]
+    As = np.ascontiguousarray(A_rows)
+    t0 = time.perf_counter()
+    r = oracle.randqb_fp(As, TOL, B, seed=SEED_OMEGA, P=P, l_tilde=L_TILDE, rank_cap=RANK_CAP)
+    t = time.perf_counter() - t0
+    scale = m_full / m_s
+    cores = os.cpu_count()
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max((i.get("num_threads") or 0) for i in threadpool_info()) or cores
+    except Exception:
+        pass
+    return {"value": t * scale, "unit": "s", "cores": cores, "kind": "oracle",
+            "sample": f"oracle randQB_FP (float64 numpy/LAPACK) on rows 0..{m_s - 1} of the same A "
+                      f"(rank {r.rank}), {t:.1f} s measured, scaled by m/{m_s} = {scale:g}"}
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    import numpy as np
+    import torch
+
+    import oracle
+    import synth
+    m_s = 1000 if args.quick else 4000
+    m, n = (8000, 4000) if args.quick else (M, N)
+    r = min(RANK_SPECTRUM, n)
+    sigma = synth.sigma_exp(r, 200.0, 1e-6)
+    # same A rows as the GPU arm when a GPU is present, else the float64 CPU generator
+    if torch.cuda.is_available():
+        A = synth.dense_from_spectrum_torch(m, n, sigma, SEED_A, "cuda:0")[:m_s].cpu().numpy()
+    else:
+        A = synth.dense_from_spectrum(m_s, n, sigma[: min(r, m_s)], SEED_A)
+    times = []
+    rank_out = None
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        res = oracle.randqb_fp(A, TOL, B, seed=SEED_OMEGA, P=P, l_tilde=L_TILDE, rank_cap=RANK_CAP)
+        t = time.perf_counter() - t0
+        rank_out = res.rank
+        if i >= args.warmup:
+            times.append(t * (m / m_s))
+        if args.warmup + args.steps > 2 and sum(times) > 120:
+            break
+    v = statistics.mean(times)
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": ws,
+            "steps": len(times), "warmup": args.warmup, "ms_per_step": v * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": config_dict(m, n),
+            "cpu_baseline": {"value": v, "unit": "s", "cores": cores, "kind": "oracle",
+                             "sample": f"oracle randQB_FP on rows 0..{m_s - 1} (rank {rank_out}), "
+                                       f"scaled by m/{m_s}"},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    _ = np
+
+
+def config_dict(m, n):
+    return {"workload": f"dense {m}x{n} sigma_j=exp(-j/200)+1e-6, randQB_FP mixed (bf16 hi+lo A), "
+                        f"b={B}, P={P}, relative tol={TOL}, l~={L_TILDE}",
+            "m": m, "n": n, "b": B, "P": P, "tol": TOL, "l_tilde": L_TILDE, "rank_cap": RANK_CAP,
+            "seed_A": SEED_A, "seed_omega": SEED_OMEGA, "parallelism": "replicas",
+            "l2": "inputs larger than L2 (A hi+lo = 3.2 GB)"}
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args, ws, rank, local):
+    import numpy as np
+    import torch
+
+    import paper_1606_09402_gb300 as qb
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    A64, sigma = make_inputs(torch, dev, args.quick)
+    m, n = A64.shape
+    hi, lo, norms = qb.quantize_bf16x2(A64)
+    normA2 = norms[0]
+    dt = torch.float32
+    Qt = torch.empty(RANK_CAP, m, dtype=dt, device=dev)
+    Bm = torch.empty(RANK_CAP, n, dtype=dt, device=dev)
+    out = {}
+
+    def step():
+        out["r"] = qb.qb_fp_dense(hi, TOL, B, P=P, seed=SEED_OMEGA, a_lo=lo, src_norm2=normA2,
+                                  prec="mixed", rank_cap=RANK_CAP, l_tilde=L_TILDE,
+                                  out=(Qt, Bm), workspace=out.get("ws"))
+
+    # workspace once (the binding reuses it)
+    import ctypes as C
+    from paper_1606_09402_gb300 import _lib
+    d = qb._dense_desc(hi, lo, normA2)
+    o = qb._opts(TOL, B, P, SEED_OMEGA, True, RANK_CAP, L_TILDE, True, "mixed")
+    wsb = _lib.load().qb_dense_workspace(C.byref(d), C.byref(o), 1)
+    out["ws"] = torch.empty(wsb, dtype=torch.uint8, device=dev)
+
+    l0 = qb.launch_count()
+    with Clocks(local) as ck:
+        t_step = timed(torch, step, args.steps, args.warmup, ws, stream)
+    launches = qb.launch_count() - l0
+    Q, Bf, info = out["r"]
+    if args.steps_only:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": t_step, "unit": "s", "rank": info.rank,
+                              "launches_per_step": launches / (args.steps + args.warmup)}))
+        return
+    # timed-region launches only: the warmup steps launched the same count per step
+    per_step = launches / (args.steps + args.warmup)
+    gpu_launches = int(round(per_step * args.steps))
+
+    # achieved error (float64, verification only; untimed)
+    err2 = 0.0
+    for r0 in range(0, m, 4096):
+        r1 = min(m, r0 + 4096)
+        D = A64[r0:r1] - (Q[r0:r1].double() @ Bf.double())
+        err2 += float((D * D).sum())
+    err_rel = (err2 / normA2) ** 0.5
+
+    # ---- kernel-level: the A passes measured with CUDA events on the launching stream
+    pk, pk_src = peaks()
+    hbm = pk["hbm_gbs"]
+    reps = 3 if args.quick else 10
+    Om = torch.randn(n, L_TILDE, device=dev, dtype=torch.float32)
+    G = torch.randn(m, L_TILDE, device=dev, dtype=torch.float32)
+    t_sk_wide = event_time(torch, lambda: qb.qb_apass_sketch(hi, Om), reps, stream)
+    t_tr_wide = event_time(torch, lambda: qb.qb_apass_trans(hi, G, precise=1, a_lo=lo), reps,
+                           stream)
+    Om64 = torch.randn(n, B, device=dev, dtype=torch.float32)
+    G64 = torch.randn(m, B, device=dev, dtype=torch.float32)
+    t_sk_nar = event_time(torch, lambda: qb.qb_apass_sketch(hi, Om64), reps, stream)
+    t_tr_nar = event_time(torch, lambda: qb.qb_apass_trans(hi, G64, precise=1, a_lo=lo), reps,
+                          stream)
+    # The binding wraps each pass in small transposes of V / Y; time them to subtract
+    t_wrap_w = event_time(torch, lambda: (Om.T.contiguous(), torch.empty(L_TILDE, m, device=dev)),
+                          reps, stream)
+    flops_wide = 2.0 * m * n * L_TILDE
+    a_hi_bytes = 2.0 * m * n
+    tf_sk = flops_wide / max(t_sk_wide - t_wrap_w, 1e-9) / 1e12
+    gbs_nar_sk = (a_hi_bytes + 4.0 * (n + m) * B) / t_sk_nar / 1e9
+    gbs_nar_tr = (2 * a_hi_bytes + 4.0 * (n + m) * B) / t_tr_nar / 1e9
+
+    # ---- float64 randQB_FP on the same A (the comparison path)
+    fp64 = None
+    if not args.no_fp64:
+        Q64 = torch.empty(RANK_CAP, m, dtype=torch.float64, device=dev)
+        B64 = torch.empty(RANK_CAP, n, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, _, inf64 = qb.qb_fp_dense(A64, TOL, B, P=P, seed=SEED_OMEGA, rank_cap=RANK_CAP,
+                                     l_tilde=L_TILDE, out=(Q64, B64))
+        torch.cuda.synchronize()
+        fp64 = {"time_to_tol_s": time.perf_counter() - t0, "rank": inf64.rank,
+                "err_est": inf64.err_est / normA2 ** 0.5, "status": inf64.status}
+        del Q64, B64
+
+    # ---- mixed randQB_EI on the same A (narrow passes)
+    ei = None
+    try:
+        def step_ei():
+            out["e"] = qb.qb_ei_dense(hi, TOL, B, P=P, seed=SEED_OMEGA, a_lo=lo, src_norm2=normA2,
+                                      prec="mixed", rank_cap=RANK_CAP, out=(Qt, Bm))
+        t_ei = timed(torch, step_ei, max(1, args.steps // 2), 1, 1, stream)
+        ie = out["e"][2]
+        ei = {"time_to_tol_s": t_ei, "rank": ie.rank, "passes": ie.passes}
+    except Exception as e:  # pragma: no cover
+        ei = {"error": str(e)}
+
+    # ---- end to end through the public API with host buffers (pinned)
+    hi_h = hi.cpu().pin_memory()
+    lo_h = lo.cpu().pin_memory()
+    hi_d = torch.empty_like(hi)
+    lo_d = torch.empty_like(lo)
+    Qh = torch.empty(RANK_CAP, m, dtype=dt).pin_memory()
+    Bh = torch.empty(RANK_CAP, n, dtype=dt).pin_memory()
+    d2h = {"b": 0}
+
+    def step_e2e():
+        hi_d.copy_(hi_h, non_blocking=True)
+        lo_d.copy_(lo_h, non_blocking=True)
+        Qx, Bx, ix = qb.qb_fp_dense(hi_d, TOL, B, P=P, seed=SEED_OMEGA, a_lo=lo_d,
+                                    src_norm2=normA2, prec="mixed", rank_cap=RANK_CAP,
+                                    l_tilde=L_TILDE, out=(Qt, Bm), workspace=out["ws"])
+        k = ix.rank
+        Qh[:k].copy_(Qt[:k], non_blocking=True)
+        Bh[:k].copy_(Bm[:k], non_blocking=True)
+        d2h["b"] = 4 * k * (m + n)
+
+    t_e2e = timed(torch, step_e2e, max(1, args.steps // 2), 1, 1, stream)
+
+    # ---- max over ranks
+    if ws > 1:
+        tt = torch.tensor([t_step], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_step = float(tt.item())
+    if rank != 0:
+        return
+
+    sustained = pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
+    cpu = cpu_baseline(A64[: (1000 if args.quick else 4000)].cpu().numpy(), m)
+    line = {
+        "metric": METRIC, "value": t_step, "unit": "s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": config_dict(m, n),
+        "result": {"rank": info.rank, "status": info.status, "err_est": info.err_est / normA2 ** 0.5,
+                   "err_true": err_rel, "passes": info.passes, "blocks": info.blocks,
+                   "svd_rank": 1382 if not args.quick else None},
+        "roofline": {"bound": "tensor", "kernel": "tcgen05 sketch G = A_hi Omega (w = l~ = 3200)",
+                     "achieved": tf_sk, "peak": sustained, "unit": "TFLOP/s",
+                     "frac": tf_sk / sustained, "traffic": None,
+                     "peak_source": f"{pk_src} bf16_tflops_sustained"},
+        "apass": {"sketch_narrow_gbs": gbs_nar_sk, "trans_narrow_precise_gbs": gbs_nar_tr,
+                  "hbm_peak_gbs": hbm, "sketch_narrow_frac": gbs_nar_sk / hbm,
+                  "trans_narrow_frac": gbs_nar_tr / hbm, "w": B,
+                  "sketch_wide_ms": t_sk_wide * 1e3, "trans_wide_precise_ms": t_tr_wide * 1e3,
+                  "peak_source": pk_src},
+        "fp64_randqb_fp": fp64,
+        "mixed_randqb_ei": ei,
+        "e2e": {"value": t_e2e, "unit": "s", "h2d_bytes_per_step": int(2 * hi.numel() * 2),
+                "d2h_bytes_per_step": int(d2h["b"])},
+        "gpu_launches": gpu_launches,
+        "clocks": ck.summary(),
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    _ = np
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        torch.distributed.init_process_group(backend)
+    if args.impl == "reference":
+        if ws > 1 and rank != 0:
+            return
+        run_reference(args, ws, rank)
+        return
+    run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -26,7 +26,10 @@
  *   - Return value: negative = error, no valid output; 0 = converged; positive = valid output with
  *     a warning (QB_NOT_CONVERGED: rank cap or Omega budget reached first, Q and B hold the
  *     valid partial factorisation of info->rank columns; QB_WARN_TOL_FLOOR: the tolerance is
- *     below the Theorem 3 floor sqrt(4 u / 0.01) ||A||_F, so E may be inaccurate).
+ *     below the Theorem 3 floor sqrt(4 u / 0.01) ||A||_F, so E may be less accurate than 1%;
+ *     u = 2^-53 on the float64 path, 2^-24 on the mixed path, where Q and B are float32).
+ *   - Mixed path stopping rule: E < eps^2 - 2 u ||A||_F^2 (u = 2^-24), the margin covering the
+ *     rounding of ||B||^2 that Theorem 3 bounds, so ||A - QB||_F < eps still holds.
  */
 #ifndef GB300_QB_H
 #define GB300_QB_H
@@ -98,8 +101,12 @@ typedef struct {
     int64_t rank_cap;    /* capacity of Q and B in columns/rows; <= 0 means min(m, n) */
     int64_t l_tilde;     /* FP only: Omega batch width; <= 0 means 50 b (Sect. 5.4) */
     int32_t prec;        /* qb_prec */
-    int32_t flags;       /* reserved, 0 */
+    int32_t flags;       /* QB_FLAG_* bits, 0 by default */
 } qb_opts;
+
+/* qb_opts.flags: run the passes over a bf16 A on the SIMT kernels instead of the tensor cores
+ * (float32 FMA on the same bf16 data; slower, used to cross-check the tensor-core kernels). */
+#define QB_FLAG_SIMT_APASS 1
 
 typedef struct {
     int64_t rank;        /* columns of Q / rows of B that are valid */
@@ -159,9 +166,10 @@ int32_t qb_fp_csr(const qb_csr* A, const qb_opts* opts, void* Q, int64_t ldq, vo
  *                    (G = A Omega of Algorithm 4, A Omega_i of Algorithm 2); a bf16x2 A is read
  *                    through its hi part only.
  *   qb_apass_trans:  Z (n x w, column-major, ldz) = A^T V, V m x w column-major (ldv)
- *                    (H = A^T G of Algorithm 4, B_i^T = A^T Q_i of Algorithm 2).  precise != 0
- *                    with a bf16x2 A accumulates A_hi V_hi + A_hi V_lo + A_lo V_hi, V split into
- *                    bf16 hi + lo on the fly; otherwise A_hi bf16(V).
+ *                    (H = A^T G of Algorithm 4, B_i^T = A^T Q_i of Algorithm 2).  For a bf16x2 A:
+ *                    precise = 0: A_hi^T bf16(V) on the tensor cores (sketch precision);
+ *                    precise != 0: (A_hi + A_lo)^T V in float32 with round-to-nearest sums
+ *                    (the precision the indicator needs).  Float64 A ignores precise.
  * Workspace: qb_apass_workspace(A, w) bytes.
  * ------------------------------------------------------------------------------------------- */
 size_t qb_apass_workspace(const qb_dense* A, int64_t w);

@@ -74,12 +74,12 @@ def _dtype_code(t) -> int:
             torch.bfloat16: _lib.QB_BF16}[t.dtype]
 
 
-def _opts(tol, b, P, seed, relative, rank_cap, l_tilde, row_by_row, prec):
+def _opts(tol, b, P, seed, relative, rank_cap, l_tilde, row_by_row, prec, flags=0):
     return _lib.qb_opts(tol=float(tol), relative=int(bool(relative)), b=int(b), P=int(P),
                         row_by_row=int(bool(row_by_row)), seed=int(seed) & ((1 << 64) - 1),
                         rank_cap=int(rank_cap or 0), l_tilde=int(l_tilde or 0),
                         prec=_lib.QB_PREC_MIXED if prec == "mixed" else _lib.QB_PREC_FP64,
-                        flags=0)
+                        flags=int(flags))
 
 
 def _check_dev(*ts):
@@ -109,7 +109,7 @@ def _info(rc, inf):
 
 
 def _dense_call(fn, name, A, tol, b, P, seed, relative, rank_cap, l_tilde, row_by_row, prec,
-                a_lo, src_norm2, stream, out, workspace):
+                a_lo, src_norm2, stream, out, workspace, flags=0):
     torch = _torch()
     lib = _lib.load()
     _check_dev(A, a_lo)
@@ -123,7 +123,7 @@ def _dense_call(fn, name, A, tol, b, P, seed, relative, rank_cap, l_tilde, row_b
     d = _lib.qb_dense(m=m, n=n, ld=A.stride(0), dtype=dt, reserved=0, a=A.data_ptr(),
                       a_lo=a_lo.data_ptr() if a_lo is not None else None,
                       src_norm2=float("nan") if src_norm2 is None else float(src_norm2))
-    o = _opts(tol, b, P, seed, relative, rank_cap, l_tilde, row_by_row, prec)
+    o = _opts(tol, b, P, seed, relative, rank_cap, l_tilde, row_by_row, prec, flags)
     algo = 1 if name.startswith("qb_fp") else 0
     wsb = lib.qb_dense_workspace(C.byref(d), C.byref(o), algo)
     if wsb == 0:
@@ -145,21 +145,23 @@ def _dense_call(fn, name, A, tol, b, P, seed, relative, rank_cap, l_tilde, row_b
 
 
 def qb_ei_dense(A, tol, b, P=0, seed=0, relative=True, rank_cap=None, row_by_row=True,
-                prec="fp64", a_lo=None, src_norm2=None, stream=None, out=None, workspace=None):
+                prec="fp64", a_lo=None, src_norm2=None, stream=None, out=None, workspace=None,
+                flags=0):
     """randQB_EI (Algorithm 2) on a dense row-major A; returns (Q, B, QBInfo).
 
     Q is an m x rank view (column-major storage), B a rank x n row-major view."""
     return _dense_call(_lib.load().qb_ei_dense, "qb_ei_dense", A, tol, b, P, seed, relative,
-                       rank_cap, None, row_by_row, prec, a_lo, src_norm2, stream, out, workspace)
+                       rank_cap, None, row_by_row, prec, a_lo, src_norm2, stream, out, workspace,
+                       flags)
 
 
 def qb_fp_dense(A, tol, b, P=0, seed=0, relative=True, rank_cap=None, l_tilde=None,
                 row_by_row=True, prec="fp64", a_lo=None, src_norm2=None, stream=None, out=None,
-                workspace=None):
+                workspace=None, flags=0):
     """randQB_FP (Algorithm 4) on a dense row-major A; returns (Q, B, QBInfo)."""
     return _dense_call(_lib.load().qb_fp_dense, "qb_fp_dense", A, tol, b, P, seed, relative,
                        rank_cap, l_tilde, row_by_row, prec, a_lo, src_norm2, stream, out,
-                       workspace)
+                       workspace, flags)
 
 
 def _csr_call(fn, name, rowptr, colind, val, shape, tol, b, P, seed, relative, rank_cap, l_tilde,
@@ -274,7 +276,7 @@ def _apass(trans, A, V, precise, a_lo, stream):
     with torch.cuda.device(A.device):
         if trans:
             rc = lib.qb_apass_trans(C.byref(d), C.c_void_p(Vt.data_ptr()), rows_in, w,
-                                    int(bool(precise)), C.c_void_p(Yt.data_ptr()), rows_out,
+                                    int(precise), C.c_void_p(Yt.data_ptr()), rows_out,
                                     C.c_void_p(ws.data_ptr()), wsb, _stream_ptr(stream))
         else:
             rc = lib.qb_apass_sketch(C.byref(d), C.c_void_p(Vt.data_ptr()), rows_in, w,
@@ -290,6 +292,7 @@ def qb_apass_sketch(A, V, a_lo=None, stream=None):
     return _apass(False, A, V, False, a_lo, stream)
 
 
-def qb_apass_trans(A, V, precise=True, a_lo=None, stream=None):
-    """Z = A^T V (one pass over a dense row-major A); ``precise`` uses the hi/lo products."""
+def qb_apass_trans(A, V, precise=1, a_lo=None, stream=None):
+    """Z = A^T V (one pass over a dense row-major A).  For bf16 hi+lo A: precise=0 uses A_hi and
+    bf16(V), 1 the three hi/lo products, 2 (A_hi + A_lo) with bf16(V)."""
     return _apass(True, A, V, precise, a_lo, stream)

@@ -41,6 +41,7 @@ int num_sms() {
 namespace {
 
 constexpr double U64 = 1.1102230246251565e-16;   // 2^-53
+constexpr double U32 = 5.9604644775390625e-08;   // 2^-24
 constexpr double THM3_DELTA = 0.01;
 
 // ------------------------------------------------------------------------------------ context
@@ -61,6 +62,7 @@ struct Ctx {
     Acc acc_gram = ACC_D;     // Grams of panels
     Acc acc_proj = ACC_D;     // projections / updates
     Acc acc_fine = ACC_D;     // cancellation-prone products (FP's B_i formula, re-orth coefficients)
+    bool simt_apass = false;  // QB_FLAG_SIMT_APASS
 
     void alloc(Arena& ar, int64_t mn_max) {
         scr.part_bytes = gemm_scratch_bytes(mn_max);
@@ -154,11 +156,17 @@ struct AOp {
     virtual ~AOp() = default;
     virtual void reserve(Arena& ar, const Ctx& c, int64_t wmax) = 0;
     virtual void prepare(Ctx& c) = 0;
-    // Y (m x w) = A X (X: n x w); sketch passes may use the reduced representation of A
-    virtual void apply(Ctx& c, const void* X, int64_t ldx, int64_t w, void* Y, int64_t ldy) = 0;
-    // Y (n x w) = A^T X (X: m x w); precise = the pass that forms B_i or H
+    // Y (m x w) = A X (X: n x w); sketch passes may use the reduced representation of A.
+    // pairs = 2: X was rounded to two bf16 terms and both are used (randQB_FP's final G).
+    virtual void apply(Ctx& c, const void* X, int64_t ldx, int64_t w, void* Y, int64_t ldy,
+                       int pairs = 1) = 0;
+    // Y (n x w) = A^T X (X: m x w).  mode 1: sketch precision; mode 2: full A with an operand
+    // already rounded by round_operand(); mode 3: full A and full-precision operand (B_i = Q_i^T A)
     virtual void apply_t(Ctx& c, const void* X, int64_t ldx, int64_t w, void* Y, int64_t ldy,
-                         bool precise) = 0;
+                         int mode) = 0;
+    // Round an operand of the coming passes to the precision the passes consume (bf16 on the
+    // tensor-core path), in place, so that the projections against Q, B use the same values.
+    virtual void round_operand(Ctx&, void*, int64_t, int64_t, int64_t, int pairs = 1) {}
     // ||A||_F^2 (float64); non-finite entries raise c.flags[0]
     virtual double norm2(Ctx& c) = 0;
     // true when a bounded device-side wait of this operator's kernels ran out
@@ -191,11 +199,11 @@ struct DenseOp : AOp {
     }
     void reserve(Arena& ar, const Ctx& c, int64_t w) override {
         wmax = w;
-        use_tc = !c.f64 && tc_ok() && (ar.base == nullptr || tc_available());
+        use_tc = !c.f64 && !c.simt_apass && tc_ok() && (ar.base == nullptr || tc_available());
         if (use_tc) {
             tc_bytes = tc_scratch_bytes(m, n, w);
             tc_scr = ar.get<char>(int64_t(tc_bytes));
-            Xb = ar.get<bf16>(align_up(n, 8) * w);
+            Xb = ar.get<bf16>(2 * align_up(n, 8) * w);
         }
     }
     void prepare(Ctx& c) override {
@@ -208,11 +216,13 @@ struct DenseOp : AOp {
         QB_CUDA(cudaStreamSynchronize(c.st));
         return h != 0;
     }
-    void apply(Ctx& c, const void* X, int64_t ldx, int64_t w, void* Y, int64_t ldy) override {
+    void apply(Ctx& c, const void* X, int64_t ldx, int64_t w, void* Y, int64_t ldy,
+               int pairs) override {
         if (use_tc) {
             const int64_t ldb = align_up(n, 8);
-            to_bf16(c.st, reinterpret_cast<const float*>(X), ldx, n, w, Xb, ldb);
-            tc_sketch(c.st, reinterpret_cast<const bf16*>(d.a), d.ld, m, n, Xb, ldb, w,
+            bf16* lo = pairs == 2 ? Xb + ldb * wmax : nullptr;
+            split_bf16(c.st, reinterpret_cast<const float*>(X), ldx, n, w, Xb, lo, ldb);
+            tc_sketch(c.st, reinterpret_cast<const bf16*>(d.a), d.ld, m, n, Xb, lo, ldb, w,
                       reinterpret_cast<float*>(Y), ldy, tc_scr, tc_bytes);
             return;
         }
@@ -221,16 +231,30 @@ struct DenseOp : AOp {
              c.f64 ? ACC_D : ACC_F, c.scr);
     }
     void apply_t(Ctx& c, const void* X, int64_t ldx, int64_t w, void* Y, int64_t ldy,
-                 bool precise) override {
-        if (use_tc) {
-            tc_trans(c.st, reinterpret_cast<const bf16*>(d.a), reinterpret_cast<const bf16*>(d.a_lo),
-                     d.ld, m, n, reinterpret_cast<const float*>(X), ldx, w,
-                     reinterpret_cast<float*>(Y), ldy, precise && d.dtype == QB_BF16X2, tc_scr,
-                     tc_bytes);
+                 int mode) override {
+        if (!c.f64 && mode >= 2 && d.dtype == QB_BF16X2) {
+            // The passes that feed the indicator (B_i = Q_i^T A, H = A^T G) run with
+            // round-to-nearest float32 sums: tensor-core float32 accumulation is not
+            // round-to-nearest and biases ||B_i||^2 low on long reductions.
+            trans_precise(c.st, reinterpret_cast<const bf16*>(d.a),
+                          reinterpret_cast<const bf16*>(d.a_lo), d.ld, m, n,
+                          reinterpret_cast<const float*>(X), ldx, w, reinterpret_cast<float*>(Y),
+                          ldy, c.scr);
             return;
         }
-        gemm(c.st, false, n, w, m, 1.0, xa(precise), X, c.f64, ldx, 0.0, Y, c.f64, ldy,
+        if (use_tc) {
+            const int md = d.dtype == QB_BF16X2 ? mode : 1;
+            tc_trans(c.st, reinterpret_cast<const bf16*>(d.a), reinterpret_cast<const bf16*>(d.a_lo),
+                     d.ld, m, n, reinterpret_cast<const float*>(X), ldx, w,
+                     reinterpret_cast<float*>(Y), ldy, md, tc_scr, tc_bytes);
+            return;
+        }
+        gemm(c.st, false, n, w, m, 1.0, xa(mode > 1), X, c.f64, ldx, 0.0, Y, c.f64, ldy,
              c.f64 ? ACC_D : ACC_F, c.scr);
+    }
+    void round_operand(Ctx& c, void* X, int64_t ldx, int64_t rows, int64_t w,
+                       int pairs) override {
+        if (use_tc) round_bf16_inplace(c.st, reinterpret_cast<float*>(X), ldx, rows, w, pairs);
     }
     double norm2(Ctx& c) override {
         if (!std::isnan(d.src_norm2)) return d.src_norm2;
@@ -262,10 +286,10 @@ struct CsrOp : AOp {
         CsrDev A{m, n, s.nnz, s.rowptr, s.colind, s.val, f64v()};
         csr_to_csc(c.st, A, colptr, rowind, cval, cnt);
     }
-    void apply(Ctx& c, const void* X, int64_t ldx, int64_t w, void* Y, int64_t ldy) override {
+    void apply(Ctx& c, const void* X, int64_t ldx, int64_t w, void* Y, int64_t ldy, int) override {
         csr_spmm(c.st, f64v(), s.rowptr, s.colind, s.val, m, n, X, ldx, w, Y, ldy, stage);
     }
-    void apply_t(Ctx& c, const void* X, int64_t ldx, int64_t w, void* Y, int64_t ldy, bool) override {
+    void apply_t(Ctx& c, const void* X, int64_t ldx, int64_t w, void* Y, int64_t ldy, int) override {
         csr_spmm(c.st, f64v(), colptr, rowind, cval, n, m, X, ldx, w, Y, ldy, stage);
     }
     double norm2(Ctx& c) override {
@@ -358,6 +382,7 @@ void run_ei(Ctx& c, AOp& A, const Plan& p, const qb_opts& o, Bufs& bf, void* Q, 
         out.omega_cols = k + bi;
         // Omega_i = randn(n, b), global columns [k, k + bi)
         omega_gen(c.st, n, k, bi, o.seed, omega_dt, bf.Om, n);
+        A.round_operand(c, bf.Om, n, n, bi);
         // Y = A Omega_i - Q (B Omega_i), computed in the slot of Q_i
         char* Y = c.col(Q, ldq, k);
         A.apply(c, bf.Om, n, bi, Y, ldq);
@@ -368,13 +393,15 @@ void run_ei(Ctx& c, AOp& A, const Plan& p, const qb_opts& o, Bufs& bf, void* Q, 
         }
         for (int it = 0; it < p.P; ++it) {
             c.cholqr2(Y, ldq, m, bi, false);                                      // Y = orth(Y)
-            A.apply_t(c, Y, ldq, bi, bf.Z, n, false);                             // Z = A^T Y
+            A.round_operand(c, Y, ldq, m, bi);
+            A.apply_t(c, Y, ldq, bi, bf.Z, n, 1);                                 // Z = A^T Y
             out.passes += 1;
             if (k > 0) {
                 c.tn(k, bi, m, 1.0, Q, ldq, Y, ldq, 0.0, bf.T1, k, c.acc_proj);   // Q^T Y
                 c.nn(n, bi, k, -1.0, B, ldb, bf.T1, k, 1.0, bf.Z, n, c.acc_proj); // Z -= B^T (.)
             }
             c.cholqr2(bf.Z, n, n, bi, false);                                     // Z = orth(Z)
+            A.round_operand(c, bf.Z, n, n, bi);
             A.apply(c, bf.Z, n, bi, Y, ldq);                                      // Y = A Z
             out.passes += 1;
             if (k > 0) {
@@ -389,7 +416,7 @@ void run_ei(Ctx& c, AOp& A, const Plan& p, const qb_opts& o, Bufs& bf, void* Q, 
         }
         // B_i = Q_i^T A, written as rows k.. of B (= column-major n x bi with ld ldb)
         char* Bs = c.col(B, ldb, k);
-        A.apply_t(c, Y, ldq, bi, Bs, ldb, true);
+        A.apply_t(c, Y, ldq, bi, Bs, ldb, 3);
         out.passes += 1;
         const Ctx::Step s = c.indicator_step(Bs, ldb, bi, n, eps2, o.row_by_row);
         out.blocks += 1;
@@ -413,6 +440,7 @@ void run_fp(Ctx& c, AOp& A, const Plan& p, const qb_opts& o, Bufs& bf, void* Q, 
         const int64_t col0 = q * p.lt;
         out.omega_cols = col0 + w;
         omega_gen(c.st, n, col0, w, o.seed, omega_dt, bf.Om, n);                 // Omega = randn(n, l~)
+        A.round_operand(c, bf.Om, n, n, w);
         for (int it = 0; it < p.P; ++it) {                                       // power scheme
             A.apply(c, bf.Om, n, w, bf.G, m);                                     // G = A Omega
             out.passes += 1;
@@ -421,16 +449,22 @@ void run_fp(Ctx& c, AOp& A, const Plan& p, const qb_opts& o, Bufs& bf, void* Q, 
                 c.nn(m, w, k, -1.0, Q, ldq, bf.T1, k, 1.0, bf.G, m, c.acc_proj);
             }
             c.orth_wide(bf.G, m, m, w, p.b, bf.Tw);                               // G = orth(.)
-            A.apply_t(c, bf.G, m, w, bf.Om, n, false);                            // Omega = A^T G
+            A.round_operand(c, bf.G, m, m, w);
+            A.apply_t(c, bf.G, m, w, bf.Om, n, 1);                                // Omega = A^T G
             out.passes += 1;
             if (k > 0) {
                 c.tn(k, w, m, 1.0, Q, ldq, bf.G, m, 0.0, bf.T1, k, c.acc_proj);
                 c.nn(n, w, k, -1.0, B, ldb, bf.T1, k, 1.0, bf.Om, n, c.acc_proj);
             }
             c.orth_wide(bf.Om, n, n, w, p.b, bf.Tw);                              // Omega = orth(.)
+            // The B_i formula cancels the components of H_i = A^T G_i along singular vectors
+            // already in Q; a bf16-rounded Omega (2^-9) would leak sigma_1^2-sized terms into
+            // every H_i, so the processed Omega keeps two bf16 terms (16 bits).
+            A.round_operand(c, bf.Om, n, n, w, 2);
         }
-        A.apply(c, bf.Om, n, w, bf.G, m);                                         // G = A Omega
-        A.apply_t(c, bf.G, m, w, bf.H, n, true);                                  // H = A^T G
+        A.apply(c, bf.Om, n, w, bf.G, m, p.P > 0 ? 2 : 1);                        // G = A Omega
+        // H = A^T G for the stored G, in the precision the B_i formula needs
+        A.apply_t(c, bf.G, m, w, bf.H, n, 3);                                     // H = A^T G
         out.passes += 1;
         for (int64_t c0 = 0; c0 < w && !stop; c0 += p.b) {
             const int bi = int(std::min<int64_t>(p.b, w - c0));
@@ -485,6 +519,7 @@ int32_t run_common(AOp& A, const qb_opts* opts, bool fp, void* Q, int64_t ldq, v
     const Plan p = make_plan(A.m, A.n, o, fp);
     Ctx c;
     setup_ctx(c, o.prec == QB_PREC_FP64);
+    c.simt_apass = (o.flags & QB_FLAG_SIMT_APASS) != 0;
     c.st = reinterpret_cast<cudaStream_t>(stream);
     Bufs bf;
     Arena ar;
@@ -522,10 +557,15 @@ int32_t run_common(AOp& A, const qb_opts* opts, bool fp, void* Q, int64_t ldq, v
         return QB_ERR_NONFINITE;
     }
     const double eps = o.relative ? o.tol * std::sqrt(normA2) : o.tol;
-    const double eps2 = eps * eps;
+    // Theorem 3 bounds the rounding error of E by 2u(||A||^2 + ||B||^2).  ||A||^2 is exact to
+    // float64 here; on the mixed path the rows of B carry float32 rounding (u = 2^-24), so the
+    // stop test keeps a margin 2 u ||A||^2 >= 2 u ||B||^2 to guarantee ||A - QB|| < eps.
+    const double u_work = o.prec == QB_PREC_FP64 ? U64 : U32;
+    const double margin = o.prec == QB_PREC_FP64 ? 0.0 : 2.0 * U32 * normA2;
+    const double eps2 = eps * eps - margin;
     if (normA2 == 0.0 || p.cap == 0) {
         out.E = normA2;
-        out.converged = normA2 < eps2 || normA2 == 0.0;
+        out.converged = normA2 < eps * eps || normA2 == 0.0;
         fill_info(out.converged ? 0 : QB_BIT_NOT_CONVERGED);
         return out.converged ? QB_OK : QB_NOT_CONVERGED;
     }
@@ -540,7 +580,7 @@ int32_t run_common(AOp& A, const qb_opts* opts, bool fp, void* Q, int64_t ldq, v
     c.read_flags(hf);
     int32_t bits = 0;
     if (hf[1]) bits |= QB_BIT_BREAKDOWN;
-    const double floor = std::sqrt(4.0 * U64 / THM3_DELTA) * std::sqrt(normA2);
+    const double floor = std::sqrt(4.0 * u_work / THM3_DELTA) * std::sqrt(normA2);
     int32_t status = QB_OK;
     if (!out.converged) {
         bits |= QB_BIT_NOT_CONVERGED;
@@ -717,8 +757,8 @@ static int32_t apass(const qb_dense* A, bool trans, const void* V, int64_t ldv, 
         DenseOp op(*A);
         op.reserve(ar, c, std::max<int64_t>(w, 1));
         op.prepare(c);
-        if (trans) op.apply_t(c, V, ldv, w, Y, ldy, precise != 0);
-        else op.apply(c, V, ldv, w, Y, ldy);
+        if (trans) op.apply_t(c, V, ldv, w, Y, ldy, precise == 0 ? 1 : (precise == 2 ? 2 : 3));
+        else op.apply(c, V, ldv, w, Y, ldy, 1);
         if (op.timed_out(c)) return int32_t(QB_ERR_TIMEOUT);
         return int32_t(QB_OK);
     });

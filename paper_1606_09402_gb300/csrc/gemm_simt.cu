@@ -218,6 +218,99 @@ void dispatch_x(cudaStream_t st, bool xt, int64_t M, int64_t N, int64_t K, doubl
     }
 }
 
+// ---------------------------------------------------------------- precise A^T V pass
+// Z (n x w, column-major) = (A_hi + A_lo)^T V, A row-major m x n as two bf16 arrays, V float32
+// column-major m x w.  Float32 FMA with exact operands (A_hi + A_lo and V are float32 values):
+// every product and partial sum is rounded to nearest, so the result carries no systematic drift
+// (the pass that forms B_i = Q_i^T A and H = A^T G feeds the indicator of Theorem 1).
+// 128 x 64 output tile, 8 x 4 per thread, k step 16, double-buffered shared memory.
+constexpr int TM_ = 128, TN_ = 64, TK_ = 16;
+
+__global__ void __launch_bounds__(256)
+k_trans_prec(int64_t m, int64_t n, int64_t w, int64_t kchunk, const bf16* __restrict__ Ahi,
+             const bf16* __restrict__ Alo, int64_t lda, const float* __restrict__ V, int64_t ldv,
+             float* __restrict__ Z, int64_t ldz, float* __restrict__ part) {
+    __shared__ __align__(16) float As[2][TK_][TM_];
+    __shared__ __align__(16) float Vs[2][TK_][TN_];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t n0 = int64_t(blockIdx.x) * TM_, w0 = int64_t(blockIdx.y) * TN_;
+    const int64_t kb = int64_t(blockIdx.z) * kchunk, ke = min(m, kb + kchunk);
+    float acc[8][4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    float ra[8], rv[4];
+    auto gload = [&](int64_t k0) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int e = tid + 256 * q, r = e / TM_, c = e % TM_;
+            const int64_t gk = k0 + r, gn = n0 + c;
+            float v = 0.f;
+            if (gk < ke && gn < n) {
+                const int64_t o = gk * lda + gn;
+                v = __bfloat162float(Ahi[o]) + __bfloat162float(Alo[o]);
+            }
+            ra[q] = v;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = tid + 256 * q, r = e % TK_, c = e / TK_;
+            const int64_t gk = k0 + r, gw = w0 + c;
+            rv[q] = (gk < ke && gw < w) ? V[gk + gw * ldv] : 0.f;
+        }
+    };
+    auto sstore = [&](int buf) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int e = tid + 256 * q;
+            As[buf][e / TM_][e % TM_] = ra[q];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = tid + 256 * q;
+            Vs[buf][e % TK_][e / TK_] = rv[q];
+        }
+    };
+    int buf = 0;
+    if (kb < ke) {
+        gload(kb);
+        sstore(0);
+    }
+    __syncthreads();
+    for (int64_t k0 = kb; k0 < ke; k0 += TK_) {
+        const bool more = k0 + TK_ < ke;
+        if (more) gload(k0 + TK_);
+#pragma unroll
+        for (int kk = 0; kk < TK_; ++kk) {
+            const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][tx * 4]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][64 + tx * 4]);
+            const float4 b = *reinterpret_cast<const float4*>(&Vs[buf][kk][ty * 4]);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        }
+        if (more) sstore(buf ^ 1);
+        __syncthreads();
+        buf ^= 1;
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int64_t gn = n0 + (i < 4 ? tx * 4 + i : 64 + tx * 4 + (i - 4));
+        if (gn >= n) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t gw = w0 + ty * 4 + j;
+            if (gw >= w) continue;
+            if (part) part[(int64_t(blockIdx.z) * w + gw) * n + gn] = acc[i][j];
+            else Z[gn + gw * ldz] = acc[i][j];
+        }
+    }
+}
+
 }  // namespace
 
 size_t gemm_scratch_bytes(int64_t mn_max) {
@@ -247,6 +340,31 @@ void gemm(cudaStream_t st, bool xt, int64_t M, int64_t N, int64_t K, double alph
         if (c_f64) throw Error{QB_ERR_UNSUPPORTED, "ACC_F writes f32"};
         dispatch_x<AccFv, float>(st, xt, M, N, K, alpha, X, Y, ldy, beta,
                                  reinterpret_cast<float*>(C), ldc, scr);
+    }
+}
+
+void trans_precise(cudaStream_t st, const bf16* Ahi, const bf16* Alo, int64_t lda, int64_t m,
+                   int64_t n, const float* V, int64_t ldv, int64_t w, float* Z, int64_t ldz,
+                   const GemmScratch& scr) {
+    if (n <= 0 || w <= 0) return;
+    const int64_t tiles = cdiv(n, TM_) * cdiv(w, TN_);
+    const int64_t target = 2LL * num_sms();
+    int64_t splits = 1;
+    if (tiles < target && m > 0) {
+        splits = std::min<int64_t>(cdiv(target, tiles), cdiv(m, 1024));
+        splits = std::max<int64_t>(1, std::min<int64_t>(splits, MAX_SPLITS));
+        while (splits > 1 && size_t(splits) * n * w * sizeof(float) > scr.part_bytes) --splits;
+    }
+    const int64_t kchunk = splits > 1 ? align_up(cdiv(m, splits), TK_) : std::max<int64_t>(m, 1);
+    splits = m > 0 ? cdiv(m, kchunk) : 1;
+    float* part = splits > 1 ? reinterpret_cast<float*>(scr.part) : nullptr;
+    dim3 grid(unsigned(cdiv(n, TM_)), unsigned(cdiv(w, TN_)), unsigned(splits));
+    k_trans_prec<<<grid, 256, 0, st>>>(m, n, w, kchunk, Ahi, Alo, lda, V, ldv, Z, ldz, part);
+    QB_LAUNCHED();
+    if (part) {
+        k_splitk_reduce<float, float><<<unsigned(cdiv(n * w, 256)), 256, 0, st>>>(
+            n, w, int(splits), part, Z, ldz, 1.0, 0.0);
+        QB_LAUNCHED();
     }
 }
 

@@ -8,8 +8,8 @@
 //   trans  (B_i^T = A^T Q_i, H = A^T G, Z = A^T Y):  D (n x w) = A^T (n x m) * V (m x w)
 //       A operand: column slab of A [64 k rows x 128 n] as two 64-column boxes (MN-major)
 //       B operand: V^T tile [BN x 64 k] (K-major)
-//   Up to three products accumulate into one tile: A_hi V_hi, A_hi V_lo, A_lo V_hi, where
-//   A = A_hi + A_lo and V = V_hi + V_lo are bf16 pairs (float32-like operands).
+//   Up to three products accumulate into one tile: A_hi V_hi, A_lo V_hi (NA = 2) and A_hi V_lo
+//   (NB = 2), where A = A_hi + A_lo and V = V_hi + V_lo are bf16 pairs.
 //
 // Persistent CTAs (one per SM).  Work is the list of (row tile, column tile) units x the k-blocks
 // of each unit.  With several column tiles every CTA takes whole units in raster order (row tile
@@ -160,7 +160,7 @@ __host__ __device__ __forceinline__ int64_t sk_begin(int64_t total, int64_t c, i
 // ---------------------------------------------------------------- kernel
 struct Params {
     int M, N, K;                 // D is M x N, reduction length K
-    int nprod;                   // 1..3 products
+    int chunk;                   // k-blocks accumulated in tensor memory before a register flush
     Sched s;
     float* D;
     int64_t ldd;
@@ -298,39 +298,42 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
         int buf = 0;
         uint32_t tphase[2] = {0, 0};
         while (ok && next_seg(pos, sg, first)) {
-            ok = mbar_wait(tempty + buf, tphase[buf] ^ 1, p.err);
-            if (!ok) break;
-            tc_fence_after();
-            const uint32_t acc = tmem + uint32_t(buf * BN);
-            for (int kb = sg.k0; kb < sg.k1 && ok; ++kb) {
-                ok = mbar_wait(full + stage, phase, p.err);
+            for (int c0 = sg.k0; c0 < sg.k1 && ok; c0 += p.chunk) {
+                const int c1 = min(sg.k1, c0 + p.chunk);
+                ok = mbar_wait(tempty + buf, tphase[buf] ^ 1, p.err);
                 if (!ok) break;
                 tc_fence_after();
-                const uint32_t sa = smem_u32(smem + stage * C::STAGE);
-                const uint32_t sbb = sa + NA * C::A_TILE;
+                const uint32_t acc = tmem + uint32_t(buf * BN);
+                for (int kb = c0; kb < c1 && ok; ++kb) {
+                    ok = mbar_wait(full + stage, phase, p.err);
+                    if (!ok) break;
+                    tc_fence_after();
+                    const uint32_t sa = smem_u32(smem + stage * C::STAGE);
+                    const uint32_t sbb = sa + NA * C::A_TILE;
 #pragma unroll
-                for (int kk = 0; kk < BK / UMMA_K; ++kk) {
-                    uint64_t da[2], db[2];
+                    for (int kk = 0; kk < BK / UMMA_K; ++kk) {
+                        uint64_t da[2], db[2];
 #pragma unroll
-                    for (int q = 0; q < NA; ++q) {
-                        const uint32_t base = sa + q * C::A_TILE;
-                        da[q] = TRANS ? sdesc(base + kk * (UMMA_K * 128), C::A_TILE / 2, 1024)
-                                      : sdesc(base + kk * (UMMA_K * 2), 16, 1024);
+                        for (int q = 0; q < NA; ++q) {
+                            const uint32_t base = sa + q * C::A_TILE;
+                            da[q] = TRANS ? sdesc(base + kk * (UMMA_K * 128), C::A_TILE / 2, 1024)
+                                          : sdesc(base + kk * (UMMA_K * 2), 16, 1024);
+                        }
+#pragma unroll
+                        for (int q = 0; q < NB; ++q)
+                            db[q] = sdesc(sbb + q * C::B_TILE + kk * (UMMA_K * 2), 16, 1024);
+                        const uint32_t accum = (kb > c0 || kk > 0) ? 1u : 0u;
+                        tc_mma(acc, da[0], db[0], idesc, accum);                   // A_hi V_hi
+                        if (NA > 1) tc_mma(acc, da[NA - 1], db[0], idesc, 1u);      // A_lo V_hi
+                        if (NB > 1) tc_mma(acc, da[0], db[NB - 1], idesc, 1u);      // A_hi V_lo
                     }
-#pragma unroll
-                    for (int q = 0; q < NB; ++q)
-                        db[q] = sdesc(sbb + q * C::B_TILE + kk * (UMMA_K * 2), 16, 1024);
-                    const uint32_t accum = (kb > sg.k0 || kk > 0) ? 1u : 0u;
-                    tc_mma(acc, da[0], db[0], idesc, accum);                  // hi * hi
-                    if (p.nprod > 1) tc_mma(acc, da[0], db[NB - 1], idesc, 1u);  // hi * V_lo
-                    if (p.nprod > 2) tc_mma(acc, da[NA - 1], db[0], idesc, 1u);  // A_lo * hi
+                    tc_commit(empty + stage);
+                    if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
                 }
-                tc_commit(empty + stage);
-                if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
+                tc_commit(tfull + buf);
+                tphase[buf] ^= 1;
+                buf ^= 1;
             }
-            tc_commit(tfull + buf);
-            tphase[buf] ^= 1;
-            buf ^= 1;
         }
     } else if (warp >= 2) {
         // ---------------------------------------------------------- epilogue
@@ -342,34 +345,42 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
         int buf = 0;
         uint32_t tphase[2] = {0, 0};
         while (ok && next_seg(pos, sg, first)) {
-            ok = mbar_wait(tfull + buf, tphase[buf], p.err);
+            // Sum the chunk accumulators of this segment in registers (round to nearest), so the
+            // float32 result carries no drift from long tensor-core accumulation chains.
+            float accr[BN];
+#pragma unroll
+            for (int j = 0; j < BN; ++j) accr[j] = 0.f;
+            for (int c0 = sg.k0; c0 < sg.k1 && ok; c0 += p.chunk) {
+                ok = mbar_wait(tfull + buf, tphase[buf], p.err);
+                if (!ok) break;
+                tc_fence_after();
+#pragma unroll
+                for (int cc = 0; cc < BN; cc += 32) {
+                    float v[32];
+                    tmem_ld32(tmem + (uint32_t(q * 32) << 16) + uint32_t(buf * BN + cc), v);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) accr[cc + j] += v[j];
+                }
+                tc_fence_before();
+                mbar_arrive(tempty + buf);
+                tphase[buf] ^= 1;
+                buf ^= 1;
+            }
             if (!ok) break;
-            tc_fence_after();
             int r0, c0;
             unit_rc(sg.u, r0, c0);
             const int64_t gr = int64_t(r0) + row;
-            float* slot = sg.slot >= 0
-                              ? p.part + ((int64_t(cta) * 2 + sg.slot) * BN) * BM
-                              : nullptr;
-#pragma unroll 1
-            for (int cc = 0; cc < BN; cc += 32) {
-                float v[32];
-                tmem_ld32(tmem + (uint32_t(q * 32) << 16) + uint32_t(buf * BN + cc), v);
-                if (slot) {
+            if (sg.slot >= 0) {
+                float* slot = p.part + ((int64_t(cta) * 2 + sg.slot) * BN) * BM;
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) slot[int64_t(cc + j) * BM + row] = v[j];
-                } else if (gr < p.M) {
+                for (int j = 0; j < BN; ++j) slot[int64_t(j) * BM + row] = accr[j];
+            } else if (gr < p.M) {
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int gc = c0 + cc + j;
-                        if (gc < p.N) p.D[gr + int64_t(gc) * p.ldd] = v[j];
-                    }
+                for (int j = 0; j < BN; ++j) {
+                    const int gc = c0 + j;
+                    if (gc < p.N) p.D[gr + int64_t(gc) * p.ldd] = accr[j];
                 }
             }
-            tc_fence_before();
-            mbar_arrive(tempty + buf);
-            tphase[buf] ^= 1;
-            buf ^= 1;
         }
     }
     __syncwarp();
@@ -461,13 +472,13 @@ CUtensorMap make_map(const void* ptr, int64_t inner, int64_t outer, int64_t ld, 
     return m;
 }
 
-// Column tile: the narrowest of 64 / 128 / 256 that holds w; the three-product passes stop at 128
-// so that three pipeline stages (64 KB each) fit in shared memory.
-int pick_bn(int64_t w, bool precise) {
-    if (w <= 64) return 64;
-    if (w <= 128 || precise) return 128;
-    return 256;
-}
+// Column tile: 64 or 128 columns (the epilogue keeps one float32 register per column).
+int pick_bn(int64_t w, bool) { return w <= 64 ? 64 : 128; }
+
+// k-blocks per tensor-memory chunk: the tensor cores' float32 accumulation drifts toward zero by
+// roughly 1e-9 (relative) per accumulated MMA (measured: -3.4e-6 over a 40000-long chain), so
+// chains are kept to 4 (sketch) or 1 (full-precision passes) k-blocks and summed in registers.
+int pick_chunk(int mode) { return mode >= 2 ? 1 : 4; }
 
 template <int BN, bool TRANS, int NA, int NB>
 void run(cudaStream_t st, const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& b0,
@@ -487,8 +498,7 @@ template <bool TRANS, int NA, int NB>
 void run_bn(int bn, cudaStream_t st, const CUtensorMap& a0, const CUtensorMap& a1,
             const CUtensorMap& b0, const CUtensorMap& b1, Params p, int G) {
     if (bn == 64) run<64, TRANS, NA, NB>(st, a0, a1, b0, b1, p, G);
-    else if (bn == 128) run<128, TRANS, NA, NB>(st, a0, a1, b0, b1, p, G);
-    else run<256, TRANS, NA, NB>(st, a0, a1, b0, b1, p, G);
+    else run<128, TRANS, NA, NB>(st, a0, a1, b0, b1, p, G);
 }
 
 struct Scratch {
@@ -558,7 +568,8 @@ size_t tc_scratch_bytes(int64_t m, int64_t n, int64_t w) {
 }
 
 void tc_sketch(cudaStream_t st, const bf16* A, int64_t lda, int64_t m, int64_t n, const bf16* Vt,
-               int64_t ldv, int64_t w, float* Y, int64_t ldy, void* scratch, size_t scratch_bytes) {
+               const bf16* Vt_lo, int64_t ldv, int64_t w, float* Y, int64_t ldy, void* scratch,
+               size_t scratch_bytes) {
     if (m <= 0 || w <= 0) return;
     Scratch s = carve(scratch, scratch_bytes, 0, 0);
     const int bn = pick_bn(w, false);
@@ -566,7 +577,7 @@ void tc_sketch(cudaStream_t st, const bf16* A, int64_t lda, int64_t m, int64_t n
     p.M = int(m);
     p.N = int(w);
     p.K = int(n);
-    p.nprod = 1;
+    p.chunk = pick_chunk(1);
     int G = num_sms();
     p.s = make_sched(m, w, n, bn, G);
     G = grid_size(p.s, G);
@@ -578,24 +589,30 @@ void tc_sketch(cudaStream_t st, const bf16* A, int64_t lda, int64_t m, int64_t n
         throw Error{QB_ERR_WORKSPACE, "tensor-core partials"};
     const CUtensorMap a = make_map(A, n, m, lda, BK, BM);
     const CUtensorMap b = make_map(Vt, n, w, ldv, BK, bn);
-    run_bn<false, 1, 1>(bn, st, a, a, b, b, p, G);
+    if (Vt_lo) {
+        const CUtensorMap b1 = make_map(Vt_lo, n, w, ldv, BK, bn);
+        run_bn<false, 1, 2>(bn, st, a, a, b, b1, p, G);
+    } else {
+        run_bn<false, 1, 1>(bn, st, a, a, b, b, p, G);
+    }
 }
 
 void tc_trans(cudaStream_t st, const bf16* A_hi, const bf16* A_lo, int64_t lda, int64_t m,
-              int64_t n, const float* V, int64_t ldv, int64_t w, float* Z, int64_t ldz,
-              bool precise, void* scratch, size_t scratch_bytes) {
+              int64_t n, const float* V, int64_t ldv, int64_t w, float* Z, int64_t ldz, int mode,
+              void* scratch, size_t scratch_bytes) {
     if (n <= 0 || w <= 0) return;
+    if (mode < 1 || mode > 3 || (mode > 1 && !A_lo)) throw Error{QB_ERR_INVALID_ARG, "tc_trans mode"};
     Scratch s = carve(scratch, scratch_bytes, m, w);
     const int64_t ldo = align_up(m, 8);
     k_split_bf16<<<unsigned(cdiv(m * w, 256)), 256, 0, st>>>(V, ldv, m, w, s.vhi,
-                                                             precise ? s.vlo : nullptr, ldo);
+                                                             mode == 3 ? s.vlo : nullptr, ldo);
     QB_LAUNCHED();
-    const int bn = pick_bn(w, precise);
+    const int bn = pick_bn(w, mode > 1);
     Params p{};
     p.M = int(n);
     p.N = int(w);
     p.K = int(m);
-    p.nprod = precise ? 3 : 1;
+    p.chunk = pick_chunk(mode);
     int G = num_sms();
     p.s = make_sched(n, w, m, bn, G);
     G = grid_size(p.s, G);
@@ -608,13 +625,42 @@ void tc_trans(cudaStream_t st, const bf16* A_hi, const bf16* A_lo, int64_t lda, 
     // A as an (n inner, m outer) tensor; boxes of 64 columns x 64 rows
     const CUtensorMap a0 = make_map(A_hi, n, m, lda, 64, BK);
     const CUtensorMap b0 = make_map(s.vhi, m, w, ldo, BK, bn);
-    if (precise) {
-        const CUtensorMap a1 = make_map(A_lo, n, m, lda, 64, BK);
-        const CUtensorMap b1 = make_map(s.vlo, m, w, ldo, BK, bn);
-        run_bn<true, 2, 2>(bn, st, a0, a1, b0, b1, p, G);
-    } else {
+    if (mode == 1) {
         run_bn<true, 1, 1>(bn, st, a0, a0, b0, b0, p, G);
+        return;
     }
+    const CUtensorMap a1 = make_map(A_lo, n, m, lda, 64, BK);
+    if (mode == 2) {
+        run_bn<true, 2, 1>(bn, st, a0, a1, b0, b0, p, G);
+        return;
+    }
+    const CUtensorMap b1 = make_map(s.vlo, m, w, ldo, BK, bn);
+    run_bn<true, 2, 2>(bn, st, a0, a1, b0, b1, p, G);
+}
+
+void split_bf16(cudaStream_t st, const float* V, int64_t ldv, int64_t rows, int64_t w, bf16* hi,
+                bf16* lo, int64_t ldo) {
+    if (rows <= 0 || w <= 0) return;
+    k_split_bf16<<<unsigned(cdiv(rows * w, 256)), 256, 0, st>>>(V, ldv, rows, w, hi, lo, ldo);
+    QB_LAUNCHED();
+}
+
+// Round a float32 column-major block to bf16-representable values in place.
+// pairs == 1: X <- bf16(X); pairs == 2: X <- bf16(X) + bf16(X - bf16(X)) (16 significant bits)
+__global__ void k_round_bf16(float* X, int64_t ldx, int64_t rows, int64_t cols, int pairs) {
+    const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (idx >= rows * cols) return;
+    const int64_t i = idx % rows, j = idx / rows;
+    float& v = X[i + j * ldx];
+    const float h = __bfloat162float(__float2bfloat16_rn(v));
+    v = pairs == 1 ? h : h + __bfloat162float(__float2bfloat16_rn(v - h));
+}
+
+void round_bf16_inplace(cudaStream_t st, float* X, int64_t ldx, int64_t rows, int64_t cols,
+                        int pairs) {
+    if (rows <= 0 || cols <= 0) return;
+    k_round_bf16<<<unsigned(cdiv(rows * cols, 256)), 256, 0, st>>>(X, ldx, rows, cols, pairs);
+    QB_LAUNCHED();
 }
 
 }  // namespace qb

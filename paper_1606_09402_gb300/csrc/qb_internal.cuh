@@ -92,22 +92,34 @@ void gemm(cudaStream_t st, bool xt, int64_t M, int64_t N, int64_t K, double alph
           Acc acc, const GemmScratch& scr);
 // bytes of split-K partial storage needed by gemm() for any (M, N) with M * N <= mn_max
 size_t gemm_scratch_bytes(int64_t mn_max);
+// Z (n x w, col-major) = (A_hi + A_lo)^T V in float32 with round-to-nearest sums (SIMT)
+void trans_precise(cudaStream_t st, const bf16* Ahi, const bf16* Alo, int64_t lda, int64_t m,
+                   int64_t n, const float* V, int64_t ldv, int64_t w, float* Z, int64_t ldz,
+                   const GemmScratch& scr);
 
 // ------------------------------------------------------------------------------------ tcgen05
 // BF16 tensor-core passes over dense A (row-major m x n, bf16 hi [+ lo]).
 //   sketch: Y (m x w, col-major, float) = A_hi * V, V given as bf16 column-major n x w
-//   trans : Z (n x w, col-major, float) = (A_hi + A_lo)^T * (V_hi + V_lo)  (3 products) or
-//           A_hi^T * V_hi (1 product); V float column-major m x w, split on the fly.
+//   trans : Z (n x w, col-major, float) = A^T V with V float column-major m x w:
+//           mode 1: A_hi^T bf16(V); mode 2: (A_hi + A_lo)^T bf16(V) (exact for bf16-valued V);
+//           mode 3: A_hi^T V_hi + A_lo^T V_hi + A_hi^T V_lo with V = V_hi + V_lo split on the fly.
 bool tc_available();
 // scratch layout starts with a 256-byte error area: word 0 is set when a bounded wait timed out
 size_t tc_scratch_bytes(int64_t m, int64_t n, int64_t w);
 int* tc_error_flag(void* scratch);
+// Vt_lo (nullable): second bf16 operand; Y = A_hi (V_hi + V_lo) as two products
 void tc_sketch(cudaStream_t st, const bf16* A, int64_t lda, int64_t m, int64_t n,
-               const bf16* Vt, int64_t ldv, int64_t w, float* Y, int64_t ldy, void* scratch,
-               size_t scratch_bytes);
+               const bf16* Vt, const bf16* Vt_lo, int64_t ldv, int64_t w, float* Y, int64_t ldy,
+               void* scratch, size_t scratch_bytes);
+// V (rows x w float, col-major) -> bf16 hi (and lo = bf16(V - hi) when lo != nullptr)
+void split_bf16(cudaStream_t st, const float* V, int64_t ldv, int64_t rows, int64_t w, bf16* hi,
+                bf16* lo, int64_t ldo);
 void tc_trans(cudaStream_t st, const bf16* A_hi, const bf16* A_lo, int64_t lda, int64_t m,
-              int64_t n, const float* V, int64_t ldv, int64_t w, float* Z, int64_t ldz,
-              bool precise, void* scratch, size_t scratch_bytes);
+              int64_t n, const float* V, int64_t ldv, int64_t w, float* Z, int64_t ldz, int mode,
+              void* scratch, size_t scratch_bytes);
+// X <- bf16(X) (pairs 1) or bf16(X) + bf16(X - bf16(X)) (pairs 2), elementwise, in place
+void round_bf16_inplace(cudaStream_t st, float* X, int64_t ldx, int64_t rows, int64_t cols,
+                        int pairs);
 
 // ------------------------------------------------------------------------------------ misc kernels
 void omega_gen(cudaStream_t st, int64_t n, int64_t col0, int64_t w, uint64_t seed, int dtype,
