@@ -179,6 +179,23 @@ int32_t qb_apass_trans(const qb_dense* A, const void* V, int64_t ldv, int64_t w,
                        void* Z, int64_t ldz, void* ws, size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------------------------
+ * Allocation-free sketch pass (no counterpart in the paper; a deployment convenience).
+ * Y (m x w, column-major, float32, ldy) = A_hi V, V float32 column-major n x w (ldv), A a
+ * bf16 or bf16x2 dense A with ld % 8 == 0 and a 16-byte aligned base, m, n >= 128: the same
+ * tensor-core kernel as qb_apass_sketch, for callers that can neither allocate device memory nor
+ * pass a workspace (a process whose device memory is entirely carved up by its own pool, a plug-in
+ * that must not call the device allocator).  Its scratch is one 16 MiB file-scope device array
+ * that every GPU loading the library reserves until exit; limits: w <= 64 and
+ * align8(n) * w * 2 bytes + 10.5 MiB <= 16 MiB (n up to about 43000 at w = 64).  Larger calls
+ * return QB_ERR_WORKSPACE.  The first call on a device looks the array's address up
+ * (cudaGetSymbolAddress) and should come before any stream capture.  All calls share the array:
+ * calls that overlap on the GPU (other streams, other host threads) race.  The call synchronises
+ * the stream to read the kernel's timeout flag.
+ * ------------------------------------------------------------------------------------------- */
+int32_t qb_apass_sketch_noalloc(const qb_dense* A, const float* V, int64_t ldv, int64_t w,
+                                float* Y, int64_t ldy, void* stream);
+
+/* ---------------------------------------------------------------------------------------------
  * Omega generator (exposed for verification).  Writes Omega rows 0..n-1, global columns
  * col0..col0+w-1 column-major into out (ld >= n), dtype QB_F64 (float64 Box-Muller on 53-bit
  * uniforms), QB_F32 (float32 Box-Muller on 24-bit uniforms) or QB_BF16 (the QB_F32 value

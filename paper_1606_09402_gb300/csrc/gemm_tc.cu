@@ -26,6 +26,8 @@
 
 #include <cuda.h>
 
+#include <mutex>
+
 namespace qb {
 namespace {
 
@@ -664,3 +666,80 @@ void round_bf16_inplace(cudaStream_t st, float* X, int64_t ldx, int64_t rows, in
 }
 
 }  // namespace qb
+
+// ============================================================================ allocation-free pass
+// A variant of the tensor-core sketch pass Y = A_hi V for callers that cannot allocate device
+// memory and cannot hand the library a workspace.  Its scratch (the bf16 copy of V, the stream-K
+// partial tiles and the wait-timeout flag) lives in one file-scope device array that every GPU
+// loading this library reserves until the process exits.
+namespace {
+constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(16) << 20;   // 16 MiB
+constexpr int64_t NOALLOC_MAX_W = 64;
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+namespace qb {
+namespace {
+// Device address of g_noalloc_scratch on the current device, looked up once per device.
+void* noalloc_scratch_address() {
+    static std::mutex mu;
+    static void* addr[64] = {};
+    int dev = 0;
+    QB_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) throw Error{QB_ERR_UNSUPPORTED, "device index"};
+    std::lock_guard<std::mutex> lk(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            record_cuda_error(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+            throw Error{QB_ERR_CUDA, "cudaGetSymbolAddress failed"};
+        }
+        addr[dev] = p;
+    }
+    return addr[dev];
+}
+}  // namespace
+
+// bytes of the shared array a call with these sizes uses
+size_t noalloc_bytes(int64_t n, int64_t w) {
+    const size_t vcopy = size_t(align_up(align_up(n, 8) * w * 2, 256));
+    const size_t part = size_t(MAX_SK_CTAS) * 2 * pick_bn(w, false) * BM * sizeof(float);
+    return vcopy + 256 + part;
+}
+}  // namespace qb
+
+extern "C" int32_t qb_apass_sketch_noalloc(const qb_dense* A, const float* V, int64_t ldv,
+                                           int64_t w, float* Y, int64_t ldy, void* stream) {
+    using namespace qb;
+    if (!A || !V || !Y || A->m < 128 || A->n < 128 || w < 1 || ldv < A->n || ldy < A->m)
+        return QB_ERR_INVALID_ARG;
+    if (A->dtype != QB_BF16 && A->dtype != QB_BF16X2) return QB_ERR_UNSUPPORTED;
+    if (A->ld < A->n || A->ld % 8 != 0 || (reinterpret_cast<uintptr_t>(A->a) & 15) != 0)
+        return QB_ERR_UNSUPPORTED;
+    if (w > NOALLOC_MAX_W || noalloc_bytes(A->n, w) > NOALLOC_SCRATCH_BYTES)
+        return QB_ERR_WORKSPACE;   // beyond the fixed array: use qb_apass_sketch with a workspace
+    try {
+        if (!tc_available()) return QB_ERR_UNSUPPORTED;
+        cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+        char* base = reinterpret_cast<char*>(noalloc_scratch_address());
+        const int64_t ldb = align_up(A->n, 8);
+        bf16* vb = reinterpret_cast<bf16*>(base);
+        char* tcs = base + align_up(ldb * w * 2, 256);
+        const size_t tcs_bytes = NOALLOC_SCRATCH_BYTES - size_t(tcs - base);
+        // the array keeps the previous call's contents: the timeout flag must start at zero
+        QB_CUDA(cudaMemsetAsync(tc_error_flag(tcs), 0, 256, st));
+        split_bf16(st, V, ldv, A->n, w, vb, nullptr, ldb);
+        tc_sketch(st, reinterpret_cast<const bf16*>(A->a), A->ld, A->m, A->n, vb, nullptr, ldb, w,
+                  Y, ldy, tcs, tcs_bytes);
+        int flag = 0;
+        QB_CUDA(cudaMemcpyAsync(&flag, tc_error_flag(tcs), sizeof flag, cudaMemcpyDeviceToHost, st));
+        QB_CUDA(cudaStreamSynchronize(st));
+        return flag ? QB_ERR_TIMEOUT : QB_OK;
+    } catch (const Error& e) {
+        return e.code;
+    } catch (...) {
+        return QB_ERR_CUDA;
+    }
+}
