@@ -179,6 +179,29 @@ int32_t qb_apass_trans(const qb_dense* A, const void* V, int64_t ldv, int64_t w,
                        void* Z, int64_t ldz, void* ws, size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------------------------
+ * Fixed-rank QB map and its adjoint (reverse-mode derivative; the paper has no adjoint, the map
+ * is k columns of randQB / randQB_EI / randQB_FP at P = 0 by Proposition 2).
+ *   forward:  Omega = the Philox columns 0..k-1 of seed (bf16-rounded on the mixed path),
+ *             Y = A Omega, Y = Q R with diag(R) > 0, B = Q^T A.
+ *             Q column-major m x k (ldq), B row-major k x n (ldb), R column-major k x k upper (ldr).
+ *   backward: for L with dL/dQ = G_Q (column-major m x k) and dL/dB = G_B (row-major k x n),
+ *             dL/dA (row-major m x n, ldga) = Q G_B + Ybar Omega^T, where
+ *             Qbar = G_Q + A G_B^T, M = -Qbar^T Q, Ybar = (Qbar + Q (tril(M) + tril(M,-1)^T)) R^-T;
+ *             Y is not stored: Omega is regenerated from the seed.
+ *   prec QB_PREC_FP64 (float64 A and buffers) or QB_PREC_MIXED (bf16 / bf16x2 A, float32
+ *   buffers, tensor-core sketch, round-to-nearest B pass).  1 <= k <= min(m, n).
+ *   Both calls synchronise the stream before returning.
+ * ------------------------------------------------------------------------------------------- */
+size_t qb_fixed_rank_workspace(const qb_dense* A, int64_t k, int32_t prec);
+int32_t qb_fixed_rank_fwd(const qb_dense* A, int64_t k, uint64_t seed, int32_t prec, void* Q,
+                          int64_t ldq, void* B, int64_t ldb, void* R, int64_t ldr, void* ws,
+                          size_t ws_bytes, void* stream);
+int32_t qb_fixed_rank_bwd(const qb_dense* A, int64_t k, uint64_t seed, int32_t prec,
+                          const void* Q, int64_t ldq, const void* R, int64_t ldr, const void* GQ,
+                          int64_t ldgq, const void* GB, int64_t ldgb, void* GA, int64_t ldga,
+                          void* ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------------------------
  * Allocation-free sketch pass (no counterpart in the paper; a deployment convenience).
  * Y (m x w, column-major, float32, ldy) = A_hi V, V float32 column-major n x w (ldv), A a
  * bf16 or bf16x2 dense A with ld % 8 == 0 and a 16-byte aligned base, m, n >= 128: the same

@@ -293,19 +293,19 @@ def randqb_fp(A, tol: float, b: int, seed: int, P: int = 0, l_tilde=None,
 
 
 # ----------------------------------------------------------------------------- fixed-rank map
-def qb_fixed_rank(A, k: int, seed: int):
+def qb_fixed_rank(A, k: int, seed: int, Omega=None):
     """The fixed-rank QB map A -> (Q, B) with Omega fixed: Y = A Omega (n x k Philox columns
-    0..k-1), Y = Q R with diag(R) > 0, B = Q^T A.  Equal in exact arithmetic to k columns of
+    0..k-1 unless ``Omega`` is given), Y = Q R with diag(R) > 0, B = Q^T A.  Equal in exact arithmetic to k columns of
     randQB / randQB_EI / randQB_FP at P = 0 (Proposition 2)."""
     m, n = A.shape
-    Om = _omega(n, 0, k, seed)
+    Om = _omega(n, 0, k, seed) if Omega is None else Omega
     Y = A @ Om
     Q, R = qr_pos(Y)
     B = np.asarray((A.T @ Q).T)
     return Q, B, R
 
 
-def qb_fixed_rank_adjoint(A, k: int, seed: int, GQ: np.ndarray, GB: np.ndarray):
+def qb_fixed_rank_adjoint(A, k: int, seed: int, GQ: np.ndarray, GB: np.ndarray, Omega=None):
     """Gradient of L = <G_Q, Q> + <G_B, B> for the fixed-rank QB map (Omega fixed).
 
     The paper has no adjoint; this is reverse-mode differentiation of the three steps above:
@@ -315,7 +315,7 @@ def qb_fixed_rank_adjoint(A, k: int, seed: int, GQ: np.ndarray, GB: np.ndarray):
       Y = A Omega            ->  Abar += Ybar Omega^T
     """
     m, n = A.shape
-    Om = _omega(n, 0, k, seed)
+    Om = _omega(n, 0, k, seed) if Omega is None else Omega
     Y = A @ Om
     Q, R = qr_pos(Y)
     Qbar = GQ + A @ GB.T

@@ -17,8 +17,8 @@ from dataclasses import dataclass
 from . import _lib
 
 __all__ = ["qb_ei_dense", "qb_fp_dense", "qb_ei_csr", "qb_fp_csr", "qb_omega",
-           "quantize_bf16x2", "qb_apass_sketch", "qb_apass_trans", "QBError", "QBInfo",
-           "launch_count", "status_str"]
+           "quantize_bf16x2", "qb_apass_sketch", "qb_apass_trans", "qb_fixed_rank_fwd",
+           "qb_fixed_rank_bwd", "QBFixedRank", "QBError", "QBInfo", "launch_count", "status_str"]
 
 
 class QBError(RuntimeError):
@@ -296,3 +296,99 @@ def qb_apass_trans(A, V, precise=1, a_lo=None, stream=None):
     """Z = A^T V (one pass over a dense row-major A).  For bf16 hi+lo A: precise=0 uses A_hi and
     bf16(V), 1 the three hi/lo products, 2 (A_hi + A_lo) with bf16(V)."""
     return _apass(True, A, V, precise, a_lo, stream)
+
+
+def _fixed_ws(lib, d, k, prec_code, device):
+    torch = _torch()
+    wsb = lib.qb_fixed_rank_workspace(C.byref(d), k, prec_code)
+    if wsb == 0:
+        raise QBError(_lib.QB_ERR_INVALID_ARG, "qb_fixed_rank_workspace")
+    return torch.empty(wsb, dtype=torch.uint8, device=device)
+
+
+def qb_fixed_rank_fwd(A, k, seed, a_lo=None, stream=None):
+    """Fixed-rank QB map (Omega = Philox columns 0..k-1): returns Q (m x k), B (k x n), R (k x k).
+    float64 A -> float64 path; bf16 A (optionally with a_lo) -> mixed path, float32 outputs."""
+    torch = _torch()
+    lib = _lib.load()
+    _check_dev(A, a_lo)
+    d = _dense_desc(A, a_lo)
+    m, n = A.shape
+    f64 = A.dtype == torch.float64
+    prec = _lib.QB_PREC_FP64 if f64 else _lib.QB_PREC_MIXED
+    dt = torch.float64 if f64 else torch.float32
+    Qt = torch.empty(k, m, dtype=dt, device=A.device)      # Q column-major
+    B = torch.empty(k, n, dtype=dt, device=A.device)
+    Rt = torch.empty(k, k, dtype=dt, device=A.device)      # R column-major
+    ws = _fixed_ws(lib, d, k, prec, A.device)
+    with torch.cuda.device(A.device):
+        rc = lib.qb_fixed_rank_fwd(C.byref(d), k, int(seed) & ((1 << 64) - 1), prec,
+                                   C.c_void_p(Qt.data_ptr()), m, C.c_void_p(B.data_ptr()), n,
+                                   C.c_void_p(Rt.data_ptr()), k, C.c_void_p(ws.data_ptr()),
+                                   ws.numel(), _stream_ptr(stream))
+    if rc < 0:
+        raise QBError(rc, "qb_fixed_rank_fwd")
+    return Qt.T, B, Rt.T
+
+
+def qb_fixed_rank_bwd(A, k, seed, Q, R, GQ, GB, a_lo=None, stream=None):
+    """dL/dA for L with dL/dQ = GQ (m x k), dL/dB = GB (k x n); Q, R from qb_fixed_rank_fwd."""
+    torch = _torch()
+    lib = _lib.load()
+    _check_dev(A, a_lo, Q, R, GQ, GB)
+    d = _dense_desc(A, a_lo)
+    m, n = A.shape
+    f64 = A.dtype == torch.float64
+    prec = _lib.QB_PREC_FP64 if f64 else _lib.QB_PREC_MIXED
+    dt = torch.float64 if f64 else torch.float32
+    Qc = Q.to(dt).T.contiguous()        # column-major Q stored as Q^T
+    Rc = R.to(dt).T.contiguous()
+    GQc = GQ.to(dt).T.contiguous()
+    GBr = GB.to(dt).contiguous()        # row-major k x n
+    GA = torch.empty(m, n, dtype=dt, device=A.device)
+    ws = _fixed_ws(lib, d, k, prec, A.device)
+    with torch.cuda.device(A.device):
+        rc = lib.qb_fixed_rank_bwd(C.byref(d), k, int(seed) & ((1 << 64) - 1), prec,
+                                   C.c_void_p(Qc.data_ptr()), m, C.c_void_p(Rc.data_ptr()), k,
+                                   C.c_void_p(GQc.data_ptr()), m, C.c_void_p(GBr.data_ptr()), n,
+                                   C.c_void_p(GA.data_ptr()), n, C.c_void_p(ws.data_ptr()),
+                                   ws.numel(), _stream_ptr(stream))
+    if rc < 0:
+        raise QBError(rc, "qb_fixed_rank_bwd")
+    return GA
+
+
+def _autograd_function():
+    torch = _torch()
+
+    class QBFixedRank(torch.autograd.Function):
+        """(Q, B) = QBFixedRank.apply(A, k, seed): the fixed-rank QB map with Omega fixed by the
+        seed; backward runs the library's adjoint (Omega regenerated, Y not stored).  The gradient
+        is returned in A's dtype."""
+
+        @staticmethod
+        def forward(ctx, A, k, seed):
+            Q, B, R = qb_fixed_rank_fwd(A, k, seed)
+            ctx.save_for_backward(A, Q, R)
+            ctx.k, ctx.seed = k, seed
+            return Q, B
+
+        @staticmethod
+        def backward(ctx, gQ, gB):
+            A, Q, R = ctx.saved_tensors
+            if gQ is None:
+                gQ = torch.zeros_like(Q)
+            if gB is None:
+                gB = torch.zeros(ctx.k, A.shape[1], dtype=Q.dtype, device=A.device)
+            GA = qb_fixed_rank_bwd(A, ctx.k, ctx.seed, Q, R, gQ, gB)
+            return GA.to(A.dtype), None, None
+
+    return QBFixedRank
+
+
+def __getattr__(name):
+    if name == "QBFixedRank":
+        f = _autograd_function()
+        globals()["QBFixedRank"] = f
+        return f
+    raise AttributeError(name)

@@ -80,6 +80,11 @@ _SIG = {
     "qb_apass_trans": (C.c_int32, [C.POINTER(qb_dense), _P, _I64, _I64, C.c_int32, _P, _I64, _P,
                                    C.c_size_t, _P]),
     "qb_apass_sketch_noalloc": (C.c_int32, [C.POINTER(qb_dense), _P, _I64, _I64, _P, _I64, _P]),
+    "qb_fixed_rank_workspace": (C.c_size_t, [C.POINTER(qb_dense), _I64, C.c_int32]),
+    "qb_fixed_rank_fwd": (C.c_int32, [C.POINTER(qb_dense), _I64, C.c_uint64, C.c_int32, _P, _I64,
+                                      _P, _I64, _P, _I64, _P, C.c_size_t, _P]),
+    "qb_fixed_rank_bwd": (C.c_int32, [C.POINTER(qb_dense), _I64, C.c_uint64, C.c_int32, _P, _I64,
+                                      _P, _I64, _P, _I64, _P, _I64, _P, _I64, _P, C.c_size_t, _P]),
     "qb_quantize_workspace": (C.c_size_t, [_I64, _I64]),
     "qb_quantize_bf16x2": (C.c_int32, [_P, _I64, _I64, _I64, _P, _P, _I64,
                                        C.POINTER(C.c_double), _P, C.c_size_t, _P]),

@@ -101,36 +101,40 @@ struct Ctx {
     }
 
     // One CholeskyQR pass: W = P^T P (float64 or float32-pair accumulation), W = R^T R,
-    // P <- P R^-1, Racc <- R Racc when acc_r.
-    void cholqr(void* P, int64_t ld, int64_t rows, int bi, bool acc_r) {
+    // P <- P R^-1, Racc <- R Racc when acc_r.  sketch: the basis only has to span the same space
+    // (the power scheme), so the Gram is accumulated and factored in float32.
+    void cholqr(void* P, int64_t ld, int64_t rows, int bi, bool acc_r, bool sketch = false) {
+        const bool fast = sketch && !f64;
         gemm(st, true, bi, bi, rows, 1.0, x(P, ld), P, f64, ld, 0.0, W, true, MAXB,
-             f64 ? ACC_D : acc_gram, scr);
-        chol_rinv(st, W, bi, tau, R, Rinv, acc_r ? Racc : nullptr, flags);
+             f64 ? ACC_D : (fast ? ACC_F : acc_gram), scr);
+        chol_rinv(st, W, bi, fast ? 1e-10 : tau, R, Rinv, acc_r ? Racc : nullptr, flags, fast);
         apply_rinv(st, f64, P, ld, rows, bi, Rinv);
     }
     // orth(P): CholeskyQR2 (two passes); Racc accumulates R2 R1 when acc_r.
-    void cholqr2(void* P, int64_t ld, int64_t rows, int bi, bool acc_r) {
-        cholqr(P, ld, rows, bi, acc_r);
-        cholqr(P, ld, rows, bi, acc_r);
+    void cholqr2(void* P, int64_t ld, int64_t rows, int bi, bool acc_r, bool sketch = false) {
+        cholqr(P, ld, rows, bi, acc_r, sketch);
+        cholqr(P, ld, rows, bi, acc_r, sketch);
     }
     // P <- P - Qk (Qk^T P), Qk = first k columns of Q (ld ldq); T: k x bi scratch (ld k)
     void project_out(const void* Q, int64_t ldq, int64_t k, void* P, int64_t ldp, int64_t rows, int bi,
-                     void* T) {
+                     void* T, bool sketch = false) {
         if (k <= 0) return;
-        tn(k, bi, rows, 1.0, Q, ldq, P, ldp, 0.0, T, k, acc_fine);
+        tn(k, bi, rows, 1.0, Q, ldq, P, ldp, 0.0, T, k, sketch ? ACC_F : acc_fine);
         nn(rows, bi, k, -1.0, Q, ldq, T, k, 1.0, P, ldp, acc_proj);
     }
-    // Orthonormalise the rows x w matrix X (column-major) panel by panel: block Gram-Schmidt with
-    // re-orthogonalisation, CholeskyQR2 per panel of width b.  T: w x b scratch.
+    // Orthonormalise the rows x w matrix X (column-major) panel by panel for the power scheme:
+    // block Gram-Schmidt with re-orthogonalisation, CholeskyQR per panel of width b.  Only the
+    // span matters here, so the mixed path works in float32 throughout.  T: w x b scratch.
     void orth_wide(void* X, int64_t ld, int64_t rows, int64_t w, int b, void* T) {
         for (int64_t j0 = 0; j0 < w; j0 += b) {
             const int bj = int(std::min<int64_t>(b, w - j0));
             char* Pj = col(X, ld, j0);
-            project_out(X, ld, j0, Pj, ld, rows, bj, T);
-            cholqr2(Pj, ld, rows, bj, false);
+            project_out(X, ld, j0, Pj, ld, rows, bj, T, true);
+            cholqr2(Pj, ld, rows, bj, false, true);
             if (j0 > 0) {
-                project_out(X, ld, j0, Pj, ld, rows, bj, T);
-                cholqr2(Pj, ld, rows, bj, false);
+                project_out(X, ld, j0, Pj, ld, rows, bj, T, true);
+                if (f64) cholqr2(Pj, ld, rows, bj, false, true);
+                else cholqr(Pj, ld, rows, bj, false, true);
             }
         }
     }
@@ -232,12 +236,13 @@ struct DenseOp : AOp {
     }
     void apply_t(Ctx& c, const void* X, int64_t ldx, int64_t w, void* Y, int64_t ldy,
                  int mode) override {
-        if (!c.f64 && mode >= 2 && d.dtype == QB_BF16X2) {
+        if (!c.f64 && mode >= 2 && bf16_storage()) {
             // The passes that feed the indicator (B_i = Q_i^T A, H = A^T G) run with
             // round-to-nearest float32 sums: tensor-core float32 accumulation is not
             // round-to-nearest and biases ||B_i||^2 low on long reductions.
             trans_precise(c.st, reinterpret_cast<const bf16*>(d.a),
-                          reinterpret_cast<const bf16*>(d.a_lo), d.ld, m, n,
+                          d.dtype == QB_BF16X2 ? reinterpret_cast<const bf16*>(d.a_lo) : nullptr,
+                          d.ld, m, n,
                           reinterpret_cast<const float*>(X), ldx, w, reinterpret_cast<float*>(Y),
                           ldy, c.scr);
             return;
@@ -593,6 +598,94 @@ int32_t run_common(AOp& A, const qb_opts* opts, bool fp, void* Q, int64_t ldq, v
     return status;
 }
 
+// ------------------------------------------------------------------------------------ fixed-rank map
+// The fixed-rank QB map A -> (Q, B) with Omega fixed (Omega = Philox columns 0..k-1): Y = A Omega,
+// Y = Q R (diag R > 0), B = Q^T A.  In exact arithmetic this is k columns of randQB / EI / FP at
+// P = 0 (Proposition 2); the QR is blocked (Gram-Schmidt with re-orthogonalisation over panels of
+// 64, CholeskyQR2 per panel) and keeps R.
+struct FixedBufs {
+    char* Om = nullptr;   // n x k
+    char* T = nullptr;    // k x 64
+    char* M = nullptr;    // k x k
+    char* C = nullptr;    // k x k
+    char* Ri = nullptr;   // k x k
+    char* Qb = nullptr;   // m x k
+    char* Yb = nullptr;   // m x k
+    char* Qt = nullptr;   // k x m
+    char* Gb = nullptr;   // n x k (mixed: rounded copy of G_B^T)
+};
+
+void fixed_reserve(Arena& ar, Ctx& c, DenseOp& A, int64_t k, FixedBufs& f, bool bwd) {
+    const int64_t m = A.m, n = A.n, es = int64_t(c.es);
+    c.alloc(ar, std::max({m, n, k}) * std::max<int64_t>(k, 64));
+    f.Om = ar.get<char>(n * k * es);
+    f.T = ar.get<char>(k * MAXB * es);
+    if (bwd) {
+        f.M = ar.get<char>(k * k * es);
+        f.C = ar.get<char>(k * k * es);
+        f.Ri = ar.get<char>(k * k * es);
+        f.Qb = ar.get<char>(m * k * es);
+        f.Yb = ar.get<char>(m * k * es);
+        f.Qt = ar.get<char>(k * m * es);
+        f.Gb = ar.get<char>(n * k * es);
+    }
+    A.reserve(ar, c, k);
+}
+
+void fixed_fwd(Ctx& c, DenseOp& A, int64_t k, uint64_t seed, FixedBufs& f, void* Q, int64_t ldq,
+               void* B, int64_t ldb, void* R, int64_t ldr) {
+    const int64_t m = A.m, n = A.n;
+    omega_gen(c.st, n, 0, k, seed, c.f64 ? QB_F64 : QB_F32, f.Om, n);
+    A.round_operand(c, f.Om, n, n, k, 1);                       // the map's Omega (bf16 on the mixed path)
+    A.apply(c, f.Om, n, k, Q, ldq, 1);                          // Y = A Omega, in Q
+    QB_CUDA(cudaMemset2DAsync(R, size_t(ldr) * c.es, 0, size_t(k) * c.es, size_t(k), c.st));
+    for (int64_t j0 = 0; j0 < k; j0 += MAXB) {
+        const int bj = int(std::min<int64_t>(MAXB, k - j0));
+        char* Pj = c.col(Q, ldq, j0);
+        char* Rj = c.col(R, ldr, j0);                           // R(0:j0, j0:j0+bj)
+        if (j0 > 0) {
+            for (int pass = 0; pass < 2; ++pass) {              // Gram-Schmidt, then re-orthogonalise
+                c.tn(j0, bj, m, 1.0, Q, ldq, Pj, ldq, 0.0, f.T, j0, c.acc_fine);
+                c.nn(m, bj, j0, -1.0, Q, ldq, f.T, j0, 1.0, Pj, ldq, c.acc_proj);
+                axpy(c.st, c.f64, j0, bj, 1.0, f.T, j0, Rj, ldr);
+            }
+        }
+        set_identity(c.st, c.Racc, bj);
+        c.cholqr2(Pj, ldq, m, bj, true);                         // Q_j R_jj = P_j
+        char* Rjj = reinterpret_cast<char*>(Rj) + size_t(j0) * c.es;
+        from_f64(c.st, c.f64, c.Racc, MAXB, bj, bj, Rjj, ldr);
+    }
+    A.apply_t(c, Q, ldq, k, B, ldb, 3);                         // B = Q^T A
+}
+
+// Abar = Q G_B + Ybar Omega^T with Qbar = G_Q + A G_B^T, M = -Qbar^T Q,
+// Ybar = (Qbar + Q copyltu(M)) R^-T (reverse mode through B = Q^T A, Y = Q R, Y = A Omega).
+void fixed_bwd(Ctx& c, DenseOp& A, int64_t k, uint64_t seed, FixedBufs& f, const void* Q,
+               int64_t ldq, const void* R, int64_t ldr, const void* GQ, int64_t ldgq,
+               const void* GB, int64_t ldgb, void* GA, int64_t ldga) {
+    const int64_t m = A.m, n = A.n;
+    omega_gen(c.st, n, 0, k, seed, c.f64 ? QB_F64 : QB_F32, f.Om, n);
+    A.round_operand(c, f.Om, n, n, k, 1);
+    // Qbar = G_Q + A G_B^T  (G_B row-major k x n = column-major n x k)
+    c.copy_cols_(GB, ldgb, n, k, f.Gb, n);
+    A.round_operand(c, f.Gb, n, n, k, 2);
+    A.apply(c, f.Gb, n, k, f.Qb, m, 2);
+    axpy(c.st, c.f64, m, k, 1.0, GQ, ldgq, f.Qb, m);
+    // M = -Qbar^T Q; C = copyltu(M); Z = Qbar + Q C (in Qbar)
+    c.tn(k, k, m, -1.0, f.Qb, m, Q, ldq, 0.0, f.M, k, c.acc_fine);
+    copyltu(c.st, c.f64, f.M, k, f.C);
+    c.nn(m, k, k, 1.0, Q, ldq, f.C, k, 1.0, f.Qb, m, c.acc_proj);
+    // Ybar = Z R^-T  =  Z (R^-1)^T
+    tri_inv_big(c.st, c.f64, R, ldr, k, f.Ri, k);
+    transpose(c.st, c.f64, f.Ri, k, k, k, f.M, k);              // M <- R^-T
+    c.nn(m, k, k, 1.0, f.Qb, m, f.M, k, 0.0, f.Yb, m, c.acc_proj);
+    // Abar^T (n x m, column-major = Abar row-major) = G_B^T Q^T + Omega Ybar^T
+    transpose(c.st, c.f64, Q, ldq, m, k, f.Qt, k);
+    c.nn(n, m, k, 1.0, GB, ldgb, f.Qt, k, 0.0, GA, ldga, c.acc_proj);
+    transpose(c.st, c.f64, f.Yb, m, m, k, f.Qt, k);
+    c.nn(n, m, k, 1.0, f.Om, n, f.Qt, k, 1.0, GA, ldga, c.acc_proj);
+}
+
 template <class F>
 int32_t guarded(F&& f) {
     try {
@@ -772,6 +865,78 @@ int32_t qb_apass_sketch(const qb_dense* A, const void* V, int64_t ldv, int64_t w
 int32_t qb_apass_trans(const qb_dense* A, const void* V, int64_t ldv, int64_t w, int32_t precise,
                        void* Z, int64_t ldz, void* ws, size_t ws_bytes, void* stream) {
     return apass(A, true, V, ldv, w, precise, Z, ldz, ws, ws_bytes, stream);
+}
+
+static bool valid_fixed(const qb_dense* A, int64_t k, int32_t prec) {
+    qb_opts o{};
+    o.b = 1;
+    o.prec = prec;
+    return (prec == QB_PREC_FP64 || prec == QB_PREC_MIXED) && valid_dense(A, &o) && k >= 1 &&
+           k <= std::min(A->m, A->n);
+}
+
+size_t qb_fixed_rank_workspace(const qb_dense* A, int64_t k, int32_t prec) {
+    if (!valid_fixed(A, k, prec)) return 0;
+    try {
+        Ctx c;
+        setup_ctx(c, prec == QB_PREC_FP64);
+        Arena ar;
+        DenseOp op(*A);
+        FixedBufs f;
+        fixed_reserve(ar, c, op, k, f, true);
+        return ar.used + 4096;
+    } catch (...) {
+        return 0;
+    }
+}
+
+int32_t qb_fixed_rank_fwd(const qb_dense* A, int64_t k, uint64_t seed, int32_t prec, void* Q,
+                          int64_t ldq, void* B, int64_t ldb, void* R, int64_t ldr, void* ws,
+                          size_t ws_bytes, void* stream) {
+    if (!valid_fixed(A, k, prec) || !Q || !B || !R || ldq < A->m || ldb < A->n || ldr < k)
+        return QB_ERR_INVALID_ARG;
+    return guarded([&] {
+        Ctx c;
+        setup_ctx(c, prec == QB_PREC_FP64);
+        c.st = reinterpret_cast<cudaStream_t>(stream);
+        Arena ar;
+        ar.base = reinterpret_cast<char*>(ws);
+        ar.cap = ws_bytes;
+        DenseOp op(*A);
+        FixedBufs f;
+        fixed_reserve(ar, c, op, k, f, false);
+        QB_CUDA(cudaMemsetAsync(c.flags, 0, 4 * sizeof(int), c.st));
+        op.prepare(c);
+        fixed_fwd(c, op, k, seed, f, Q, ldq, B, ldb, R, ldr);
+        if (op.timed_out(c)) return int32_t(QB_ERR_TIMEOUT);
+        QB_CUDA(cudaStreamSynchronize(c.st));
+        return int32_t(QB_OK);
+    });
+}
+
+int32_t qb_fixed_rank_bwd(const qb_dense* A, int64_t k, uint64_t seed, int32_t prec,
+                          const void* Q, int64_t ldq, const void* R, int64_t ldr, const void* GQ,
+                          int64_t ldgq, const void* GB, int64_t ldgb, void* GA, int64_t ldga,
+                          void* ws, size_t ws_bytes, void* stream) {
+    if (!valid_fixed(A, k, prec) || !Q || !R || !GQ || !GB || !GA || ldq < A->m || ldr < k ||
+        ldgq < A->m || ldgb < A->n || ldga < A->n)
+        return QB_ERR_INVALID_ARG;
+    return guarded([&] {
+        Ctx c;
+        setup_ctx(c, prec == QB_PREC_FP64);
+        c.st = reinterpret_cast<cudaStream_t>(stream);
+        Arena ar;
+        ar.base = reinterpret_cast<char*>(ws);
+        ar.cap = ws_bytes;
+        DenseOp op(*A);
+        FixedBufs f;
+        fixed_reserve(ar, c, op, k, f, true);
+        op.prepare(c);
+        fixed_bwd(c, op, k, seed, f, Q, ldq, R, ldr, GQ, ldgq, GB, ldgb, GA, ldga);
+        if (op.timed_out(c)) return int32_t(QB_ERR_TIMEOUT);
+        QB_CUDA(cudaStreamSynchronize(c.st));
+        return int32_t(QB_OK);
+    });
 }
 
 size_t qb_quantize_workspace(int64_t, int64_t) { return (3 * 1024 + 8) * sizeof(double); }

@@ -7,14 +7,13 @@
 // column-major n x m matrix (A Omega is TN, A^T V is NN) and B (row-major k x n) as a
 // column-major n x k matrix (B Omega_i is TN, B^T C is NN).
 //
-// 64 x 64 output tile per 256-thread block, 4 x 4 outputs per thread, K step 16.  Long K is split
+// 128 x 64 output tile per 256-thread block, 8 x 4 outputs per thread, K step 16.  Long K is split
 // across blockIdx.z; split partials go to scratch and are summed in a fixed order (deterministic).
 #include "qb_internal.cuh"
 
 namespace qb {
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16;
 
 // ---------------------------------------------------------------- loaders (value type V)
 template <class V> struct LdF64 {
@@ -73,63 +72,111 @@ struct AccDFv {
     __device__ __forceinline__ double get() const { return double(hi) + double(lo); }
 };
 
+// 128 x 64 output tile, 8 x 4 outputs per thread (rows tx*4.. and 64+tx*4.., columns ty*4..),
+// k step 16, double-buffered shared memory; operands converted to the accumulator's value type V
+// on load.
+constexpr int GM = 128, GN = 64, GK = 16, GPAD = 4;
+
+template <class V> struct Vec4;
+template <> struct Vec4<float> {
+    __device__ __forceinline__ static void load(const float* p, float (&o)[4]) {
+        const float4 v = *reinterpret_cast<const float4*>(p);
+        o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    }
+};
+template <> struct Vec4<double> {
+    __device__ __forceinline__ static void load(const double* p, double (&o)[4]) {
+        const double2 a = *reinterpret_cast<const double2*>(p);
+        const double2 b = *reinterpret_cast<const double2*>(p + 2);
+        o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+    }
+};
+
 template <class LX, class LY, class A, bool XT, class TC>
 __global__ void __launch_bounds__(256)
-k_gemm(int64_t M, int64_t N, int64_t K, int64_t kchunk, LX X, int64_t ldx, LY Y, int64_t ldy,
-       TC* __restrict__ C, int64_t ldc, double alpha, double beta, typename A::P* __restrict__ part) {
+k_gemm2(int64_t M, int64_t N, int64_t K, int64_t kchunk, LX X, int64_t ldx, LY Y, int64_t ldy,
+        TC* __restrict__ C, int64_t ldc, double alpha, double beta, typename A::P* __restrict__ part) {
     using V = typename A::V;
-    __shared__ V Xs[BK][BM + 1];
-    __shared__ V Ys[BK][BN + 1];
+    // k step: 16 for float operands, 8 for double (static shared memory stays below 48 KB)
+    constexpr int KS = sizeof(V) == 8 ? 8 : GK;
+    constexpr int NXQ = GM * KS / 256, NYQ = GN * KS / 256;
+    __shared__ __align__(16) V Xs[2][KS][GM + GPAD];
+    __shared__ __align__(16) V Ys[2][KS][GN + GPAD];
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
-    const int64_t m0 = int64_t(blockIdx.x) * BM, n0 = int64_t(blockIdx.y) * BN;
+    const int64_t m0 = int64_t(blockIdx.x) * GM, n0 = int64_t(blockIdx.y) * GN;
     const int64_t kb = int64_t(blockIdx.z) * kchunk;
     const int64_t ke = min(K, kb + kchunk);
-    A acc[4][4];
+    A acc[8][4];
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
+    for (int r = 0; r < 8; ++r)
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[r][c].init();
-
-    for (int64_t k0 = kb; k0 < ke; k0 += BK) {
+    V rx[NXQ], ry[NYQ];
+    auto gload = [&](int64_t k0) {
 #pragma unroll
-        for (int e = tid; e < BM * BK; e += 256) {
+        for (int q = 0; q < NXQ; ++q) {
+            const int e = tid + 256 * q;
             int i, kk;
-            if (XT) { kk = e % BK; i = e / BK; } else { i = e % BM; kk = e / BM; }
+            if (XT) { kk = e % KS; i = e / KS; } else { i = e % GM; kk = e / GM; }
             const int64_t gi = m0 + i, gk = k0 + kk;
-            V v = V(0);
-            if (gi < M && gk < ke) v = X(XT ? gk + gi * ldx : gi + gk * ldx);
-            Xs[kk][i] = v;
+            rx[q] = (gi < M && gk < ke) ? X(XT ? gk + gi * ldx : gi + gk * ldx) : V(0);
         }
 #pragma unroll
-        for (int e = tid; e < BN * BK; e += 256) {
-            const int kk = e % BK, j = e / BK;
+        for (int q = 0; q < NYQ; ++q) {
+            const int e = tid + 256 * q, kk = e % KS, j = e / KS;
             const int64_t gj = n0 + j, gk = k0 + kk;
-            V v = V(0);
-            if (gj < N && gk < ke) v = Y(gk + gj * ldy);
-            Ys[kk][j] = v;
+            ry[q] = (gj < N && gk < ke) ? Y(gk + gj * ldy) : V(0);
         }
-        __syncthreads();
+    };
+    auto sstore = [&](int b) {
 #pragma unroll
-        for (int kk = 0; kk < BK; ++kk) {
-            V a[4], b[4];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) a[r] = Xs[kk][tx + 16 * r];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) b[c] = Ys[kk][ty + 16 * c];
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) acc[r][c].add(a[r], b[c]);
+        for (int q = 0; q < NXQ; ++q) {
+            const int e = tid + 256 * q;
+            if (XT) Xs[b][e % KS][e / KS] = rx[q];
+            else Xs[b][e / GM][e % GM] = rx[q];
         }
+#pragma unroll
+        for (int q = 0; q < NYQ; ++q) {
+            const int e = tid + 256 * q;
+            Ys[b][e % KS][e / KS] = ry[q];
+        }
+    };
+    int buf = 0;
+    if (kb < ke) {
+        gload(kb);
+        sstore(0);
+    }
+    __syncthreads();
+    for (int64_t k0 = kb; k0 < ke; k0 += KS) {
+        const bool more = k0 + KS < ke;
+        if (more) gload(k0 + KS);
+#pragma unroll
+        for (int kk = 0; kk < KS; ++kk) {
+            V a[8], bv[4];
+            V t0[4], t1[4];
+            Vec4<V>::load(&Xs[buf][kk][tx * 4], t0);
+            Vec4<V>::load(&Xs[buf][kk][64 + tx * 4], t1);
+            Vec4<V>::load(&Ys[buf][kk][ty * 4], bv);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) { a[r] = t0[r]; a[4 + r] = t1[r]; }
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c].add(a[r], bv[c]);
+        }
+        if (more) sstore(buf ^ 1);
         __syncthreads();
+        buf ^= 1;
     }
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < 8; ++r) {
+        const int64_t gi = m0 + (r < 4 ? tx * 4 + r : 64 + tx * 4 + (r - 4));
+        if (gi >= M) continue;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            const int64_t gi = m0 + tx + 16 * r, gj = n0 + ty + 16 * c;
-            if (gi >= M || gj >= N) continue;
+            const int64_t gj = n0 + ty * 4 + c;
+            if (gj >= N) continue;
             if (part) {
                 part[(int64_t(blockIdx.z) * N + gj) * M + gi] = typename A::P(acc[r][c].get());
             } else {
@@ -161,7 +208,7 @@ void launch(cudaStream_t st, bool xt, int64_t M, int64_t N, int64_t K, double al
             int64_t ldx, LY Y, int64_t ldy, double beta, TC* C, int64_t ldc,
             const GemmScratch& scr) {
     if (M <= 0 || N <= 0) return;
-    const int64_t tiles = cdiv(M, BM) * cdiv(N, BN);
+    const int64_t tiles = cdiv(M, GM) * cdiv(N, GN);
     const int64_t target = 2LL * num_sms();
     int64_t splits = 1;
     if (K > 0 && tiles < target) {
@@ -169,17 +216,17 @@ void launch(cudaStream_t st, bool xt, int64_t M, int64_t N, int64_t K, double al
         splits = std::max<int64_t>(1, std::min<int64_t>(splits, MAX_SPLITS));
         while (splits > 1 && size_t(splits) * M * N * sizeof(typename A::P) > scr.part_bytes) --splits;
     }
-    const int64_t kchunk = splits > 1 ? align_up(cdiv(K, splits), BK) : std::max<int64_t>(K, 1);
+    const int64_t kchunk = splits > 1 ? align_up(cdiv(K, splits), GK) : std::max<int64_t>(K, 1);
     splits = K > 0 ? cdiv(K, kchunk) : 1;
-    dim3 grid(unsigned(cdiv(M, BM)), unsigned(cdiv(N, BN)), unsigned(splits));
-    if (cdiv(N, BN) > 65535) throw Error{QB_ERR_INVALID_ARG, "gemm: N too large"};
+    dim3 grid(unsigned(cdiv(M, GM)), unsigned(cdiv(N, GN)), unsigned(splits));
+    if (cdiv(N, GN) > 65535) throw Error{QB_ERR_INVALID_ARG, "gemm: N too large"};
     typename A::P* part = splits > 1 ? reinterpret_cast<typename A::P*>(scr.part) : nullptr;
     if (xt)
-        k_gemm<LX, LY, A, true, TC><<<grid, 256, 0, st>>>(M, N, K, kchunk, X, ldx, Y, ldy, C, ldc,
-                                                           alpha, beta, part);
-    else
-        k_gemm<LX, LY, A, false, TC><<<grid, 256, 0, st>>>(M, N, K, kchunk, X, ldx, Y, ldy, C, ldc,
+        k_gemm2<LX, LY, A, true, TC><<<grid, 256, 0, st>>>(M, N, K, kchunk, X, ldx, Y, ldy, C, ldc,
                                                             alpha, beta, part);
+    else
+        k_gemm2<LX, LY, A, false, TC><<<grid, 256, 0, st>>>(M, N, K, kchunk, X, ldx, Y, ldy, C,
+                                                             ldc, alpha, beta, part);
     QB_LAUNCHED();
     if (part) {
         const int64_t tot = M * N;
@@ -219,8 +266,8 @@ void dispatch_x(cudaStream_t st, bool xt, int64_t M, int64_t N, int64_t K, doubl
 }
 
 // ---------------------------------------------------------------- precise A^T V pass
-// Z (n x w, column-major) = (A_hi + A_lo)^T V, A row-major m x n as two bf16 arrays, V float32
-// column-major m x w.  Float32 FMA with exact operands (A_hi + A_lo and V are float32 values):
+// Z (n x w, column-major) = (A_hi + A_lo)^T V, A row-major m x n as two bf16 arrays (A_lo may be
+// null: a plain bf16 A), V float32 column-major m x w.  Float32 FMA with exact operands (A_hi + A_lo and V are float32 values):
 // every product and partial sum is rounded to nearest, so the result carries no systematic drift
 // (the pass that forms B_i = Q_i^T A and H = A^T G feeds the indicator of Theorem 1).
 // 128 x 64 output tile, 8 x 4 per thread, k step 16, double-buffered shared memory.
@@ -249,7 +296,8 @@ k_trans_prec(int64_t m, int64_t n, int64_t w, int64_t kchunk, const bf16* __rest
             float v = 0.f;
             if (gk < ke && gn < n) {
                 const int64_t o = gk * lda + gn;
-                v = __bfloat162float(Ahi[o]) + __bfloat162float(Alo[o]);
+                v = __bfloat162float(Ahi[o]);
+                if (Alo) v += __bfloat162float(Alo[o]);
             }
             ra[q] = v;
         }
@@ -337,9 +385,12 @@ void gemm(cudaStream_t st, bool xt, int64_t M, int64_t N, int64_t K, double alph
             dispatch_x<AccDFv, float>(st, xt, M, N, K, alpha, X, Y, ldy, beta,
                                       reinterpret_cast<float*>(C), ldc, scr);
     } else {
-        if (c_f64) throw Error{QB_ERR_UNSUPPORTED, "ACC_F writes f32"};
-        dispatch_x<AccFv, float>(st, xt, M, N, K, alpha, X, Y, ldy, beta,
-                                 reinterpret_cast<float*>(C), ldc, scr);
+        if (c_f64)
+            dispatch_x<AccFv, float>(st, xt, M, N, K, alpha, X, Y, ldy, beta,
+                                     reinterpret_cast<double*>(C), ldc, scr);
+        else
+            dispatch_x<AccFv, float>(st, xt, M, N, K, alpha, X, Y, ldy, beta,
+                                     reinterpret_cast<float*>(C), ldc, scr);
     }
 }
 

@@ -249,3 +249,112 @@ void quantize_bf16x2(cudaStream_t st, const double* src, int64_t m, int64_t n, i
 }
 
 }  // namespace qb
+
+// ============================================================================ small dense helpers
+namespace qb {
+namespace {
+template <class T>
+__global__ void k_transpose(const T* __restrict__ X, int64_t ldx, int64_t rows, int64_t cols,
+                            T* __restrict__ Y, int64_t ldy) {
+    __shared__ T tile[32][33];
+    const int64_t r0 = int64_t(blockIdx.x) * 32, c0 = int64_t(blockIdx.y) * 32;
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int64_t r = r0 + threadIdx.x, c = c0 + k;
+        if (r < rows && c < cols) tile[k][threadIdx.x] = X[r + c * ldx];
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int64_t c = c0 + threadIdx.x, r = r0 + k;
+        if (r < rows && c < cols) Y[c + r * ldy] = tile[threadIdx.x][k];
+    }
+}
+
+// C = tril(M) + tril(M, -1)^T, k x k column-major (ld k)
+template <class T>
+__global__ void k_copyltu(const T* __restrict__ M, int64_t k, T* __restrict__ C) {
+    const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (idx >= k * k) return;
+    const int64_t i = idx % k, j = idx / k;
+    C[i + j * k] = i >= j ? M[i + j * k] : M[j + i * k];
+}
+
+// Y[i + j ldy] = (T) X[i + j ldx] from float64
+template <class T>
+__global__ void k_from_f64(const double* __restrict__ X, int64_t ldx, int64_t rows, int64_t cols,
+                           T* __restrict__ Y, int64_t ldy) {
+    const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (idx >= rows * cols) return;
+    const int64_t i = idx % rows, j = idx / rows;
+    Y[i + j * ldy] = T(X[i + j * ldx]);
+}
+
+template <class T>
+__global__ void k_axpy(int64_t rows, int64_t cols, T alpha, const T* __restrict__ X, int64_t ldx,
+                       T* __restrict__ Y, int64_t ldy) {
+    const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (idx >= rows * cols) return;
+    const int64_t i = idx % rows, j = idx / rows;
+    Y[i + j * ldy] += alpha * X[i + j * ldx];
+}
+
+// Inverse of an upper-triangular k x k R (column-major, ld), one column of X per thread, R read
+// through the cache; any k.
+template <class T>
+__global__ void k_tri_inv_big(const T* __restrict__ R, int64_t ldr, int64_t k, T* __restrict__ X,
+                              int64_t ldx) {
+    const int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (c >= k) return;
+    for (int64_t i = c + 1; i < k; ++i) X[i + c * ldx] = T(0);
+    X[c + c * ldx] = T(1) / R[c + c * ldr];
+    for (int64_t i = c - 1; i >= 0; --i) {
+        T s = T(0);
+        for (int64_t l = i + 1; l <= c; ++l) s = fma(R[i + l * ldr], X[l + c * ldx], s);
+        X[i + c * ldx] = -s / R[i + i * ldr];
+    }
+}
+}  // namespace
+
+void transpose(cudaStream_t st, bool f64, const void* X, int64_t ldx, int64_t rows, int64_t cols,
+               void* Y, int64_t ldy) {
+    if (rows <= 0 || cols <= 0) return;
+    dim3 g(unsigned(cdiv(rows, 32)), unsigned(cdiv(cols, 32))), b(32, 8);
+    if (f64) k_transpose<double><<<g, b, 0, st>>>(reinterpret_cast<const double*>(X), ldx, rows, cols, reinterpret_cast<double*>(Y), ldy);
+    else k_transpose<float><<<g, b, 0, st>>>(reinterpret_cast<const float*>(X), ldx, rows, cols, reinterpret_cast<float*>(Y), ldy);
+    QB_LAUNCHED();
+}
+
+void copyltu(cudaStream_t st, bool f64, const void* M, int64_t k, void* C) {
+    if (k <= 0) return;
+    const unsigned g = unsigned(cdiv(k * k, 256));
+    if (f64) k_copyltu<double><<<g, 256, 0, st>>>(reinterpret_cast<const double*>(M), k, reinterpret_cast<double*>(C));
+    else k_copyltu<float><<<g, 256, 0, st>>>(reinterpret_cast<const float*>(M), k, reinterpret_cast<float*>(C));
+    QB_LAUNCHED();
+}
+
+void from_f64(cudaStream_t st, bool f64, const double* X, int64_t ldx, int64_t rows, int64_t cols,
+              void* Y, int64_t ldy) {
+    if (rows <= 0 || cols <= 0) return;
+    const unsigned g = unsigned(cdiv(rows * cols, 256));
+    if (f64) k_from_f64<double><<<g, 256, 0, st>>>(X, ldx, rows, cols, reinterpret_cast<double*>(Y), ldy);
+    else k_from_f64<float><<<g, 256, 0, st>>>(X, ldx, rows, cols, reinterpret_cast<float*>(Y), ldy);
+    QB_LAUNCHED();
+}
+
+void axpy(cudaStream_t st, bool f64, int64_t rows, int64_t cols, double alpha, const void* X,
+          int64_t ldx, void* Y, int64_t ldy) {
+    if (rows <= 0 || cols <= 0) return;
+    const unsigned g = unsigned(cdiv(rows * cols, 256));
+    if (f64) k_axpy<double><<<g, 256, 0, st>>>(rows, cols, alpha, reinterpret_cast<const double*>(X), ldx, reinterpret_cast<double*>(Y), ldy);
+    else k_axpy<float><<<g, 256, 0, st>>>(rows, cols, float(alpha), reinterpret_cast<const float*>(X), ldx, reinterpret_cast<float*>(Y), ldy);
+    QB_LAUNCHED();
+}
+
+void tri_inv_big(cudaStream_t st, bool f64, const void* R, int64_t ldr, int64_t k, void* X,
+                 int64_t ldx) {
+    if (k <= 0) return;
+    const unsigned g = unsigned(cdiv(k, 64));
+    if (f64) k_tri_inv_big<double><<<g, 64, 0, st>>>(reinterpret_cast<const double*>(R), ldr, k, reinterpret_cast<double*>(X), ldx);
+    else k_tri_inv_big<float><<<g, 64, 0, st>>>(reinterpret_cast<const float*>(R), ldr, k, reinterpret_cast<float*>(X), ldx);
+    QB_LAUNCHED();
+}
+}  // namespace qb

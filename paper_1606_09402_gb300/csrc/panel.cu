@@ -12,32 +12,34 @@ constexpr int LDS = MAXB + 1;
 // Breakdown: a pivot d <= tau_rel * max_diag(W) (or NaN) is replaced by tau_rel * max_diag (or
 // the smallest normal double) and flags[1] is raised; the column it produces has norm <= 1.
 // Dynamic shared memory: two MAXB x LDS float64 arrays (S holds W and becomes R in place).
+template <class T>
 __global__ void __launch_bounds__(256)
 k_chol(const double* __restrict__ W, int bi, double tau_rel, double* __restrict__ Rout,
        double* __restrict__ Rinv, double* __restrict__ Racc, int* flags) {
     extern __shared__ double smem[];
-    double (*S)[LDS] = reinterpret_cast<double (*)[LDS]>(smem);
-    double (*X)[LDS] = reinterpret_cast<double (*)[LDS]>(smem + MAXB * LDS);
-    __shared__ double piv;
-    __shared__ double dmax;
+    T (*S)[LDS] = reinterpret_cast<T (*)[LDS]>(smem);
+    T (*X)[LDS] = reinterpret_cast<T (*)[LDS]>(reinterpret_cast<T*>(smem) + MAXB * LDS);
+    __shared__ T piv;
+    __shared__ T dmax;
     const int tid = threadIdx.x;
     for (int e = tid; e < MAXB * MAXB; e += blockDim.x) {
         const int i = e % MAXB, j = e / MAXB;
-        S[i][j] = (i < bi && j < bi && i <= j) ? W[i + j * MAXB] : 0.0;
-        X[i][j] = 0.0;
+        S[i][j] = (i < bi && j < bi && i <= j) ? T(W[i + j * MAXB]) : T(0);
+        X[i][j] = T(0);
     }
     __syncthreads();
     if (tid == 0) {
-        double m = 0.0;
-        for (int i = 0; i < bi; ++i) m = fmax(m, S[i][i]);
+        T m = T(0);
+        for (int i = 0; i < bi; ++i) m = S[i][i] > m ? S[i][i] : m;
         dmax = m;
     }
     __syncthreads();
-    const double floor_piv = fmax(tau_rel * dmax, 2.2250738585072014e-308);
+    const T tiny = sizeof(T) == 8 ? T(2.2250738585072014e-308) : T(1.1754943508222875e-38);
+    const T floor_piv = T(tau_rel) * dmax > tiny ? T(tau_rel) * dmax : tiny;
     for (int j = 0; j < bi; ++j) {
         if (tid == 0) {
-            double d = S[j][j];
-            if (!(d > tau_rel * dmax)) {
+            T d = S[j][j];
+            if (!(d > T(tau_rel) * dmax)) {
                 d = floor_piv;
                 atomicOr(flags + 1, 1);
             }
@@ -57,9 +59,9 @@ k_chol(const double* __restrict__ W, int bi, double tau_rel, double* __restrict_
     }
     // inverse of the upper-triangular R, one column per thread (back substitution)
     for (int c = tid; c < bi; c += blockDim.x) {
-        X[c][c] = 1.0 / S[c][c];
+        X[c][c] = T(1) / S[c][c];
         for (int i = c - 1; i >= 0; --i) {
-            double s = 0.0;
+            T s = T(0);
             for (int l = i + 1; l <= c; ++l) s = fma(S[i][l], X[l][c], s);
             X[i][c] = -s / S[i][i];
         }
@@ -67,23 +69,23 @@ k_chol(const double* __restrict__ W, int bi, double tau_rel, double* __restrict_
     __syncthreads();
     for (int e = tid; e < MAXB * MAXB; e += blockDim.x) {
         const int i = e % MAXB, j = e / MAXB;
-        if (Rout) Rout[i + j * MAXB] = i <= j ? S[i][j] : 0.0;
-        if (Rinv) Rinv[i + j * MAXB] = X[i][j];
+        if (Rout) Rout[i + j * MAXB] = i <= j ? double(S[i][j]) : 0.0;
+        if (Rinv) Rinv[i + j * MAXB] = double(X[i][j]);
     }
     if (Racc) {
         // Racc <- R * Racc (both upper triangular); X reused for the old Racc
         __syncthreads();
         for (int e = tid; e < MAXB * MAXB; e += blockDim.x) {
             const int i = e % MAXB, j = e / MAXB;
-            X[i][j] = Racc[i + j * MAXB];
+            X[i][j] = T(Racc[i + j * MAXB]);
         }
         __syncthreads();
         for (int e = tid; e < MAXB * MAXB; e += blockDim.x) {
             const int i = e % MAXB, j = e / MAXB;
-            double s = 0.0;
+            T s = T(0);
             if (i < bi && j < bi)
                 for (int l = i; l <= j; ++l) s = fma(S[i][l], X[l][j], s);
-            Racc[i + j * MAXB] = s;
+            Racc[i + j * MAXB] = double(s);
         }
     }
 }
@@ -200,9 +202,14 @@ void allow_smem(K kernel, size_t bytes) {
 }
 
 void chol_rinv(cudaStream_t st, const double* W, int bi, double tau_rel, double* R, double* Rinv,
-               double* R_acc, int* flags) {
-    allow_smem(k_chol, CHOL_SMEM);
-    k_chol<<<1, 256, CHOL_SMEM, st>>>(W, bi, tau_rel, R, Rinv, R_acc, flags);
+               double* R_acc, int* flags, bool f32) {
+    if (f32) {
+        allow_smem(k_chol<float>, CHOL_SMEM);
+        k_chol<float><<<1, 256, CHOL_SMEM, st>>>(W, bi, tau_rel, R, Rinv, R_acc, flags);
+    } else {
+        allow_smem(k_chol<double>, CHOL_SMEM);
+        k_chol<double><<<1, 256, CHOL_SMEM, st>>>(W, bi, tau_rel, R, Rinv, R_acc, flags);
+    }
     QB_LAUNCHED();
 }
 

@@ -137,14 +137,30 @@ void quantize_bf16x2(cudaStream_t st, const double* src, int64_t m, int64_t n, i
 void copy_cols(cudaStream_t st, bool f64, const void* X, int64_t ldx, int64_t rows,
                int64_t cols, void* Y, int64_t ldy);
 void fill_zero(cudaStream_t st, void* p, size_t bytes);
+// Y (cols x rows) = X^T, column-major blocks
+void transpose(cudaStream_t st, bool f64, const void* X, int64_t ldx, int64_t rows, int64_t cols,
+               void* Y, int64_t ldy);
+// C = tril(M) + tril(M, -1)^T (k x k, ld k)
+void copyltu(cudaStream_t st, bool f64, const void* M, int64_t k, void* C);
+// Y = X converted from float64 (column-major blocks)
+void from_f64(cudaStream_t st, bool f64, const double* X, int64_t ldx, int64_t rows, int64_t cols,
+              void* Y, int64_t ldy);
+// Y += alpha X (column-major blocks)
+void axpy(cudaStream_t st, bool f64, int64_t rows, int64_t cols, double alpha, const void* X,
+          int64_t ldx, void* Y, int64_t ldy);
+// X = R^-1 for upper-triangular k x k R (any k)
+void tri_inv_big(cudaStream_t st, bool f64, const void* R, int64_t ldr, int64_t k, void* X,
+                 int64_t ldx);
 
 // ------------------------------------------------------------------------------------ panel
 // Small b x b float64 matrices are column-major with ld = 64.
 constexpr int MAXB = 64;
 // W (bi x bi Gram, col-major ld 64) -> R (upper, W = R^T R) and Rinv; breakdown clamps the pivot
 // and sets flags[1]; R_acc <- R * R_acc if R_acc != nullptr (R_acc starts as identity).
+// f32: factor in float32 (the orthonormalisation inside the power scheme, where only the span
+// matters); otherwise float64.
 void chol_rinv(cudaStream_t st, const double* W, int bi, double tau_rel, double* R,
-               double* Rinv, double* R_acc, int* flags);
+               double* Rinv, double* R_acc, int* flags, bool f32 = false);
 void set_identity(cudaStream_t st, double* R, int bi);
 // R_out = Rinv of an upper-triangular R (bi x bi)
 void tri_inv(cudaStream_t st, const double* R, int bi, double* Rinv);
