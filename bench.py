@@ -188,6 +188,68 @@ def cpu_baseline(A_rows, m_full):
                       f"(rank {r.rank}), {t:.1f} s measured, scaled by m/{m_s} = {scale:g}"}
 
 
+def run_batched(torch, qb, dev, stream):
+    """The batched workload: 256 float32 matrices (seed 1606), b = 16, P = 0; one call factorises
+    all of them (conditional CUDA graph).  Spectra are truncated at j <= 512 (the tail beyond
+    carries < 3e-9 of ||A||^2)."""
+    import numpy as np
+
+    import synth
+    specs = synth.batched_specs(256, 1606)
+    mats = []
+    for s in specs:
+        r = min(s.m, s.n, 512)
+        mats.append(synth.dense_from_spectrum_torch(s.m, s.n, synth.sigma_pow(r, 2.0, s.scale),
+                                                    s.seed, dev, dtype=torch.float32))
+    tols = [s.tol for s in specs]
+    outs = [(torch.empty(min(s.m, s.n), s.m, device=dev), torch.empty(min(s.m, s.n), s.n, device=dev))
+            for s in specs]
+    res = qb.qb_ei_batched(mats, tols, seed=9402, outs=outs)        # warm-up (and result)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(3):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = qb.qb_ei_batched(mats, tols, seed=9402, outs=outs)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    ranks = [r[2].rank for r in res]
+    ok = sum(1 for r in res if r[2].converged)
+    a_bytes = sum(4.0 * s.m * s.n for s in specs)
+    # true error of a sample of results (float64, verification only)
+    worst = 0.0
+    for t in range(0, 256, 32):
+        A = mats[t].double()
+        Q, B, _ = res[t]
+        worst = max(worst, float(torch.linalg.norm(A - Q.double() @ B.double()) / torch.linalg.norm(A)) / tols[t])
+    return {"matrices": 256, "time_s": statistics.median(times), "converged": ok,
+            "rank_min": int(min(ranks)), "rank_max": int(max(ranks)),
+            "blocks_total": int(sum(r[2].blocks for r in res)),
+            "a_bytes_per_sweep": a_bytes, "worst_err_over_tol_sampled": worst,
+            "note": "one graph launch per call; includes graph build/instantiate"}
+
+
+def run_adjoint(torch, qb, dev, stream):
+    """Fixed-rank k = 256 QB of an 8192 x 8192 bf16 A (sigma_j = 1/j): forward and backward."""
+    import numpy as np
+
+    import synth
+    m = n = 8192
+    k = 256
+    A = synth.dense_from_spectrum_torch(m, n, 1.0 / np.arange(1, n + 1), 1606, dev,
+                                        dtype=torch.float32).to(torch.bfloat16)
+    GQ, GB = synth.cotangents(m, n, k, seed=5)
+    GQ = torch.tensor(GQ, dtype=torch.float32, device=dev)
+    GB = torch.tensor(GB, dtype=torch.float32, device=dev)
+    Q, B, R = qb.qb_fixed_rank_fwd(A, k, 9)
+    qb.qb_fixed_rank_bwd(A, k, 9, Q, R, GQ, GB)
+    tf = event_time(torch, lambda: qb.qb_fixed_rank_fwd(A, k, 9), 3, stream)
+    tb = event_time(torch, lambda: qb.qb_fixed_rank_bwd(A, k, 9, Q, R, GQ, GB), 3, stream)
+    return {"m": m, "n": n, "k": k, "forward_s": tf, "backward_s": tb}
+
+
 # ----------------------------------------------------------------------------- reference arm
 def run_reference(args, ws, rank):
     if rank != 0:
@@ -277,10 +339,15 @@ def run_ours(args, ws, rank, local):
         t_step = timed(torch, step, args.steps, args.warmup, ws, stream)
     launches = qb.launch_count() - l0
     Q, Bf, info = out["r"]
+    # one extra, untimed factorisation with phase events (QB_FLAG_PROFILE) for the breakdown
+    qb.qb_fp_dense(hi, TOL, B, P=P, seed=SEED_OMEGA, a_lo=lo, src_norm2=normA2, prec="mixed",
+                   rank_cap=RANK_CAP, l_tilde=L_TILDE, out=(Qt, Bm), workspace=out["ws"], flags=2)
+    phases = qb.profile_last()
     if args.steps_only:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": t_step, "unit": "s", "rank": info.rank,
-                              "launches_per_step": launches / (args.steps + args.warmup)}))
+                              "launches_per_step": launches / (args.steps + args.warmup),
+                              "phases_ms": phases}))
         return
     # timed-region launches only: the warmup steps launched the same count per step
     per_step = launches / (args.steps + args.warmup)
@@ -343,6 +410,11 @@ def run_ours(args, ws, rank, local):
     except Exception as e:  # pragma: no cover
         ei = {"error": str(e)}
 
+    # ---- batched: 256 float32 matrices, m, n ~ U[256, 4096], sigma_j = s j^-2, tol in {1e-2, 1e-3}
+    batched = None if args.quick else run_batched(torch, qb, dev, stream)
+    # ---- fixed-rank adjoint: 8192 x 8192 bf16, k = 256, sigma_j = 1/j
+    adjoint = None if args.quick else run_adjoint(torch, qb, dev, stream)
+
     # ---- end to end through the public API with host buffers (pinned)
     hi_h = hi.cpu().pin_memory()
     lo_h = lo.cpu().pin_memory()
@@ -392,8 +464,11 @@ def run_ours(args, ws, rank, local):
                   "trans_narrow_frac": gbs_nar_tr / hbm, "w": B,
                   "sketch_wide_ms": t_sk_wide * 1e3, "trans_wide_precise_ms": t_tr_wide * 1e3,
                   "peak_source": pk_src},
+        "phases_ms": phases,
         "fp64_randqb_fp": fp64,
         "mixed_randqb_ei": ei,
+        "batched_ei_256": batched,
+        "fixed_rank_adjoint_8192": adjoint,
         "e2e": {"value": t_e2e, "unit": "s", "h2d_bytes_per_step": int(2 * hi.numel() * 2),
                 "d2h_bytes_per_step": int(d2h["b"])},
         "gpu_launches": gpu_launches,

@@ -107,6 +107,9 @@ typedef struct {
 /* qb_opts.flags: run the passes over a bf16 A on the SIMT kernels instead of the tensor cores
  * (float32 FMA on the same bf16 data; slower, used to cross-check the tensor-core kernels). */
 #define QB_FLAG_SIMT_APASS 1
+/* qb_opts.flags: record CUDA events around the phases of the call (adds a synchronisation at the
+ * end); read the device milliseconds with qb_profile_last(). */
+#define QB_FLAG_PROFILE 2
 
 typedef struct {
     int64_t rank;        /* columns of Q / rows of B that are valid */
@@ -128,6 +131,13 @@ const char* qb_last_cuda_error(void);
 
 /* Total kernels launched by the library in this process (all calls). */
 int64_t qb_launch_count(void);
+
+/* Device milliseconds per phase of the last call made with QB_FLAG_PROFILE, in this order:
+ * 0 Omega generation, 1 sketch passes over A (A X), 2 transposed passes over A (A^T X),
+ * 3 power-scheme orthonormalisation, 4 projections against Q and B, 5 CholeskyQR2 of the new
+ * block (with its re-orthogonalisation), 6 randQB_FP's B_i formula, 7 indicator and host
+ * round trip.  Writes min(n, phases) values; returns the number of phases. */
+int32_t qb_profile_last(double* ms, int32_t n);
 
 /* ---------------------------------------------------------------------------------------------
  * Dense fixed-precision QB.  algo: 0 = randQB_EI (Algorithm 2), 1 = randQB_FP (Algorithm 4).
@@ -177,6 +187,26 @@ int32_t qb_apass_sketch(const qb_dense* A, const void* V, int64_t ldv, int64_t w
                         int64_t ldy, void* ws, size_t ws_bytes, void* stream);
 int32_t qb_apass_trans(const qb_dense* A, const void* V, int64_t ldv, int64_t w, int32_t precise,
                        void* Z, int64_t ldz, void* ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * Batched randQB_EI (Algorithm 2 with P = 0 and the row-by-row stop) over `count` independent
+ * float32 matrices of any shapes, each with its own tolerance tols[t] (relative when
+ * opts->relative) and Omega seed opts->seed + t.  Every stage of one iteration is a single launch
+ * over all matrices still running; the iteration is captured in a CUDA graph whose conditional
+ * WHILE node repeats it until every matrix has converged or reached its rank cap (matrices that
+ * finish early drop out of the work lists).  Requirements: opts->b == 16, opts->P == 0,
+ * opts->prec == QB_PREC_MIXED, As[t].dtype == QB_F32.  As, tols, Qs, ldqs, Bs, ldbs, infos are
+ * HOST arrays of `count` entries (the matrices they point to live on the device): Q_t is
+ * column-major m_t x cap_t (ldqs[t] >= m_t), B_t row-major cap_t x n_t (ldbs[t] >= n_t),
+ * cap_t = min(m_t, n_t, rank_cap).  Q and B are float32; the indicator is float64 and the stop
+ * test keeps the 2 u ||A_t||^2 margin of the mixed path.  infos[t] receives each result; the
+ * return value is the worst status over the batch.  Synchronises the stream.
+ * ------------------------------------------------------------------------------------------- */
+size_t qb_ei_batched_workspace(int32_t count, const qb_dense* As, const qb_opts* opts);
+int32_t qb_ei_batched(int32_t count, const qb_dense* As, const double* tols,
+                      const qb_opts* opts, void* const* Qs, const int64_t* ldqs,
+                      void* const* Bs, const int64_t* ldbs, void* ws, size_t ws_bytes,
+                      qb_info* infos, void* stream);
 
 /* ---------------------------------------------------------------------------------------------
  * Fixed-rank QB map and its adjoint (reverse-mode derivative; the paper has no adjoint, the map

@@ -18,7 +18,8 @@ from . import _lib
 
 __all__ = ["qb_ei_dense", "qb_fp_dense", "qb_ei_csr", "qb_fp_csr", "qb_omega",
            "quantize_bf16x2", "qb_apass_sketch", "qb_apass_trans", "qb_fixed_rank_fwd",
-           "qb_fixed_rank_bwd", "QBFixedRank", "QBError", "QBInfo", "launch_count", "status_str"]
+           "qb_fixed_rank_bwd", "QBFixedRank", "qb_ei_batched", "QBError", "QBInfo",
+           "launch_count", "status_str"]
 
 
 class QBError(RuntimeError):
@@ -55,6 +56,13 @@ def status_str(code: int) -> str:
 
 def launch_count() -> int:
     return int(_lib.load().qb_launch_count())
+
+
+def profile_last() -> dict:
+    """Per-phase device milliseconds of the last call made with flags=QB_FLAG_PROFILE (2)."""
+    buf = (C.c_double * len(_lib.PHASES))()
+    _lib.load().qb_profile_last(buf, len(_lib.PHASES))
+    return dict(zip(_lib.PHASES, (float(x) for x in buf)))
 
 
 def _torch():
@@ -356,6 +364,57 @@ def qb_fixed_rank_bwd(A, k, seed, Q, R, GQ, GB, a_lo=None, stream=None):
     if rc < 0:
         raise QBError(rc, "qb_fixed_rank_bwd")
     return GA
+
+
+def qb_ei_batched(As, tols, seed=0, rank_cap=None, relative=True, row_by_row=True, stream=None,
+                  outs=None, workspace=None):
+    """Batched randQB_EI (b = 16, P = 0) over a list of float32 row-major CUDA matrices with
+    per-matrix tolerances; returns a list of (Q_t, B_t, QBInfo).  Matrix t uses seed + t."""
+    torch = _torch()
+    lib = _lib.load()
+    count = len(As)
+    descs = (_lib.qb_dense * count)()
+    for t, A in enumerate(As):
+        _check_dev(A)
+        assert A.dtype == torch.float32 and A.stride(1) == 1
+        descs[t] = _dense_desc(A)
+    tol_arr = (C.c_double * count)(*[float(x) for x in tols])
+    o = _opts(0.0, 16, 0, seed, relative, rank_cap, None, row_by_row, "mixed")
+    if outs is None:
+        outs = []
+        for A in As:
+            m, n = A.shape
+            cap = min(m, n) if not rank_cap else min(m, n, int(rank_cap))
+            outs.append((torch.empty(cap, m, dtype=torch.float32, device=A.device),
+                         torch.empty(cap, n, dtype=torch.float32, device=A.device)))
+    qp = (C.c_void_p * count)(*[q.data_ptr() for q, _ in outs])
+    bp = (C.c_void_p * count)(*[b.data_ptr() for _, b in outs])
+    ldq = (C.c_int64 * count)(*[q.stride(0) for q, _ in outs])
+    ldb = (C.c_int64 * count)(*[b.stride(0) for _, b in outs])
+    wsb = lib.qb_ei_batched_workspace(count, descs, C.byref(o))
+    if wsb == 0:
+        raise QBError(_lib.QB_ERR_INVALID_ARG, "qb_ei_batched_workspace")
+    ws = workspace if workspace is not None and workspace.numel() >= wsb else \
+        torch.empty(wsb, dtype=torch.uint8, device=As[0].device)
+    infos = (_lib.qb_info * count)()
+    with torch.cuda.device(As[0].device):
+        rc = lib.qb_ei_batched(count, descs, tol_arr, C.byref(o), qp, ldq, bp, ldb,
+                               C.c_void_p(ws.data_ptr()), ws.numel(), infos, _stream_ptr(stream))
+    if rc < 0:
+        raise QBError(rc, "qb_ei_batched")
+    res = []
+    for t in range(count):
+        inf = infos[t]
+        st = _lib.QB_OK
+        if inf.status_bits & _lib.QB_BIT_NOT_CONVERGED:
+            st = _lib.QB_NOT_CONVERGED
+        elif inf.status_bits & _lib.QB_BIT_TOL_FLOOR:
+            st = _lib.QB_WARN_TOL_FLOOR
+        info = _info(st, inf)
+        k = info.rank
+        q, b = outs[t]
+        res.append((q[:k].T, b[:k], info))
+    return res
 
 
 def _autograd_function():

@@ -26,6 +26,9 @@ QB_BIT_TOL_FLOOR = 2
 QB_BIT_NOT_CONVERGED = 4
 
 QB_F64, QB_F32, QB_BF16, QB_BF16X2 = 0, 1, 2, 3
+QB_FLAG_SIMT_APASS, QB_FLAG_PROFILE = 1, 2
+PHASES = ("omega", "sketch", "trans", "power_orth", "projections", "cholqr2", "fp_b_formula",
+          "indicator")
 QB_PREC_FP64, QB_PREC_MIXED = 0, 1
 
 
@@ -63,6 +66,7 @@ _SIG = {
     "qb_status_str": (C.c_char_p, [C.c_int32]),
     "qb_last_cuda_error": (C.c_char_p, []),
     "qb_launch_count": (C.c_int64, []),
+    "qb_profile_last": (C.c_int32, [C.POINTER(C.c_double), C.c_int32]),
     "qb_dense_workspace": (C.c_size_t, [C.POINTER(qb_dense), C.POINTER(qb_opts), C.c_int32]),
     "qb_ei_dense": (C.c_int32, [C.POINTER(qb_dense), C.POINTER(qb_opts), _P, _I64, _P, _I64, _P,
                                 C.c_size_t, C.POINTER(qb_info), _P]),
@@ -85,6 +89,11 @@ _SIG = {
                                       _P, _I64, _P, _I64, _P, C.c_size_t, _P]),
     "qb_fixed_rank_bwd": (C.c_int32, [C.POINTER(qb_dense), _I64, C.c_uint64, C.c_int32, _P, _I64,
                                       _P, _I64, _P, _I64, _P, _I64, _P, _I64, _P, C.c_size_t, _P]),
+    "qb_ei_batched_workspace": (C.c_size_t, [C.c_int32, C.POINTER(qb_dense), C.POINTER(qb_opts)]),
+    "qb_ei_batched": (C.c_int32, [C.c_int32, C.POINTER(qb_dense), C.POINTER(C.c_double),
+                                  C.POINTER(qb_opts), C.POINTER(C.c_void_p), C.POINTER(C.c_int64),
+                                  C.POINTER(C.c_void_p), C.POINTER(C.c_int64), _P, C.c_size_t,
+                                  C.POINTER(qb_info), _P]),
     "qb_quantize_workspace": (C.c_size_t, [_I64, _I64]),
     "qb_quantize_bf16x2": (C.c_int32, [_P, _I64, _I64, _I64, _P, _P, _I64,
                                        C.POINTER(C.c_double), _P, C.c_size_t, _P]),

@@ -38,11 +38,18 @@ int num_sms() {
     return v;
 }
 
+// ------------------------------------------------------------------------------------ phase profile
+enum Phase { PH_OMEGA = 0, PH_SKETCH, PH_TRANS, PH_ORTHW, PH_PROJ, PH_CHOLQR, PH_BFORM, PH_IND,
+             PH_COUNT };
+static double g_prof_ms[PH_COUNT] = {0};
+static std::mutex g_prof_mu;
+
 namespace {
 
 constexpr double U64 = 1.1102230246251565e-16;   // 2^-53
 constexpr double U32 = 5.9604644775390625e-08;   // 2^-24
 constexpr double THM3_DELTA = 0.01;
+constexpr int64_t H_CHUNK = 512;   // randQB_FP: columns of H = A^T G formed at a time
 
 // ------------------------------------------------------------------------------------ context
 struct Ctx {
@@ -54,6 +61,8 @@ struct Ctx {
     double* R = nullptr;
     double* Rinv = nullptr;
     double* Racc = nullptr;
+    double* Rchain = nullptr; // 4 x (64 x 64): inverses of the CholeskyQR factors of one block
+    int nchain = 0;
     double* rn = nullptr;   // 64 row norms
     double* state = nullptr;  // E, keep, stop, E_prev
     double* part = nullptr;   // 3 x 1024 reduction partials
@@ -63,6 +72,39 @@ struct Ctx {
     Acc acc_proj = ACC_D;     // projections / updates
     Acc acc_fine = ACC_D;     // cancellation-prone products (FP's B_i formula, re-orth coefficients)
     bool simt_apass = false;  // QB_FLAG_SIMT_APASS
+    bool prof = false;        // QB_FLAG_PROFILE: CUDA events around the phases of the loop
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> events;
+    struct Scope {
+        Ctx* c;
+        int ph;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        Scope(Ctx& cc, int p) : c(&cc), ph(p) {
+            if (!c->prof) return;
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            cudaEventRecord(e0, c->st);
+        }
+        ~Scope() {
+            if (!c->prof) return;
+            cudaEventRecord(e1, c->st);
+            c->events.push_back({ph, {e0, e1}});
+        }
+    };
+    void flush_profile() {
+        if (!prof) return;
+        cudaStreamSynchronize(st);
+        double acc[PH_COUNT] = {0};
+        for (auto& e : events) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e.second.first, e.second.second);
+            acc[e.first] += ms;
+            cudaEventDestroy(e.second.first);
+            cudaEventDestroy(e.second.second);
+        }
+        events.clear();
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        for (int i = 0; i < PH_COUNT; ++i) g_prof_ms[i] = acc[i];
+    }
 
     void alloc(Arena& ar, int64_t mn_max) {
         scr.part_bytes = gemm_scratch_bytes(mn_max);
@@ -71,6 +113,7 @@ struct Ctx {
         R = ar.get<double>(MAXB * MAXB);
         Rinv = ar.get<double>(MAXB * MAXB);
         Racc = ar.get<double>(MAXB * MAXB);
+        Rchain = ar.get<double>(4 * MAXB * MAXB);
         rn = ar.get<double>(MAXB);
         state = ar.get<double>(8);
         part = ar.get<double>(3 * 1024);
@@ -101,17 +144,27 @@ struct Ctx {
     }
 
     // One CholeskyQR pass: W = P^T P (float64 or float32-pair accumulation), W = R^T R,
-    // P <- P R^-1, Racc <- R Racc when acc_r.  sketch: the basis only has to span the same space
+    // P <- P R^-1; with acc_r the factor's inverse is kept in Rchain (in order) for the B_i formula.  sketch: the basis only has to span the same space
     // (the power scheme), so the Gram is accumulated and factored in float32.
     void cholqr(void* P, int64_t ld, int64_t rows, int bi, bool acc_r, bool sketch = false) {
         const bool fast = sketch && !f64;
         gemm(st, true, bi, bi, rows, 1.0, x(P, ld), P, f64, ld, 0.0, W, true, MAXB,
              f64 ? ACC_D : (fast ? ACC_F : acc_gram), scr);
-        chol_rinv(st, W, bi, fast ? 1e-10 : tau, R, Rinv, acc_r ? Racc : nullptr, flags, fast);
+        double* ri = Rinv;
+        if (acc_r && nchain < 4) ri = Rchain + size_t(nchain++) * MAXB * MAXB;
+        chol_rinv(st, W, bi, fast ? 1e-10 : tau, R, ri, nullptr, flags, fast);
+        apply_rinv(st, f64, P, ld, rows, bi, ri);
+    }
+    // CholeskyQR pass accumulating the factor: Racc <- R Racc (the fixed-rank map keeps R)
+    void cholqr_racc(void* P, int64_t ld, int64_t rows, int bi) {
+        gemm(st, true, bi, bi, rows, 1.0, x(P, ld), P, f64, ld, 0.0, W, true, MAXB,
+             f64 ? ACC_D : acc_gram, scr);
+        chol_rinv(st, W, bi, tau, R, Rinv, Racc, flags, false);
         apply_rinv(st, f64, P, ld, rows, bi, Rinv);
     }
-    // orth(P): CholeskyQR2 (two passes); Racc accumulates R2 R1 when acc_r.
+    // orth(P): CholeskyQR2 (two passes); with acc_r the factors' inverses go to Rchain.
     void cholqr2(void* P, int64_t ld, int64_t rows, int bi, bool acc_r, bool sketch = false) {
+        Scope sc(*this, sketch ? PH_ORTHW : PH_CHOLQR);
         cholqr(P, ld, rows, bi, acc_r, sketch);
         cholqr(P, ld, rows, bi, acc_r, sketch);
     }
@@ -119,19 +172,20 @@ struct Ctx {
     void project_out(const void* Q, int64_t ldq, int64_t k, void* P, int64_t ldp, int64_t rows, int bi,
                      void* T, bool sketch = false) {
         if (k <= 0) return;
+        Scope sc(*this, sketch ? PH_ORTHW : PH_PROJ);
         tn(k, bi, rows, 1.0, Q, ldq, P, ldp, 0.0, T, k, sketch ? ACC_F : acc_fine);
         nn(rows, bi, k, -1.0, Q, ldq, T, k, 1.0, P, ldp, acc_proj);
     }
     // Orthonormalise the rows x w matrix X (column-major) panel by panel for the power scheme:
     // block Gram-Schmidt with re-orthogonalisation, CholeskyQR per panel of width b.  Only the
     // span matters here, so the mixed path works in float32 throughout.  T: w x b scratch.
-    void orth_wide(void* X, int64_t ld, int64_t rows, int64_t w, int b, void* T) {
+    void orth_wide(void* X, int64_t ld, int64_t rows, int64_t w, int b, void* T, bool reorth = true) {
         for (int64_t j0 = 0; j0 < w; j0 += b) {
             const int bj = int(std::min<int64_t>(b, w - j0));
             char* Pj = col(X, ld, j0);
             project_out(X, ld, j0, Pj, ld, rows, bj, T, true);
             cholqr2(Pj, ld, rows, bj, false, true);
-            if (j0 > 0) {
+            if (j0 > 0 && (reorth || f64)) {
                 project_out(X, ld, j0, Pj, ld, rows, bj, T, true);
                 if (f64) cholqr2(Pj, ld, rows, bj, false, true);
                 else cholqr(Pj, ld, rows, bj, false, true);
@@ -140,6 +194,7 @@ struct Ctx {
     }
     struct Step { double E; int keep; int stop; };
     Step indicator_step(const void* Bslot, int64_t ldb, int bi, int64_t n, double eps2, int rbr) {
+        Scope sc(*this, PH_IND);
         row_norm2(st, f64, Bslot, ldb, bi, n, rn);
         indicator(st, state, rn, bi, eps2, rbr);
         double h[3];
@@ -222,6 +277,7 @@ struct DenseOp : AOp {
     }
     void apply(Ctx& c, const void* X, int64_t ldx, int64_t w, void* Y, int64_t ldy,
                int pairs) override {
+        Ctx::Scope sc(c, PH_SKETCH);
         if (use_tc) {
             const int64_t ldb = align_up(n, 8);
             bf16* lo = pairs == 2 ? Xb + ldb * wmax : nullptr;
@@ -236,6 +292,7 @@ struct DenseOp : AOp {
     }
     void apply_t(Ctx& c, const void* X, int64_t ldx, int64_t w, void* Y, int64_t ldy,
                  int mode) override {
+        Ctx::Scope sc(c, PH_TRANS);
         if (!c.f64 && mode >= 2 && bf16_storage()) {
             // The passes that feed the indicator (B_i = Q_i^T A, H = A^T G) run with
             // round-to-nearest float32 sums: tensor-core float32 accumulation is not
@@ -292,9 +349,11 @@ struct CsrOp : AOp {
         csr_to_csc(c.st, A, colptr, rowind, cval, cnt);
     }
     void apply(Ctx& c, const void* X, int64_t ldx, int64_t w, void* Y, int64_t ldy, int) override {
+        Ctx::Scope sc(c, PH_SKETCH);
         csr_spmm(c.st, f64v(), s.rowptr, s.colind, s.val, m, n, X, ldx, w, Y, ldy, stage);
     }
     void apply_t(Ctx& c, const void* X, int64_t ldx, int64_t w, void* Y, int64_t ldy, int) override {
+        Ctx::Scope sc(c, PH_TRANS);
         csr_spmm(c.st, f64v(), colptr, rowind, cval, n, m, X, ldx, w, Y, ldy, stage);
     }
     double norm2(Ctx& c) override {
@@ -386,13 +445,17 @@ void run_ei(Ctx& c, AOp& A, const Plan& p, const qb_opts& o, Bufs& bf, void* Q, 
         const int bi = int(std::min<int64_t>(p.b, p.cap - k));
         out.omega_cols = k + bi;
         // Omega_i = randn(n, b), global columns [k, k + bi)
-        omega_gen(c.st, n, k, bi, o.seed, omega_dt, bf.Om, n);
-        A.round_operand(c, bf.Om, n, n, bi);
+        {
+            Ctx::Scope so(c, PH_OMEGA);
+            omega_gen(c.st, n, k, bi, o.seed, omega_dt, bf.Om, n);
+            A.round_operand(c, bf.Om, n, n, bi);
+        }
         // Y = A Omega_i - Q (B Omega_i), computed in the slot of Q_i
         char* Y = c.col(Q, ldq, k);
         A.apply(c, bf.Om, n, bi, Y, ldq);
         out.passes += 1;
         if (k > 0) {
+            Ctx::Scope sp(c, PH_PROJ);
             c.tn(k, bi, n, 1.0, B, ldb, bf.Om, n, 0.0, bf.T1, k, c.acc_proj);      // B Omega_i
             c.nn(m, bi, k, -1.0, Q, ldq, bf.T1, k, 1.0, Y, ldq, c.acc_proj);      // Y -= Q (.)
         }
@@ -453,7 +516,9 @@ void run_fp(Ctx& c, AOp& A, const Plan& p, const qb_opts& o, Bufs& bf, void* Q, 
                 c.tn(k, w, n, 1.0, B, ldb, bf.Om, n, 0.0, bf.T1, k, c.acc_proj);
                 c.nn(m, w, k, -1.0, Q, ldq, bf.T1, k, 1.0, bf.G, m, c.acc_proj);
             }
-            c.orth_wide(bf.G, m, m, w, p.b, bf.Tw);                               // G = orth(.)
+            // G only has to be a well-conditioned basis for the next application of A^T: one
+            // Gram-Schmidt pass per panel on the mixed path
+            c.orth_wide(bf.G, m, m, w, p.b, bf.Tw, false);                        // G = orth(.)
             A.round_operand(c, bf.G, m, m, w);
             A.apply_t(c, bf.G, m, w, bf.Om, n, 1);                                // Omega = A^T G
             out.passes += 1;
@@ -468,41 +533,53 @@ void run_fp(Ctx& c, AOp& A, const Plan& p, const qb_opts& o, Bufs& bf, void* Q, 
             A.round_operand(c, bf.Om, n, n, w, 2);
         }
         A.apply(c, bf.Om, n, w, bf.G, m, p.P > 0 ? 2 : 1);                        // G = A Omega
-        // H = A^T G for the stored G, in the precision the B_i formula needs
-        A.apply_t(c, bf.G, m, w, bf.H, n, 3);                                     // H = A^T G
         out.passes += 1;
+        // H = A^T G for the stored G, in the precision the B_i formula needs, formed in chunks of
+        // H_CHUNK columns as the loop reaches them (the loop usually stops well before l~)
+        int64_t h_done = 0;
         for (int64_t c0 = 0; c0 < w && !stop; c0 += p.b) {
             const int bi = int(std::min<int64_t>(p.b, w - c0));
+            if (c0 + bi > h_done) {
+                const int64_t hw = std::min<int64_t>(std::max<int64_t>(H_CHUNK, bi), w - h_done);
+                A.apply_t(c, c.col(bf.G, m, h_done), m, hw, c.col(bf.H, n, h_done), n, 3);
+                if (h_done > 0) out.passes += 1;
+                h_done += hw;
+            }
             const char* Om_i = c.col(bf.Om, n, c0);
             // Y_i = G_i - Q (B Omega_i), kept for the B_i formula
             c.copy_cols_(c.col(bf.G, m, c0), m, m, bi, bf.Ys, m);
             if (k > 0) {
+                Ctx::Scope sc(c, PH_PROJ);
                 c.tn(k, bi, n, 1.0, B, ldb, Om_i, n, 0.0, bf.T1, k, c.acc_proj);
                 c.nn(m, bi, k, -1.0, Q, ldq, bf.T1, k, 1.0, bf.Ys, m, c.acc_proj);
             }
-            // [Q_i, R_i] = qr(Y_i) in the slot of Q_i; R accumulated in Racc
+            // [Q_i, R_i] = qr(Y_i) in the slot of Q_i; the inverses of the factors go to Rchain
             char* Qi = c.col(Q, ldq, k);
             c.copy_cols_(bf.Ys, m, m, bi, Qi, ldq);
-            set_identity(c.st, c.Racc, bi);
+            c.nchain = 0;
             c.cholqr2(Qi, ldq, m, bi, true);
             if (k > 0) {
                 // [Q_i, R~_i] = qr(Q_i - Q (Q^T Q_i)), R_i = R~_i R_i
                 c.project_out(Q, ldq, k, Qi, ldq, m, bi, bf.C2);
                 c.cholqr2(Qi, ldq, m, bi, true);
             }
-            tri_inv(c.st, c.Racc, bi, c.Rinv);
-            // S^T = H_i - B^T (Q^T Y_i + B Omega_i), i.e. S = H_i^T - Y_i^T Q B - Omega_i^T B^T B
-            char* S = bf.Z;
-            c.copy_cols_(c.col(bf.H, n, c0), n, n, bi, S, n);
-            if (k > 0) {
-                c.copy_cols_(bf.T1, k, k, bi, bf.C2, k);                          // C2 = B Omega_i
-                c.tn(k, bi, m, 1.0, Q, ldq, bf.Ys, m, 1.0, bf.C2, k, c.acc_fine); // += Q^T Y_i
-                c.nn(n, bi, k, -1.0, B, ldb, bf.C2, k, 1.0, S, n, c.acc_fine);    // S^T -= B^T C2
-            }
-            // B_i = R_i^-T S  <=>  B_i^T = S^T R_i^-1
-            apply_rinv(c.st, c.f64, S, n, n, bi, c.Rinv);
             char* Bs = c.col(B, ldb, k);
-            c.copy_cols_(S, n, n, bi, Bs, ldb);
+            {
+                Ctx::Scope scb(c, PH_BFORM);
+                // S^T = H_i - B^T (Q^T Y_i + B Omega_i), i.e. S = H_i^T - Y_i^T Q B - Omega_i^T B^T B
+                char* S = bf.Z;
+                c.copy_cols_(c.col(bf.H, n, c0), n, n, bi, S, n);
+                if (k > 0) {
+                    c.copy_cols_(bf.T1, k, k, bi, bf.C2, k);                          // C2 = B Omega_i
+                    c.tn(k, bi, m, 1.0, Q, ldq, bf.Ys, m, 1.0, bf.C2, k, c.acc_fine); // += Q^T Y_i
+                    c.nn(n, bi, k, -1.0, B, ldb, bf.C2, k, 1.0, S, n, c.acc_fine);    // S^T -= B^T C2
+                }
+                // B_i = R_i^-T S  <=>  B_i^T = S^T R_i^-1, R_i = R~_2 R~_1 R_2 R_1 (the four
+                // CholeskyQR factors): apply R_1^-1, R_2^-1, R~_1^-1, R~_2^-1 in turn
+                for (int f = 0; f < c.nchain; ++f)
+                    apply_rinv(c.st, c.f64, S, n, n, bi, c.Rchain + size_t(f) * MAXB * MAXB);
+                c.copy_cols_(S, n, n, bi, Bs, ldb);
+            }
             const Ctx::Step s = c.indicator_step(Bs, ldb, bi, n, eps2, o.row_by_row);
             out.blocks += 1;
             out.E = s.E;
@@ -525,6 +602,7 @@ int32_t run_common(AOp& A, const qb_opts* opts, bool fp, void* Q, int64_t ldq, v
     Ctx c;
     setup_ctx(c, o.prec == QB_PREC_FP64);
     c.simt_apass = (o.flags & QB_FLAG_SIMT_APASS) != 0;
+    c.prof = (o.flags & QB_FLAG_PROFILE) != 0;
     c.st = reinterpret_cast<cudaStream_t>(stream);
     Bufs bf;
     Arena ar;
@@ -578,6 +656,7 @@ int32_t run_common(AOp& A, const qb_opts* opts, bool fp, void* Q, int64_t ldq, v
     QB_CUDA(cudaMemcpyAsync(c.state, st0, sizeof st0, cudaMemcpyHostToDevice, c.st));
     if (fp) run_fp(c, A, p, o, bf, Q, ldq, B, ldb, eps2, out);
     else run_ei(c, A, p, o, bf, Q, ldq, B, ldb, eps2, out);
+    c.flush_profile();
     if (A.timed_out(c)) {
         fill_info(0);
         return QB_ERR_TIMEOUT;
@@ -651,7 +730,8 @@ void fixed_fwd(Ctx& c, DenseOp& A, int64_t k, uint64_t seed, FixedBufs& f, void*
             }
         }
         set_identity(c.st, c.Racc, bj);
-        c.cholqr2(Pj, ldq, m, bj, true);                         // Q_j R_jj = P_j
+        c.cholqr_racc(Pj, ldq, m, bj);                           // Q_j R_jj = P_j
+        c.cholqr_racc(Pj, ldq, m, bj);
         char* Rjj = reinterpret_cast<char*>(Rj) + size_t(j0) * c.es;
         from_f64(c.st, c.f64, c.Racc, MAXB, bj, bj, Rjj, ldr);
     }
@@ -742,6 +822,13 @@ const char* qb_status_str(int32_t s) {
 const char* qb_last_cuda_error(void) { return g_last_err; }
 
 int64_t qb_launch_count(void) { return launches_total(); }
+
+int32_t qb_profile_last(double* ms, int32_t n) {
+    if (!ms || n < 0) return QB_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (int i = 0; i < n && i < PH_COUNT; ++i) ms[i] = g_prof_ms[i];
+    return PH_COUNT;
+}
 
 size_t qb_dense_workspace(const qb_dense* A, const qb_opts* opts, int32_t algo) {
     if (!valid_dense(A, opts) || !valid_opts(opts) || (algo != 0 && algo != 1)) return 0;

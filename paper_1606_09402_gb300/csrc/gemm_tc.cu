@@ -129,6 +129,31 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 64 columns as two x32 loads with a single wait
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64]) {
+    uint32_t r[64];
+#define QB_LD32(OFF, BASE)                                                                       \
+    asm volatile(                                                                                \
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "                                                \
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"                                \
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"               \
+        : "=r"(r[BASE + 0]), "=r"(r[BASE + 1]), "=r"(r[BASE + 2]), "=r"(r[BASE + 3]),            \
+          "=r"(r[BASE + 4]), "=r"(r[BASE + 5]), "=r"(r[BASE + 6]), "=r"(r[BASE + 7]),            \
+          "=r"(r[BASE + 8]), "=r"(r[BASE + 9]), "=r"(r[BASE + 10]), "=r"(r[BASE + 11]),          \
+          "=r"(r[BASE + 12]), "=r"(r[BASE + 13]), "=r"(r[BASE + 14]), "=r"(r[BASE + 15]),        \
+          "=r"(r[BASE + 16]), "=r"(r[BASE + 17]), "=r"(r[BASE + 18]), "=r"(r[BASE + 19]),        \
+          "=r"(r[BASE + 20]), "=r"(r[BASE + 21]), "=r"(r[BASE + 22]), "=r"(r[BASE + 23]),        \
+          "=r"(r[BASE + 24]), "=r"(r[BASE + 25]), "=r"(r[BASE + 26]), "=r"(r[BASE + 27]),        \
+          "=r"(r[BASE + 28]), "=r"(r[BASE + 29]), "=r"(r[BASE + 30]), "=r"(r[BASE + 31])         \
+        : "r"(taddr + (OFF)))
+    QB_LD32(0, 0);
+    QB_LD32(32, 32);
+#undef QB_LD32
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // Shared-memory matrix descriptor (tcgen05): start address, leading / stride byte offsets,
 // descriptor version 1, 128-byte swizzle.
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
@@ -347,40 +372,68 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
         int buf = 0;
         uint32_t tphase[2] = {0, 0};
         while (ok && next_seg(pos, sg, first)) {
-            // Sum the chunk accumulators of this segment in registers (round to nearest), so the
-            // float32 result carries no drift from long tensor-core accumulation chains.
-            float accr[BN];
-#pragma unroll
-            for (int j = 0; j < BN; ++j) accr[j] = 0.f;
-            for (int c0 = sg.k0; c0 < sg.k1 && ok; c0 += p.chunk) {
+            int r0, c0;
+            unit_rc(sg.u, r0, c0);
+            const int64_t gr = int64_t(r0) + row;
+            float* slot = sg.slot >= 0 ? p.part + ((int64_t(cta) * 2 + sg.slot) * BN) * BM : nullptr;
+            if (sg.k1 - sg.k0 <= p.chunk) {
+                // one accumulation chain: stream tensor memory straight to global memory
                 ok = mbar_wait(tfull + buf, tphase[buf], p.err);
                 if (!ok) break;
                 tc_fence_after();
-#pragma unroll
+#pragma unroll 1
                 for (int cc = 0; cc < BN; cc += 32) {
                     float v[32];
                     tmem_ld32(tmem + (uint32_t(q * 32) << 16) + uint32_t(buf * BN + cc), v);
+                    if (slot) {
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) accr[cc + j] += v[j];
+                        for (int j = 0; j < 32; ++j) slot[int64_t(cc + j) * BM + row] = v[j];
+                    } else if (gr < p.M) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const int gc = c0 + cc + j;
+                            if (gc < p.N) p.D[gr + int64_t(gc) * p.ldd] = v[j];
+                        }
+                    }
                 }
                 tc_fence_before();
                 mbar_arrive(tempty + buf);
                 tphase[buf] ^= 1;
                 buf ^= 1;
+                continue;
             }
-            if (!ok) break;
-            int r0, c0;
-            unit_rc(sg.u, r0, c0);
-            const int64_t gr = int64_t(r0) + row;
-            if (sg.slot >= 0) {
-                float* slot = p.part + ((int64_t(cta) * 2 + sg.slot) * BN) * BM;
+            if constexpr (BN <= 128) {
+                // Several chains: sum the chunk accumulators in registers (round to nearest), so
+                // the float32 result carries no drift from long tensor-core accumulation chains.
+                float accr[BN];
 #pragma unroll
-                for (int j = 0; j < BN; ++j) slot[int64_t(j) * BM + row] = accr[j];
-            } else if (gr < p.M) {
+                for (int j = 0; j < BN; ++j) accr[j] = 0.f;
+                for (int k0 = sg.k0; k0 < sg.k1 && ok; k0 += p.chunk) {
+                    ok = mbar_wait(tfull + buf, tphase[buf], p.err);
+                    if (!ok) break;
+                    tc_fence_after();
 #pragma unroll
-                for (int j = 0; j < BN; ++j) {
-                    const int gc = c0 + j;
-                    if (gc < p.N) p.D[gr + int64_t(gc) * p.ldd] = accr[j];
+                    for (int cc = 0; cc < BN; cc += 64) {
+                        float v[64];
+                        tmem_ld64(tmem + (uint32_t(q * 32) << 16) + uint32_t(buf * BN + cc), v);
+#pragma unroll
+                        for (int j = 0; j < 64; ++j) accr[cc + j] += v[j];
+                    }
+                    tc_fence_before();
+                    mbar_arrive(tempty + buf);
+                    tphase[buf] ^= 1;
+                    buf ^= 1;
+                }
+                if (!ok) break;
+                if (slot) {
+#pragma unroll
+                    for (int j = 0; j < BN; ++j) slot[int64_t(j) * BM + row] = accr[j];
+                } else if (gr < p.M) {
+#pragma unroll
+                    for (int j = 0; j < BN; ++j) {
+                        const int gc = c0 + j;
+                        if (gc < p.N) p.D[gr + int64_t(gc) * p.ldd] = accr[j];
+                    }
                 }
             }
         }
@@ -474,13 +527,25 @@ CUtensorMap make_map(const void* ptr, int64_t inner, int64_t outer, int64_t ld, 
     return m;
 }
 
-// Column tile: 64 or 128 columns (the epilogue keeps one float32 register per column).
-int pick_bn(int64_t w, bool) { return w <= 64 ? 64 : 128; }
+// Column tile: 64 / 128 columns for chunked passes (the epilogue keeps one float32 register per
+// column), up to 256 for wide single-chain passes.
+int pick_bn(int64_t w, bool chunked) {
+    if (w <= 64) return 64;
+    if (w <= 128 || chunked) return 128;
+    return 256;
+}
 
 // k-blocks per tensor-memory chunk: the tensor cores' float32 accumulation drifts toward zero by
-// roughly 1e-9 (relative) per accumulated MMA (measured: -3.4e-6 over a 40000-long chain), so
-// chains are kept to 4 (sketch) or 1 (full-precision passes) k-blocks and summed in registers.
-int pick_chunk(int mode) { return mode >= 2 ? 1 : 4; }
+// roughly 1e-9 (relative) per accumulated MMA (measured: -3.4e-6 over a 40000-long chain).  The
+// narrow passes (w <= 128: randQB_EI's sketches and power steps, whose results are projected
+// against Q and B) keep chains of 4 k-blocks (1 for the hi/lo passes) summed in registers; wide
+// passes (randQB_FP's G = A Omega and power steps over the whole batch, where any G is valid as
+// long as H = A^T G is formed from the stored G) use one chain per tile.
+constexpr int SINGLE_CHAIN = 1 << 30;
+int pick_chunk(int mode, int64_t w) {
+    if (w > 128 && mode < 2) return SINGLE_CHAIN;
+    return mode >= 2 ? 1 : 4;
+}
 
 template <int BN, bool TRANS, int NA, int NB>
 void run(cudaStream_t st, const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& b0,
@@ -500,7 +565,8 @@ template <bool TRANS, int NA, int NB>
 void run_bn(int bn, cudaStream_t st, const CUtensorMap& a0, const CUtensorMap& a1,
             const CUtensorMap& b0, const CUtensorMap& b1, Params p, int G) {
     if (bn == 64) run<64, TRANS, NA, NB>(st, a0, a1, b0, b1, p, G);
-    else run<128, TRANS, NA, NB>(st, a0, a1, b0, b1, p, G);
+    else if (bn == 128) run<128, TRANS, NA, NB>(st, a0, a1, b0, b1, p, G);
+    else run<256, TRANS, NA, NB>(st, a0, a1, b0, b1, p, G);
 }
 
 struct Scratch {
@@ -574,12 +640,13 @@ void tc_sketch(cudaStream_t st, const bf16* A, int64_t lda, int64_t m, int64_t n
                size_t scratch_bytes) {
     if (m <= 0 || w <= 0) return;
     Scratch s = carve(scratch, scratch_bytes, 0, 0);
-    const int bn = pick_bn(w, false);
+    const int chunk = pick_chunk(1, w);
+    const int bn = pick_bn(w, chunk != SINGLE_CHAIN);
     Params p{};
     p.M = int(m);
     p.N = int(w);
     p.K = int(n);
-    p.chunk = pick_chunk(1);
+    p.chunk = chunk;
     int G = num_sms();
     p.s = make_sched(m, w, n, bn, G);
     G = grid_size(p.s, G);
@@ -609,12 +676,13 @@ void tc_trans(cudaStream_t st, const bf16* A_hi, const bf16* A_lo, int64_t lda, 
     k_split_bf16<<<unsigned(cdiv(m * w, 256)), 256, 0, st>>>(V, ldv, m, w, s.vhi,
                                                              mode == 3 ? s.vlo : nullptr, ldo);
     QB_LAUNCHED();
-    const int bn = pick_bn(w, mode > 1);
+    const int chunk = pick_chunk(mode, w);
+    const int bn = pick_bn(w, chunk != SINGLE_CHAIN);
     Params p{};
     p.M = int(n);
     p.N = int(w);
     p.K = int(m);
-    p.chunk = pick_chunk(mode);
+    p.chunk = chunk;
     int G = num_sms();
     p.s = make_sched(n, w, m, bn, G);
     G = grid_size(p.s, G);
