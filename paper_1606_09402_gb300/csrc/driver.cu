@@ -72,6 +72,12 @@ struct Ctx {
     Acc acc_proj = ACC_D;     // projections / updates
     Acc acc_fine = ACC_D;     // cancellation-prone products (FP's B_i formula, re-orth coefficients)
     bool simt_apass = false;  // QB_FLAG_SIMT_APASS
+    // tensor-core projections for the power-scheme orthonormalisation (mixed path)
+    void* tcs = nullptr;
+    size_t tcs_bytes = 0;
+    bf16* xb_hi = nullptr;    // bf16 shadow of the panels finished so far (hi, lo)
+    bf16* xb_lo = nullptr;
+    int64_t xb_ld = 0;
     bool prof = false;        // QB_FLAG_PROFILE: CUDA events around the phases of the loop
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> events;
     struct Scope {
@@ -179,17 +185,39 @@ struct Ctx {
     // Orthonormalise the rows x w matrix X (column-major) panel by panel for the power scheme:
     // block Gram-Schmidt with re-orthogonalisation, CholeskyQR per panel of width b.  Only the
     // span matters here, so the mixed path works in float32 throughout.  T: w x b scratch.
+    //
+    // On the mixed path with a TMA-compatible layout the projections run on the tensor cores
+    // against a bf16 shadow of the finished panels: bf16 only for G (one pass; any well-conditioned
+    // basis will do), bf16 hi + lo with three products for Omega (its residual overlap with earlier
+    // panels leaks sigma_1^2-sized terms into the B_i formula).
     void orth_wide(void* X, int64_t ld, int64_t rows, int64_t w, int b, void* T, bool reorth = true) {
+        const bool tc = !f64 && xb_hi && rows % 8 == 0 && rows <= xb_ld;
+        bf16* lo = reorth ? xb_lo : nullptr;
+        auto project = [&](int64_t j0, char* Pj, int bj) {
+            if (j0 <= 0) return;
+            if (!tc) {
+                project_out(X, ld, j0, Pj, ld, rows, bj, T, true);
+                return;
+            }
+            Scope sc(*this, PH_ORTHW);
+            tc_xtp(st, xb_hi, lo, xb_ld, rows, j0, reinterpret_cast<const float*>(Pj), ld, bj,
+                   reinterpret_cast<float*>(T), j0, tcs, tcs_bytes);
+            tc_p_minus_xt(st, xb_hi, lo, xb_ld, rows, j0, reinterpret_cast<const float*>(T), j0,
+                          bj, reinterpret_cast<float*>(Pj), ld, tcs, tcs_bytes);
+        };
         for (int64_t j0 = 0; j0 < w; j0 += b) {
             const int bj = int(std::min<int64_t>(b, w - j0));
             char* Pj = col(X, ld, j0);
-            project_out(X, ld, j0, Pj, ld, rows, bj, T, true);
+            project(j0, Pj, bj);
             cholqr2(Pj, ld, rows, bj, false, true);
             if (j0 > 0 && (reorth || f64)) {
-                project_out(X, ld, j0, Pj, ld, rows, bj, T, true);
+                project(j0, Pj, bj);
                 if (f64) cholqr2(Pj, ld, rows, bj, false, true);
                 else cholqr(Pj, ld, rows, bj, false, true);
             }
+            if (tc)
+                split_bf16(st, reinterpret_cast<const float*>(Pj), ld, rows, bj,
+                           xb_hi + j0 * xb_ld, lo ? lo + j0 * xb_ld : nullptr, xb_ld);
         }
     }
     struct Step { double E; int keep; int stop; };
@@ -230,6 +258,8 @@ struct AOp {
     virtual double norm2(Ctx& c) = 0;
     // true when a bounded device-side wait of this operator's kernels ran out
     virtual bool timed_out(Ctx&) { return false; }
+    // tensor-core scratch of this operator, if it has one
+    virtual bool tc_scratch(void**, size_t*) { return false; }
 };
 
 struct DenseOp : AOp {
@@ -267,6 +297,12 @@ struct DenseOp : AOp {
     }
     void prepare(Ctx& c) override {
         if (use_tc) QB_CUDA(cudaMemsetAsync(tc_error_flag(tc_scr), 0, 256, c.st));
+    }
+    bool tc_scratch(void** p, size_t* b) override {
+        if (!use_tc) return false;
+        *p = tc_scr;
+        *b = tc_bytes;
+        return true;
     }
     bool timed_out(Ctx& c) override {
         if (!use_tc) return false;
@@ -425,6 +461,11 @@ void reserve_all(Arena& ar, Ctx& c, AOp& A, const Plan& p, bool fp, Bufs& bf) {
         bf.Tw = ar.get<char>(p.lt * p.b * es);
     }
     A.reserve(ar, c, wmax);
+    if (fp && p.P > 0 && A.tc_scratch(&c.tcs, &c.tcs_bytes)) {
+        c.xb_ld = align_up(std::max(p.m, p.n), 8);
+        c.xb_hi = ar.get<bf16>(c.xb_ld * p.lt);
+        c.xb_lo = ar.get<bf16>(c.xb_ld * p.lt);
+    }
 }
 
 struct RunOut {

@@ -188,6 +188,7 @@ __host__ __device__ __forceinline__ int64_t sk_begin(int64_t total, int64_t c, i
 struct Params {
     int M, N, K;                 // D is M x N, reduction length K
     int chunk;                   // k-blocks accumulated in tensor memory before a register flush
+    float alpha, beta;           // D = alpha * (product) + beta * D
     Sched s;
     float* D;
     int64_t ldd;
@@ -392,7 +393,10 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
 #pragma unroll
                         for (int j = 0; j < 32; ++j) {
                             const int gc = c0 + cc + j;
-                            if (gc < p.N) p.D[gr + int64_t(gc) * p.ldd] = v[j];
+                            if (gc < p.N) {
+                                float* o = p.D + gr + int64_t(gc) * p.ldd;
+                                *o = p.beta != 0.f ? fmaf(p.alpha, v[j], p.beta * *o) : p.alpha * v[j];
+                            }
                         }
                     }
                 }
@@ -432,7 +436,10 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
 #pragma unroll
                     for (int j = 0; j < BN; ++j) {
                         const int gc = c0 + j;
-                        if (gc < p.N) p.D[gr + int64_t(gc) * p.ldd] = accr[j];
+                        if (gc < p.N) {
+                            float* o = p.D + gr + int64_t(gc) * p.ldd;
+                            *o = p.beta != 0.f ? fmaf(p.alpha, accr[j], p.beta * *o) : p.alpha * accr[j];
+                        }
                     }
                 }
             }
@@ -475,7 +482,10 @@ __global__ void k_tc_fixup(Params p, int G) {
         }
         const int64_t gr = int64_t(r0) + row;
         const int gc = c0 + col;
-        if (gr < p.M && gc < p.N) p.D[gr + int64_t(gc) * p.ldd] = s;
+        if (gr < p.M && gc < p.N) {
+            float* o = p.D + gr + int64_t(gc) * p.ldd;
+            *o = p.beta != 0.f ? fmaf(p.alpha, s, p.beta * *o) : p.alpha * s;
+        }
     }
 }
 
@@ -647,6 +657,8 @@ void tc_sketch(cudaStream_t st, const bf16* A, int64_t lda, int64_t m, int64_t n
     p.N = int(w);
     p.K = int(n);
     p.chunk = chunk;
+    p.alpha = 1.f;
+    p.beta = 0.f;
     int G = num_sms();
     p.s = make_sched(m, w, n, bn, G);
     G = grid_size(p.s, G);
@@ -683,6 +695,8 @@ void tc_trans(cudaStream_t st, const bf16* A_hi, const bf16* A_lo, int64_t lda, 
     p.N = int(w);
     p.K = int(m);
     p.chunk = chunk;
+    p.alpha = 1.f;
+    p.beta = 0.f;
     int G = num_sms();
     p.s = make_sched(n, w, m, bn, G);
     G = grid_size(p.s, G);
@@ -705,6 +719,90 @@ void tc_trans(cudaStream_t st, const bf16* A_hi, const bf16* A_lo, int64_t lda, 
         return;
     }
     const CUtensorMap b1 = make_map(s.vlo, m, w, ldo, BK, bn);
+    run_bn<true, 2, 2>(bn, st, a0, a1, b0, b1, p, G);
+}
+
+// T (j0 x bw, col-major, ldt) = X^T P for X column-major rows x j0 held as bf16 hi [+ lo] (ldx),
+// P float32 column-major rows x bw (ldp), split to bf16 hi [+ lo] on the fly.  Tensor cores,
+// chunked accumulation.  Products: X_hi P_hi [+ X_lo P_hi + X_hi P_lo when X_lo != nullptr].
+void tc_xtp(cudaStream_t st, const bf16* Xhi, const bf16* Xlo, int64_t ldx, int64_t rows,
+            int64_t j0, const float* P, int64_t ldp, int64_t bw, float* T, int64_t ldt,
+            void* scratch, size_t scratch_bytes) {
+    if (j0 <= 0 || bw <= 0) return;
+    // scratch: [err 256][P hi][P lo][partials]
+    Scratch s = carve(scratch, scratch_bytes, rows, bw);
+    const int64_t ldb = align_up(rows, 8);
+    k_split_bf16<<<unsigned(cdiv(rows * bw, 256)), 256, 0, st>>>(P, ldp, rows, bw, s.vhi,
+                                                              Xlo ? s.vlo : nullptr, ldb);
+    QB_LAUNCHED();
+    const int chunk = pick_chunk(Xlo ? 3 : 1, bw);
+    const int bn = pick_bn(bw, true);
+    Params p{};
+    p.M = int(j0);
+    p.N = int(bw);
+    p.K = int(rows);
+    p.chunk = chunk;
+    p.alpha = 1.f;
+    p.beta = 0.f;
+    int G = num_sms();
+    p.s = make_sched(j0, bw, rows, bn, G);
+    G = grid_size(p.s, G);
+    p.D = T;
+    p.ldd = ldt;
+    p.part = s.part;
+    p.err = s.err;
+    if (p.s.streamk && size_t(G) * 2 * bn * BM * sizeof(float) > s.part_bytes)
+        throw Error{QB_ERR_WORKSPACE, "tensor-core partials"};
+    // "A" operand: X^T as a row-major j0 x rows matrix = X column-major
+    const CUtensorMap a0 = make_map(Xhi, rows, j0, ldx, BK, BM);
+    const CUtensorMap b0 = make_map(s.vhi, rows, bw, ldb, BK, bn);
+    if (!Xlo) {
+        run_bn<false, 1, 1>(bn, st, a0, a0, b0, b0, p, G);
+        return;
+    }
+    const CUtensorMap a1 = make_map(Xlo, rows, j0, ldx, BK, BM);
+    const CUtensorMap b1 = make_map(s.vlo, rows, bw, ldb, BK, bn);
+    run_bn<false, 2, 2>(bn, st, a0, a1, b0, b1, p, G);
+}
+
+// P (rows x bw, col-major, ldp) -= X T for X column-major rows x j0 (bf16 hi [+ lo], ldx) and
+// T float32 j0 x bw (ldt), split to bf16 on the fly.  Tensor cores, chunked accumulation.
+void tc_p_minus_xt(cudaStream_t st, const bf16* Xhi, const bf16* Xlo, int64_t ldx, int64_t rows,
+                   int64_t j0, const float* T, int64_t ldt, int64_t bw, float* P, int64_t ldp,
+                   void* scratch, size_t scratch_bytes) {
+    if (j0 <= 0 || bw <= 0 || rows <= 0) return;
+    Scratch s = carve(scratch, scratch_bytes, j0, bw);
+    const int64_t ldo = align_up(j0, 8);
+    k_split_bf16<<<unsigned(cdiv(j0 * bw, 256)), 256, 0, st>>>(T, ldt, j0, bw, s.vhi,
+                                                             Xlo ? s.vlo : nullptr, ldo);
+    QB_LAUNCHED();
+    const int chunk = pick_chunk(Xlo ? 3 : 1, bw);
+    const int bn = pick_bn(bw, true);
+    Params p{};
+    p.M = int(rows);
+    p.N = int(bw);
+    p.K = int(j0);
+    p.chunk = chunk;
+    p.alpha = -1.f;
+    p.beta = 1.f;
+    int G = num_sms();
+    p.s = make_sched(rows, bw, j0, bn, G);
+    G = grid_size(p.s, G);
+    p.D = P;
+    p.ldd = ldp;
+    p.part = s.part;
+    p.err = s.err;
+    if (p.s.streamk && size_t(G) * 2 * bn * BM * sizeof(float) > s.part_bytes)
+        throw Error{QB_ERR_WORKSPACE, "tensor-core partials"};
+    // "A" operand of the transposed form: X^T as a row-major j0 x rows tensor (K = j0, M = rows)
+    const CUtensorMap a0 = make_map(Xhi, rows, j0, ldx, 64, BK);
+    const CUtensorMap b0 = make_map(s.vhi, j0, bw, ldo, BK, bn);
+    if (!Xlo) {
+        run_bn<true, 1, 1>(bn, st, a0, a0, b0, b0, p, G);
+        return;
+    }
+    const CUtensorMap a1 = make_map(Xlo, rows, j0, ldx, 64, BK);
+    const CUtensorMap b1 = make_map(s.vlo, j0, bw, ldo, BK, bn);
     run_bn<true, 2, 2>(bn, st, a0, a1, b0, b1, p, G);
 }
 

@@ -20,7 +20,9 @@ k_chol(const double* __restrict__ W, int bi, double tau_rel, double* __restrict_
     T (*S)[LDS] = reinterpret_cast<T (*)[LDS]>(smem);
     T (*X)[LDS] = reinterpret_cast<T (*)[LDS]>(reinterpret_cast<T*>(smem) + MAXB * LDS);
     __shared__ T piv;
+    __shared__ T ipiv;
     __shared__ T dmax;
+    __shared__ T idiag[MAXB];
     const int tid = threadIdx.x;
     for (int e = tid; e < MAXB * MAXB; e += blockDim.x) {
         const int i = e % MAXB, j = e / MAXB;
@@ -44,10 +46,12 @@ k_chol(const double* __restrict__ W, int bi, double tau_rel, double* __restrict_
                 atomicOr(flags + 1, 1);
             }
             piv = sqrt(d);
+            ipiv = T(1) / piv;
+            idiag[j] = ipiv;
             S[j][j] = piv;
         }
         __syncthreads();
-        for (int c = j + 1 + tid; c < bi; c += blockDim.x) S[j][c] /= piv;
+        for (int c = j + 1 + tid; c < bi; c += blockDim.x) S[j][c] *= ipiv;
         __syncthreads();
         // trailing update of the upper triangle: S[a][c] -= R[j][a] R[j][c], j < a <= c
         const int t = bi - j - 1;
@@ -57,16 +61,20 @@ k_chol(const double* __restrict__ W, int bi, double tau_rel, double* __restrict_
         }
         __syncthreads();
     }
-    // inverse of the upper-triangular R, one column per thread (back substitution)
-    for (int c = tid; c < bi; c += blockDim.x) {
-        X[c][c] = T(1) / S[c][c];
-        for (int i = c - 1; i >= 0; --i) {
-            T s = T(0);
-            for (int l = i + 1; l <= c; ++l) s = fma(S[i][l], X[l][c], s);
-            X[i][c] = -s / S[i][i];
-        }
-    }
+    // inverse of the upper-triangular R by back substitution, all columns at once: X[i][c]
+    // (i < l) accumulates sum_{l' > i} R[i][l'] X[l'][c] while l sweeps down
     __syncthreads();
+    for (int l = bi - 1; l >= 0; --l) {
+        for (int c = l + tid; c < bi; c += blockDim.x)
+            X[l][c] = (c == l ? T(1) : -X[l][c]) * idiag[l];
+        __syncthreads();
+        const int rows = l, cols = bi - l;
+        for (int e = tid; e < rows * cols; e += blockDim.x) {
+            const int i = e % rows, c = l + e / rows;
+            X[i][c] = fma(S[i][l], X[l][c], X[i][c]);
+        }
+        __syncthreads();
+    }
     for (int e = tid; e < MAXB * MAXB; e += blockDim.x) {
         const int i = e % MAXB, j = e / MAXB;
         if (Rout) Rout[i + j * MAXB] = i <= j ? double(S[i][j]) : 0.0;

@@ -111,6 +111,15 @@ int* tc_error_flag(void* scratch);
 void tc_sketch(cudaStream_t st, const bf16* A, int64_t lda, int64_t m, int64_t n,
                const bf16* Vt, const bf16* Vt_lo, int64_t ldv, int64_t w, float* Y, int64_t ldy,
                void* scratch, size_t scratch_bytes);
+// Tensor-core products with a column-major X held as bf16 hi [+ lo] (rows % 8 == 0):
+//   tc_xtp:        T (j0 x bw) = X[:, :j0]^T P
+//   tc_p_minus_xt: P (rows x bw) -= X[:, :j0] T
+void tc_xtp(cudaStream_t st, const bf16* Xhi, const bf16* Xlo, int64_t ldx, int64_t rows,
+            int64_t j0, const float* P, int64_t ldp, int64_t bw, float* T, int64_t ldt,
+            void* scratch, size_t scratch_bytes);
+void tc_p_minus_xt(cudaStream_t st, const bf16* Xhi, const bf16* Xlo, int64_t ldx, int64_t rows,
+                   int64_t j0, const float* T, int64_t ldt, int64_t bw, float* P, int64_t ldp,
+                   void* scratch, size_t scratch_bytes);
 // V (rows x w float, col-major) -> bf16 hi (and lo = bf16(V - hi) when lo != nullptr)
 void split_bf16(cudaStream_t st, const float* V, int64_t ldv, int64_t rows, int64_t w, bf16* hi,
                 bf16* lo, int64_t ldo);
