@@ -177,9 +177,13 @@ int32_t qb_fp_csr(const qb_csr* A, const qb_opts* opts, void* Q, int64_t ldq, vo
  *                    through its hi part only.
  *   qb_apass_trans:  Z (n x w, column-major, ldz) = A^T V, V m x w column-major (ldv)
  *                    (H = A^T G of Algorithm 4, B_i^T = A^T Q_i of Algorithm 2).  For a bf16x2 A:
- *                    precise = 0: A_hi^T bf16(V) on the tensor cores (sketch precision);
- *                    precise != 0: (A_hi + A_lo)^T V in float32 with round-to-nearest sums
- *                    (the precision the indicator needs).  Float64 A ignores precise.
+ *                    precise = 0: A_hi^T bf16(V) (sketch precision);
+ *                    precise = 1: (A_hi + A_lo)^T V, V split exactly into three bf16 terms;
+ *                    precise = 2: (A_hi + A_lo)^T bf16(V).
+ *                    With precise != 0 the leading product A_hi^T V_hi is summed per MMA in
+ *                    float32 registers with round-to-nearest (the precision the indicator
+ *                    needs; a single tensor-core accumulation chain would bias it toward zero).
+ *                    Float64 A ignores precise.
  * Workspace: qb_apass_workspace(A, w) bytes.
  * ------------------------------------------------------------------------------------------- */
 size_t qb_apass_workspace(const qb_dense* A, int64_t w);

@@ -154,18 +154,17 @@ struct Ctx {
     // (the power scheme), so the Gram is accumulated and factored in float32.
     void cholqr(void* P, int64_t ld, int64_t rows, int bi, bool acc_r, bool sketch = false) {
         const bool fast = sketch && !f64;
-        gemm(st, true, bi, bi, rows, 1.0, x(P, ld), P, f64, ld, 0.0, W, true, MAXB,
-             f64 ? ACC_D : (fast ? ACC_F : acc_gram), scr);
+        gram(st, P, ld, rows, bi, f64, f64 ? ACC_D : (fast ? ACC_F : acc_gram), W, scr);
         double* ri = Rinv;
         if (acc_r && nchain < 4) ri = Rchain + size_t(nchain++) * MAXB * MAXB;
-        chol_rinv(st, W, bi, fast ? 1e-10 : tau, R, ri, nullptr, flags, fast);
+        chol_rinv(st, W, bi, fast ? 1e-10 : tau, nullptr, ri, nullptr, flags,
+                  f64 ? CHOL_F64 : (fast ? CHOL_F32 : CHOL_F64_INV_F32));
         apply_rinv(st, f64, P, ld, rows, bi, ri);
     }
     // CholeskyQR pass accumulating the factor: Racc <- R Racc (the fixed-rank map keeps R)
     void cholqr_racc(void* P, int64_t ld, int64_t rows, int bi) {
-        gemm(st, true, bi, bi, rows, 1.0, x(P, ld), P, f64, ld, 0.0, W, true, MAXB,
-             f64 ? ACC_D : acc_gram, scr);
-        chol_rinv(st, W, bi, tau, R, Rinv, Racc, flags, false);
+        gram(st, P, ld, rows, bi, f64, f64 ? ACC_D : acc_gram, W, scr);
+        chol_rinv(st, W, bi, tau, nullptr, Rinv, Racc, flags, f64 ? CHOL_F64 : CHOL_F64_INV_F32);
         apply_rinv(st, f64, P, ld, rows, bi, Rinv);
     }
     // orth(P): CholeskyQR2 (two passes); with acc_r the factors' inverses go to Rchain.
@@ -329,10 +328,19 @@ struct DenseOp : AOp {
     void apply_t(Ctx& c, const void* X, int64_t ldx, int64_t w, void* Y, int64_t ldy,
                  int mode) override {
         Ctx::Scope sc(c, PH_TRANS);
+        if (use_tc && mode >= 2) {
+            // The passes that feed the indicator (B_i = Q_i^T A, H = A^T G): full A, the operand
+            // split exactly into bf16 terms, the leading product summed per MMA in registers with
+            // round-to-nearest (tensor-core float32 accumulation is not round-to-nearest and
+            // would bias ||B_i||^2 low on long reductions).
+            tc_trans(c.st, reinterpret_cast<const bf16*>(d.a),
+                     d.dtype == QB_BF16X2 ? reinterpret_cast<const bf16*>(d.a_lo) : nullptr, d.ld,
+                     m, n, reinterpret_cast<const float*>(X), ldx, w, reinterpret_cast<float*>(Y),
+                     ldy, mode, tc_scr, tc_bytes);
+            return;
+        }
         if (!c.f64 && mode >= 2 && bf16_storage()) {
-            // The passes that feed the indicator (B_i = Q_i^T A, H = A^T G) run with
-            // round-to-nearest float32 sums: tensor-core float32 accumulation is not
-            // round-to-nearest and biases ||B_i||^2 low on long reductions.
+            // round-to-nearest float32 sums on the SIMT cores
             trans_precise(c.st, reinterpret_cast<const bf16*>(d.a),
                           d.dtype == QB_BF16X2 ? reinterpret_cast<const bf16*>(d.a_lo) : nullptr,
                           d.ld, m, n,
@@ -341,10 +349,9 @@ struct DenseOp : AOp {
             return;
         }
         if (use_tc) {
-            const int md = d.dtype == QB_BF16X2 ? mode : 1;
             tc_trans(c.st, reinterpret_cast<const bf16*>(d.a), reinterpret_cast<const bf16*>(d.a_lo),
                      d.ld, m, n, reinterpret_cast<const float*>(X), ldx, w,
-                     reinterpret_cast<float*>(Y), ldy, md, tc_scr, tc_bytes);
+                     reinterpret_cast<float*>(Y), ldy, 1, tc_scr, tc_bytes);
             return;
         }
         gemm(c.st, false, n, w, m, 1.0, xa(mode > 1), X, c.f64, ldx, 0.0, Y, c.f64, ldy,
@@ -432,7 +439,7 @@ void setup_ctx(Ctx& c, bool f64) {
     c.tau = f64 ? 1e-14 : 1e-12;
     c.acc_gram = f64 ? ACC_D : ACC_DF;
     c.acc_proj = f64 ? ACC_D : ACC_F;
-    c.acc_fine = f64 ? ACC_D : ACC_DF;
+    c.acc_fine = f64 ? ACC_D : ACC_F2;
 }
 
 struct Bufs {

@@ -43,6 +43,7 @@ struct AccDv {
     double v;
     __device__ __forceinline__ void init() { v = 0.0; }
     __device__ __forceinline__ void add(double a, double b) { v = fma(a, b, v); }
+    __device__ __forceinline__ void flush() {}
     __device__ __forceinline__ double get() const { return v; }
 };
 struct AccFv {
@@ -51,6 +52,7 @@ struct AccFv {
     float v;
     __device__ __forceinline__ void init() { v = 0.f; }
     __device__ __forceinline__ void add(float a, float b) { v = fmaf(a, b, v); }
+    __device__ __forceinline__ void flush() {}
     __device__ __forceinline__ float get() const { return v; }
 };
 // float32 pair: the product a*b is split exactly into p + e with one FMA, p is added to hi with
@@ -69,7 +71,27 @@ struct AccDFv {
         hi = s;
         lo += err + e;
     }
+    __device__ __forceinline__ void flush() {}
     __device__ __forceinline__ double get() const { return double(hi) + double(lo); }
+};
+// Two levels: float32 FMAs over one shared-memory stage (16 k-steps), then the stage sum is added
+// to a float32 pair with Knuth's two-sum.  The error is a few float32 roundings of the terms
+// instead of growing with the reduction length, at about 1.4 instructions per FMA (the pair above
+// costs 9).  For products of float32 data whose own representation error is one rounding.
+struct AccF2v {
+    using V = float;
+    using P = double;
+    float v, hi, lo;
+    __device__ __forceinline__ void init() { v = 0.f; hi = 0.f; lo = 0.f; }
+    __device__ __forceinline__ void add(float a, float b) { v = fmaf(a, b, v); }
+    __device__ __forceinline__ void flush() {
+        const float s = hi + v;
+        const float bb = s - hi;
+        lo += (hi - (s - bb)) + (v - bb);
+        hi = s;
+        v = 0.f;
+    }
+    __device__ __forceinline__ double get() const { return double(hi) + double(lo) + double(v); }
 };
 
 // 128 x 64 output tile, 8 x 4 outputs per thread (rows tx*4.. and 64+tx*4.., columns ty*4..),
@@ -165,6 +187,10 @@ k_gemm2(int64_t M, int64_t N, int64_t K, int64_t kchunk, LX X, int64_t ldx, LY Y
 #pragma unroll
                 for (int c = 0; c < 4; ++c) acc[r][c].add(a[r], bv[c]);
         }
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[r][c].flush();
         if (more) sstore(buf ^ 1);
         __syncthreads();
         buf ^= 1;
@@ -359,6 +385,93 @@ k_trans_prec(int64_t m, int64_t n, int64_t w, int64_t kchunk, const bf16* __rest
     }
 }
 
+// ---------------------------------------------------------------- panel Gram
+// W = P^T P for a rows x bi panel (bi <= MAXB).  Rows are split evenly across CTAs; thread t < 136
+// owns the t-th 4 x 4 block of the upper triangle of the 16 x 16 block grid (row-major order), so
+// the upper triangle is formed once.  CTA partials go to scratch and k_gram_reduce sums them in
+// CTA order (deterministic) into the symmetric W.
+constexpr int GRAM_THREADS = 160, GRAM_BLOCKS = 136, GRAM_ROWS = 32, GRAM_LD = MAXB + 4;
+
+template <class A, class T>
+__global__ void __launch_bounds__(GRAM_THREADS)
+k_gram(const T* __restrict__ P, int64_t ldp, int64_t rows, int bi, int64_t rows_per,
+       typename A::P* __restrict__ part) {
+    using V = typename A::V;
+    __shared__ __align__(16) V Ps[GRAM_ROWS][GRAM_LD];
+    const int tid = threadIdx.x;
+    const bool active = tid < GRAM_BLOCKS;
+    int gi = 0, gj = 0;
+    {
+        int t = active ? tid : 0;
+        while (t >= 16 - gi) { t -= 16 - gi; ++gi; }
+        gj = gi + t;
+    }
+    const int64_t r_beg = int64_t(blockIdx.x) * rows_per;
+    const int64_t r_end = min(rows, r_beg + rows_per);
+    A acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b].init();
+    for (int64_t r0 = r_beg; r0 < r_end; r0 += GRAM_ROWS) {
+        __syncthreads();
+        for (int e = tid; e < GRAM_ROWS * MAXB; e += GRAM_THREADS) {
+            const int rr = e % GRAM_ROWS, c = e / GRAM_ROWS;
+            const int64_t gr = r0 + rr;
+            Ps[rr][c] = (gr < r_end && c < bi) ? V(P[gr + int64_t(c) * ldp]) : V(0);
+        }
+        __syncthreads();
+        if (active) {
+#pragma unroll 4
+            for (int rr = 0; rr < GRAM_ROWS; ++rr) {
+                V x[4], y[4];
+                Vec4<V>::load(&Ps[rr][gi * 4], x);
+                Vec4<V>::load(&Ps[rr][gj * 4], y);
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) acc[a][b].add(x[a], y[b]);
+            }
+        }
+    }
+    if (!active) return;
+    typename A::P* out = part + int64_t(blockIdx.x) * MAXB * MAXB;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) out[(gi * 4 + a) + (gj * 4 + b) * MAXB] = acc[a][b].get();
+}
+
+template <class P>
+__global__ void k_gram_reduce(const P* __restrict__ part, int G, int bi, double* __restrict__ W) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= MAXB * MAXB) return;
+    const int i = e % MAXB, j = e / MAXB;
+    if (i > j) return;
+    double s = 0.0;
+    if (j < bi)
+        for (int c = 0; c < G; ++c) s += double(part[int64_t(c) * MAXB * MAXB + e]);
+    W[i + j * MAXB] = s;
+    W[j + i * MAXB] = s;
+}
+
+template <class A, class T>
+void launch_gram(cudaStream_t st, const T* P, int64_t ldp, int64_t rows, int bi, double* W,
+                 const GemmScratch& scr) {
+    using PT = typename A::P;
+    const int64_t cap = int64_t(scr.part_bytes / (sizeof(PT) * MAXB * MAXB));
+    int64_t G = std::min<int64_t>(std::min<int64_t>(2LL * num_sms(), cdiv(std::max<int64_t>(rows, 1), 64)), cap);
+    G = std::max<int64_t>(G, 1);
+    const int64_t rows_per = align_up(cdiv(std::max<int64_t>(rows, 1), G), GRAM_ROWS);
+    G = cdiv(std::max<int64_t>(rows, 1), rows_per);
+    if (cap < 1) throw Error{QB_ERR_WORKSPACE, "gram partials"};
+    PT* part = reinterpret_cast<PT*>(scr.part);
+    k_gram<A, T><<<unsigned(G), GRAM_THREADS, 0, st>>>(P, ldp, rows, bi, rows_per, part);
+    QB_LAUNCHED();
+    k_gram_reduce<PT><<<MAXB * MAXB / 256, 256, 0, st>>>(part, int(G), bi, W);
+    QB_LAUNCHED();
+}
+
 }  // namespace
 
 size_t gemm_scratch_bytes(int64_t mn_max) {
@@ -384,6 +497,13 @@ void gemm(cudaStream_t st, bool xt, int64_t M, int64_t N, int64_t K, double alph
         else
             dispatch_x<AccDFv, float>(st, xt, M, N, K, alpha, X, Y, ldy, beta,
                                       reinterpret_cast<float*>(C), ldc, scr);
+    } else if (acc == ACC_F2) {
+        if (c_f64)
+            dispatch_x<AccF2v, float>(st, xt, M, N, K, alpha, X, Y, ldy, beta,
+                                      reinterpret_cast<double*>(C), ldc, scr);
+        else
+            dispatch_x<AccF2v, float>(st, xt, M, N, K, alpha, X, Y, ldy, beta,
+                                      reinterpret_cast<float*>(C), ldc, scr);
     } else {
         if (c_f64)
             dispatch_x<AccFv, float>(st, xt, M, N, K, alpha, X, Y, ldy, beta,
@@ -391,6 +511,19 @@ void gemm(cudaStream_t st, bool xt, int64_t M, int64_t N, int64_t K, double alph
         else
             dispatch_x<AccFv, float>(st, xt, M, N, K, alpha, X, Y, ldy, beta,
                                      reinterpret_cast<float*>(C), ldc, scr);
+    }
+}
+
+void gram(cudaStream_t st, const void* P, int64_t ldp, int64_t rows, int bi, bool f64, Acc acc,
+          double* W, const GemmScratch& scr) {
+    if (bi < 1 || bi > MAXB) throw Error{QB_ERR_INVALID_ARG, "gram width"};
+    if (f64 || acc == ACC_D) {
+        if (!f64) throw Error{QB_ERR_UNSUPPORTED, "ACC_D needs f64 operands"};
+        launch_gram<AccDv>(st, reinterpret_cast<const double*>(P), ldp, rows, bi, W, scr);
+    } else if (acc == ACC_DF) {
+        launch_gram<AccDFv>(st, reinterpret_cast<const float*>(P), ldp, rows, bi, W, scr);
+    } else {
+        launch_gram<AccFv>(st, reinterpret_cast<const float*>(P), ldp, rows, bi, W, scr);
     }
 }
 

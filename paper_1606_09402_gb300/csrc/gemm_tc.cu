@@ -455,8 +455,293 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
     }
 }
 
+// ---------------------------------------------------------------- precise transposed pass
+// D (n x w) = (A_hi [+ A_lo])^T V where V is given exactly by NB bf16 terms (NB = 1: V is
+// bf16-representable; NB = 3: V = V_hi + V_mid + V_lo reproduces any float32 V).  The tensor
+// cores' float32 accumulation is not round-to-nearest and biases long sums toward zero, which the
+// Frobenius indicator cannot absorb (it subtracts ||B_i||^2 from ||A||^2).  So the leading
+// product A_hi V_hi never accumulates in tensor memory: every MMA of it writes a fresh slot of a
+// ring (accumulate flag off) and the epilogue adds the slots in registers with round-to-nearest.
+// The lower-order products (A_lo V_hi, A_hi V_mid: 2^-9 of the leading one; A_hi V_lo,
+// A_lo V_mid: 2^-18) accumulate in tensor memory over PREC_CHUNK k-blocks, where their bias is
+// scaled down by those factors.  A_lo V_lo (2^-27) is dropped.
+constexpr int PREC_CHUNK = 8;
+
+template <int BN, int NA, int NB>
+struct PCfg {
+    static constexpr int A_TILE = BM * BK * 2;
+    static constexpr int B_TILE = BN * BK * 2;
+    static constexpr int STAGE = NA * A_TILE + NB * B_TILE;
+    static constexpr int STAGES = (200 * 1024) / STAGE < 8 ? (200 * 1024) / STAGE : 8;
+    static constexpr int SMEM = STAGES * STAGE + 1024 + 512;
+    static constexpr int NSMALL = (NA == 2 ? 1 : 0) + (NB == 3 ? (NA == 2 ? 3 : 2) : 0);
+    static constexpr int SMALL_COLS = NSMALL > 0 ? 2 * BN : 0;   // double-buffered chain
+    static constexpr int NSLOT = (512 - SMALL_COLS) / BN < 8 ? (512 - SMALL_COLS) / BN : 8;
+    static constexpr int TMEM_COLS = 512;
+};
+
+template <int BN, int NA, int NB>
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+k_tc_prec(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
+          const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1,
+          const __grid_constant__ CUtensorMap mB2, Params p) {
+    using C = PCfg<BN, NA, NB>;
+    static_assert(C::STAGES >= 2, "precise pass needs two stages");
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE);
+    uint64_t* empty = full + C::STAGES;
+    uint64_t* sfull = empty + C::STAGES;   // [2] small-product chain
+    uint64_t* sempty = sfull + 2;          // [2]
+    uint64_t* bfull = sempty + 2;          // [NSLOT] leading-product slots
+    uint64_t* bempty = bfull + C::NSLOT;   // [NSLOT]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bempty + C::NSLOT);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int G = gridDim.x, cta = blockIdx.x;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < C::STAGES; ++s) {
+            mbar_init(full + s, 1);
+            mbar_init(empty + s, 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(sfull + b, 1);
+            mbar_init(sempty + b, 128);
+        }
+        for (int b = 0; b < C::NSLOT; ++b) {
+            mbar_init(bfull + b, 1);
+            mbar_init(bempty + b, 128);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(C::TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t tm_small = tmem;                          // 2 x BN columns
+    const uint32_t tm_big = tmem + uint32_t(C::SMALL_COLS);  // NSLOT x BN columns
+
+    const Sched& sc = p.s;
+    const int64_t units = int64_t(sc.tiles_m) * sc.tiles_n;
+    int64_t beg, end;
+    if (sc.streamk) {
+        beg = sk_begin(units * sc.kb, cta, G);
+        end = sk_begin(units * sc.kb, cta + 1, G);
+    } else {
+        beg = cta;
+        end = units;
+    }
+    auto next_seg = [&](int64_t& pos, Seg& sg, bool& first) -> bool {
+        if (pos >= end) return false;
+        if (sc.streamk) {
+            const int64_t u = pos / sc.kb;
+            const int k0 = int(pos - u * sc.kb);
+            const int64_t rem = end - u * sc.kb;
+            const int k1 = int(rem < sc.kb ? rem : int64_t(sc.kb));
+            const bool whole = (k0 == 0 && k1 == sc.kb);
+            sg = Seg{int(u), k0, k1, whole ? -1 : (first ? 0 : 1)};
+            pos = u * sc.kb + k1;
+        } else {
+            sg = Seg{int(pos), 0, sc.kb, -1};
+            pos += G;
+        }
+        first = false;
+        return true;
+    };
+
+    bool ok = true;
+    if (warp == 0 && lane == 0) {
+        // ---------------------------------------------------------- TMA producer
+        int stage = 0;
+        uint32_t phase = 0;
+        int64_t pos = beg;
+        bool first = true;
+        Seg sg;
+        while (ok && next_seg(pos, sg, first)) {
+            const int r0 = (sg.u / sc.tiles_n) * BM, c0 = (sg.u % sc.tiles_n) * BN;
+            for (int kb = sg.k0; kb < sg.k1 && ok; ++kb) {
+                ok = mbar_wait(empty + stage, phase ^ 1, p.err);
+                if (!ok) break;
+                mbar_expect_tx(full + stage, uint32_t(C::STAGE));
+                unsigned char* st = smem + stage * C::STAGE;
+                const int k = kb * BK;
+                tma_load_2d(st, &mA0, full + stage, r0, k);
+                tma_load_2d(st + C::A_TILE / 2, &mA0, full + stage, r0 + 64, k);
+                if (NA > 1) {
+                    tma_load_2d(st + C::A_TILE, &mA1, full + stage, r0, k);
+                    tma_load_2d(st + C::A_TILE + C::A_TILE / 2, &mA1, full + stage, r0 + 64, k);
+                }
+                unsigned char* sb = st + NA * C::A_TILE;
+                tma_load_2d(sb, &mB0, full + stage, k, c0);
+                if (NB > 1) {
+                    tma_load_2d(sb + C::B_TILE, &mB1, full + stage, k, c0);
+                    tma_load_2d(sb + 2 * C::B_TILE, &mB2, full + stage, k, c0);
+                }
+                if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---------------------------------------------------------- MMA issuer
+        constexpr uint32_t idesc = idesc_bf16(BN, true);
+        int stage = 0;
+        uint32_t phase = 0;
+        int slot = 0;
+        uint32_t slot_ph = 0;   // bit s: phase of slot s
+        int sbuf = 0;
+        uint32_t sph = 0;   // bit b: phase of chain buffer b
+        int64_t pos = beg;
+        bool first = true;
+        Seg sg;
+        while (ok && next_seg(pos, sg, first)) {
+            for (int c0 = sg.k0; c0 < sg.k1 && ok; c0 += PREC_CHUNK) {
+                const int c1 = min(sg.k1, c0 + PREC_CHUNK);
+                const uint32_t acc_s = tm_small + uint32_t(sbuf * BN);
+                if (C::NSMALL > 0) {
+                    ok = mbar_wait(sempty + sbuf, ((sph >> sbuf) & 1u) ^ 1u, p.err);
+                    if (!ok) break;
+                    tc_fence_after();
+                }
+                for (int kb = c0; kb < c1 && ok; ++kb) {
+                    ok = mbar_wait(full + stage, phase, p.err);
+                    if (!ok) break;
+                    tc_fence_after();
+                    const uint32_t sa = smem_u32(smem + stage * C::STAGE);
+                    const uint32_t sbb = sa + NA * C::A_TILE;
+#pragma unroll
+                    for (int kk = 0; kk < BK / UMMA_K; ++kk) {
+                        const uint64_t a_hi = sdesc(sa + kk * (UMMA_K * 128), C::A_TILE / 2, 1024);
+                        const uint64_t a_lo =
+                            sdesc(sa + (NA - 1) * C::A_TILE + kk * (UMMA_K * 128), C::A_TILE / 2, 1024);
+                        const uint64_t v_hi = sdesc(sbb + kk * (UMMA_K * 2), 16, 1024);
+                        const uint64_t v_mid =
+                            sdesc(sbb + (NB > 1 ? 1 : 0) * C::B_TILE + kk * (UMMA_K * 2), 16, 1024);
+                        const uint64_t v_lo =
+                            sdesc(sbb + (NB > 1 ? 2 : 0) * C::B_TILE + kk * (UMMA_K * 2), 16, 1024);
+                        // leading product into a fresh slot
+                        ok = mbar_wait(bempty + slot, ((slot_ph >> slot) & 1u) ^ 1u, p.err);
+                        if (!ok) break;
+                        tc_fence_after();
+                        tc_mma(tm_big + uint32_t(slot * BN), a_hi, v_hi, idesc, 0u);
+                        tc_commit(bfull + slot);
+                        slot_ph ^= 1u << slot;
+                        if (++slot == C::NSLOT) slot = 0;
+                        // lower-order products, smallest first
+                        const uint32_t acc0 = (kb > c0 || kk > 0) ? 1u : 0u;
+                        if (NB == 3) {
+                            tc_mma(acc_s, a_hi, v_lo, idesc, acc0);
+                            if (NA == 2) tc_mma(acc_s, a_lo, v_mid, idesc, 1u);
+                            tc_mma(acc_s, a_hi, v_mid, idesc, 1u);
+                            if (NA == 2) tc_mma(acc_s, a_lo, v_hi, idesc, 1u);
+                        } else if (NA == 2) {
+                            tc_mma(acc_s, a_lo, v_hi, idesc, acc0);
+                        }
+                    }
+                    if (!ok) break;
+                    tc_commit(empty + stage);
+                    if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
+                }
+                if (!ok) break;
+                if (C::NSMALL > 0) {
+                    tc_commit(sfull + sbuf);
+                    sph ^= 1u << sbuf;
+                    sbuf ^= 1;
+                }
+            }
+        }
+    } else if (warp >= 2) {
+        // ---------------------------------------------------------- epilogue
+        const int q = warp & 3;
+        const int row = q * 32 + lane;
+        const uint32_t lane_off = uint32_t(q * 32) << 16;
+        int slot = 0;
+        uint32_t slot_ph = 0;
+        int sbuf = 0;
+        uint32_t sph = 0;   // bit b: phase of chain buffer b
+        int64_t pos = beg;
+        bool first = true;
+        Seg sg;
+        while (ok && next_seg(pos, sg, first)) {
+            const int r0 = (sg.u / sc.tiles_n) * BM, c0 = (sg.u % sc.tiles_n) * BN;
+            const int64_t gr = int64_t(r0) + row;
+            float* pslot = sg.slot >= 0 ? p.part + ((int64_t(cta) * 2 + sg.slot) * BN) * BM : nullptr;
+            float accr[BN];
+#pragma unroll
+            for (int j = 0; j < BN; ++j) accr[j] = 0.f;
+            for (int k0 = sg.k0; k0 < sg.k1 && ok; k0 += PREC_CHUNK) {
+                const int k1 = min(sg.k1, k0 + PREC_CHUNK);
+                for (int kb = k0; kb < k1 && ok; ++kb) {
+                    for (int kk = 0; kk < BK / UMMA_K && ok; ++kk) {
+                        ok = mbar_wait(bfull + slot, (slot_ph >> slot) & 1u, p.err);
+                        if (!ok) break;
+                        tc_fence_after();
+#pragma unroll
+                        for (int cc = 0; cc < BN; cc += 64) {
+                            float v[64];
+                            tmem_ld64(tm_big + lane_off + uint32_t(slot * BN + cc), v);
+#pragma unroll
+                            for (int j = 0; j < 64; ++j) accr[cc + j] += v[j];
+                        }
+                        tc_fence_before();
+                        mbar_arrive(bempty + slot);
+                        slot_ph ^= 1u << slot;
+                        if (++slot == C::NSLOT) slot = 0;
+                    }
+                }
+                if (!ok) break;
+                if (C::NSMALL > 0) {
+                    ok = mbar_wait(sfull + sbuf, (sph >> sbuf) & 1u, p.err);
+                    if (!ok) break;
+                    tc_fence_after();
+#pragma unroll
+                    for (int cc = 0; cc < BN; cc += 64) {
+                        float v[64];
+                        tmem_ld64(tm_small + lane_off + uint32_t(sbuf * BN + cc), v);
+#pragma unroll
+                        for (int j = 0; j < 64; ++j) accr[cc + j] += v[j];
+                    }
+                    tc_fence_before();
+                    mbar_arrive(sempty + sbuf);
+                    sph ^= 1u << sbuf;
+                    sbuf ^= 1;
+                }
+            }
+            if (!ok) break;
+            if (pslot) {
+#pragma unroll
+                for (int j = 0; j < BN; ++j) pslot[int64_t(j) * BM + row] = accr[j];
+            } else if (gr < p.M) {
+#pragma unroll
+                for (int j = 0; j < BN; ++j) {
+                    const int gc = c0 + j;
+                    if (gc < p.N) {
+                        float* o = p.D + gr + int64_t(gc) * p.ldd;
+                        *o = p.beta != 0.f ? fmaf(p.alpha, accr[j], p.beta * *o) : p.alpha * accr[j];
+                    }
+                }
+            }
+        }
+    }
+    __syncwarp();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(C::TMEM_COLS));
+    }
+}
+
 // Stream-K fix-up: D tile of unit u = sum of the partial slots of the CTAs that share it, in CTA
-// order.  A unit covered by one CTA was written directly and is skipped.
+// order.  A unit covered by one CTA was written directly and is skipped.  Grid: (units, BM*BN/256),
+// one output element per thread, so a unit shared by every CTA of the launch is still summed by
+// many CTAs in parallel.
 template <int BN>
 __global__ void k_tc_fixup(Params p, int G) {
     const Sched& sc = p.s;
@@ -471,21 +756,20 @@ __global__ void k_tc_fixup(Params p, int G) {
     };
     const int64_t c_first = owner(f), c_last = owner(l);
     if (c_first == c_last) return;
-    const int r0 = (u / sc.tiles_n) * BM, c0 = (u % sc.tiles_n) * BN;
-    for (int e = threadIdx.x; e < BM * BN; e += blockDim.x) {
-        const int row = e % BM, col = e / BM;
-        float s = 0.f;
-        for (int64_t c = c_first; c <= c_last; ++c) {
-            const int64_t b = sk_begin(total, c, G);
-            const int slot = (b / sc.kb == u) ? 0 : 1;
-            s += p.part[((c * 2 + slot) * BN + col) * BM + row];
-        }
-        const int64_t gr = int64_t(r0) + row;
-        const int gc = c0 + col;
-        if (gr < p.M && gc < p.N) {
-            float* o = p.D + gr + int64_t(gc) * p.ldd;
-            *o = p.beta != 0.f ? fmaf(p.alpha, s, p.beta * *o) : p.alpha * s;
-        }
+    const int e = blockIdx.y * blockDim.x + threadIdx.x;
+    if (e >= BM * BN) return;
+    const int row = e % BM, col = e / BM;
+    float s = 0.f;
+    for (int64_t c = c_first; c <= c_last; ++c) {
+        const int64_t b = sk_begin(total, c, G);
+        const int slot = (b / sc.kb == u) ? 0 : 1;
+        s += p.part[((c * 2 + slot) * BN + col) * BM + row];
+    }
+    const int64_t gr = int64_t((u / sc.tiles_n) * BM) + row;
+    const int gc = (u % sc.tiles_n) * BN + col;
+    if (gr < p.M && gc < p.N) {
+        float* o = p.D + gr + int64_t(gc) * p.ldd;
+        *o = p.beta != 0.f ? fmaf(p.alpha, s, p.beta * *o) : p.alpha * s;
     }
 }
 
@@ -499,6 +783,25 @@ __global__ void k_split_bf16(const float* __restrict__ V, int64_t ldv, int64_t r
     const bf16 h = __float2bfloat16_rn(v);
     hi[i + j * ldo] = h;
     if (lo) lo[i + j * ldo] = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
+// V (rows x w float, col-major ld) -> hi, mid, lo bf16 with hi + mid + lo == V exactly: each term
+// is the bf16 rounding of what the previous ones left (8 significant bits each, and the float32
+// remainders are exact), so three terms carry all 24 bits of a normal float32.
+__global__ void k_split3_bf16(const float* __restrict__ V, int64_t ldv, int64_t rows, int64_t w,
+                              bf16* __restrict__ hi, bf16* __restrict__ mid, bf16* __restrict__ lo,
+                              int64_t ldo) {
+    const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (idx >= rows * w) return;
+    const int64_t i = idx % rows, j = idx / rows;
+    const float v = V[i + j * ldv];
+    const bf16 h = __float2bfloat16_rn(v);
+    const float r1 = v - __bfloat162float(h);
+    const bf16 mdl = __float2bfloat16_rn(r1);
+    const float r2 = r1 - __bfloat162float(mdl);
+    hi[i + j * ldo] = h;
+    mid[i + j * ldo] = mdl;
+    lo[i + j * ldo] = __float2bfloat16_rn(r2);
 }
 
 // ---------------------------------------------------------------- host side
@@ -566,7 +869,8 @@ void run(cudaStream_t st, const CUtensorMap& a0, const CUtensorMap& a1, const CU
     kern<<<G, NUM_THREADS, C::SMEM, st>>>(a0, a1, b0, b1, p);
     QB_LAUNCHED();
     if (p.s.streamk) {
-        k_tc_fixup<BN><<<p.s.tiles_m * p.s.tiles_n, 256, 0, st>>>(p, G);
+        const dim3 grid(unsigned(p.s.tiles_m * p.s.tiles_n), unsigned(BM * BN / 256));
+        k_tc_fixup<BN><<<grid, 256, 0, st>>>(p, G);
         QB_LAUNCHED();
     }
 }
@@ -579,16 +883,40 @@ void run_bn(int bn, cudaStream_t st, const CUtensorMap& a0, const CUtensorMap& a
     else run<256, TRANS, NA, NB>(st, a0, a1, b0, b1, p, G);
 }
 
+template <int BN, int NA, int NB>
+void run_prec(cudaStream_t st, const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& b0,
+              const CUtensorMap& b1, const CUtensorMap& b2, Params p, int G) {
+    using C = PCfg<BN, NA, NB>;
+    auto kern = k_tc_prec<BN, NA, NB>;
+    QB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+    kern<<<G, NUM_THREADS, C::SMEM, st>>>(a0, a1, b0, b1, b2, p);
+    QB_LAUNCHED();
+    if (p.s.streamk) {
+        const dim3 grid(unsigned(p.s.tiles_m * p.s.tiles_n), unsigned(BM * BN / 256));
+        k_tc_fixup<BN><<<grid, 256, 0, st>>>(p, G);
+        QB_LAUNCHED();
+    }
+}
+
+template <int NA, int NB>
+void run_prec_bn(int bn, cudaStream_t st, const CUtensorMap& a0, const CUtensorMap& a1,
+                 const CUtensorMap& b0, const CUtensorMap& b1, const CUtensorMap& b2, Params p,
+                 int G) {
+    if (bn == 64) run_prec<64, NA, NB>(st, a0, a1, b0, b1, b2, p, G);
+    else run_prec<128, NA, NB>(st, a0, a1, b0, b1, b2, p, G);
+}
+
 struct Scratch {
     float* part;
     int* err;
     bf16* vhi;
     bf16* vlo;
+    bf16* vmid;
     size_t part_bytes;
 };
 
 Scratch carve(void* scratch, size_t bytes, int64_t rows, int64_t w) {
-    // [err 256 B][V hi][V lo][partials]
+    // [err 256 B][V hi][V lo][V mid][partials]
     char* p = reinterpret_cast<char*>(scratch);
     Scratch s;
     s.err = reinterpret_cast<int*>(p);
@@ -596,9 +924,10 @@ Scratch carve(void* scratch, size_t bytes, int64_t rows, int64_t w) {
     const size_t vb = size_t(align_up(ldv * w * 2, 256));
     s.vhi = reinterpret_cast<bf16*>(p + 256);
     s.vlo = reinterpret_cast<bf16*>(p + 256 + vb);
-    s.part = reinterpret_cast<float*>(p + 256 + 2 * vb);
-    if (256 + 2 * vb > bytes) throw Error{QB_ERR_WORKSPACE, "tensor-core scratch too small"};
-    s.part_bytes = bytes - 256 - 2 * vb;
+    s.vmid = reinterpret_cast<bf16*>(p + 256 + 2 * vb);
+    s.part = reinterpret_cast<float*>(p + 256 + 3 * vb);
+    if (256 + 3 * vb > bytes) throw Error{QB_ERR_WORKSPACE, "tensor-core scratch too small"};
+    s.part_bytes = bytes - 256 - 3 * vb;
     return s;
 }
 
@@ -642,7 +971,7 @@ size_t tc_scratch_bytes(int64_t m, int64_t n, int64_t w) {
     const int64_t rows = std::max(m, n);
     const size_t vb = size_t(align_up(align_up(rows, 8) * w * 2, 256));
     const size_t part = size_t(MAX_SK_CTAS) * 2 * pick_bn(w, false) * BM * sizeof(float);
-    return 256 + 2 * vb + part;
+    return 256 + 3 * vb + part;
 }
 
 void tc_sketch(cudaStream_t st, const bf16* A, int64_t lda, int64_t m, int64_t n, const bf16* Vt,
@@ -682,19 +1011,22 @@ void tc_trans(cudaStream_t st, const bf16* A_hi, const bf16* A_lo, int64_t lda, 
               int64_t n, const float* V, int64_t ldv, int64_t w, float* Z, int64_t ldz, int mode,
               void* scratch, size_t scratch_bytes) {
     if (n <= 0 || w <= 0) return;
-    if (mode < 1 || mode > 3 || (mode > 1 && !A_lo)) throw Error{QB_ERR_INVALID_ARG, "tc_trans mode"};
+    if (mode < 1 || mode > 3) throw Error{QB_ERR_INVALID_ARG, "tc_trans mode"};
     Scratch s = carve(scratch, scratch_bytes, m, w);
     const int64_t ldo = align_up(m, 8);
-    k_split_bf16<<<unsigned(cdiv(m * w, 256)), 256, 0, st>>>(V, ldv, m, w, s.vhi,
-                                                             mode == 3 ? s.vlo : nullptr, ldo);
+    if (mode == 3) {
+        k_split3_bf16<<<unsigned(cdiv(m * w, 256)), 256, 0, st>>>(V, ldv, m, w, s.vhi, s.vmid,
+                                                                  s.vlo, ldo);
+    } else {
+        k_split_bf16<<<unsigned(cdiv(m * w, 256)), 256, 0, st>>>(V, ldv, m, w, s.vhi, nullptr, ldo);
+    }
     QB_LAUNCHED();
-    const int chunk = pick_chunk(mode, w);
-    const int bn = pick_bn(w, chunk != SINGLE_CHAIN);
+    const int bn = mode == 1 ? pick_bn(w, pick_chunk(1, w) != SINGLE_CHAIN) : (w <= 64 ? 64 : 128);
     Params p{};
     p.M = int(n);
     p.N = int(w);
     p.K = int(m);
-    p.chunk = chunk;
+    p.chunk = pick_chunk(1, w);
     p.alpha = 1.f;
     p.beta = 0.f;
     int G = num_sms();
@@ -713,13 +1045,16 @@ void tc_trans(cudaStream_t st, const bf16* A_hi, const bf16* A_lo, int64_t lda, 
         run_bn<true, 1, 1>(bn, st, a0, a0, b0, b0, p, G);
         return;
     }
-    const CUtensorMap a1 = make_map(A_lo, n, m, lda, 64, BK);
+    const CUtensorMap a1 = A_lo ? make_map(A_lo, n, m, lda, 64, BK) : a0;
     if (mode == 2) {
-        run_bn<true, 2, 1>(bn, st, a0, a1, b0, b0, p, G);
+        if (A_lo) run_prec_bn<2, 1>(bn, st, a0, a1, b0, b0, b0, p, G);
+        else run_prec_bn<1, 1>(bn, st, a0, a0, b0, b0, b0, p, G);
         return;
     }
-    const CUtensorMap b1 = make_map(s.vlo, m, w, ldo, BK, bn);
-    run_bn<true, 2, 2>(bn, st, a0, a1, b0, b1, p, G);
+    const CUtensorMap b1 = make_map(s.vmid, m, w, ldo, BK, bn);
+    const CUtensorMap b2 = make_map(s.vlo, m, w, ldo, BK, bn);
+    if (A_lo) run_prec_bn<2, 3>(bn, st, a0, a1, b0, b1, b2, p, G);
+    else run_prec_bn<1, 3>(bn, st, a0, a0, b0, b1, b2, p, G);
 }
 
 // T (j0 x bw, col-major, ldt) = X^T P for X column-major rows x j0 held as bf16 hi [+ lo] (ldx),

@@ -71,7 +71,9 @@ struct Arena {
 //   xt == true : op(X) = X^T with X column-major K x M (ldx)   ("TN": both operands K-contiguous)
 //   xt == false: op(X) = X   with X column-major M x K (ldx)   ("NN")
 // Accumulation: ACC_D float64, ACC_F float32, ACC_DF float32 pair (exact products, ~48-bit sums).
-enum Acc { ACC_D = 0, ACC_F = 1, ACC_DF = 2 };
+// ACC_D: float64; ACC_F: float32; ACC_DF: float32 pair with exact products (~48 bits);
+// ACC_F2: float32 per 16-step stage, stage sums into a float32 pair
+enum Acc { ACC_D = 0, ACC_F = 1, ACC_DF = 2, ACC_F2 = 3 };
 enum XKind { X_F64 = 0, X_F32 = 1, X_BF16 = 2, X_BF16X2 = 3 };
 
 struct GemmScratch {
@@ -90,6 +92,10 @@ struct XOp {
 void gemm(cudaStream_t st, bool xt, int64_t M, int64_t N, int64_t K, double alpha, XOp X,
           const void* Y, bool y_f64, int64_t ldy, double beta, void* C, bool c_f64, int64_t ldc,
           Acc acc, const GemmScratch& scr);
+// W (MAXB x MAXB, symmetric, zero outside bi x bi) = P^T P for the rows x bi panel P (column-major,
+// float64 when f64 else float32), bi <= MAXB; partials in scr
+void gram(cudaStream_t st, const void* P, int64_t ldp, int64_t rows, int bi, bool f64, Acc acc,
+          double* W, const GemmScratch& scr);
 // bytes of split-K partial storage needed by gemm() for any (M, N) with M * N <= mn_max
 size_t gemm_scratch_bytes(int64_t mn_max);
 // Z (n x w, col-major) = (A_hi + A_lo)^T V in float32 with round-to-nearest sums (SIMT)
@@ -101,8 +107,10 @@ void trans_precise(cudaStream_t st, const bf16* Ahi, const bf16* Alo, int64_t ld
 // BF16 tensor-core passes over dense A (row-major m x n, bf16 hi [+ lo]).
 //   sketch: Y (m x w, col-major, float) = A_hi * V, V given as bf16 column-major n x w
 //   trans : Z (n x w, col-major, float) = A^T V with V float column-major m x w:
-//           mode 1: A_hi^T bf16(V); mode 2: (A_hi + A_lo)^T bf16(V) (exact for bf16-valued V);
-//           mode 3: A_hi^T V_hi + A_lo^T V_hi + A_hi^T V_lo with V = V_hi + V_lo split on the fly.
+//           mode 1: A_hi^T bf16(V), float32 tensor-core accumulation (sketch precision);
+//           mode 2: (A_hi [+ A_lo])^T bf16(V) (exact operand for bf16-valued V);
+//           mode 3: (A_hi [+ A_lo])^T V with V = V_hi + V_mid + V_lo split exactly on the fly.
+//           Modes 2 and 3 sum the leading product per MMA in registers (round-to-nearest).
 bool tc_available();
 // scratch layout starts with a 256-byte error area: word 0 is set when a bounded wait timed out
 size_t tc_scratch_bytes(int64_t m, int64_t n, int64_t w);
@@ -166,10 +174,12 @@ void tri_inv_big(cudaStream_t st, bool f64, const void* R, int64_t ldr, int64_t 
 constexpr int MAXB = 64;
 // W (bi x bi Gram, col-major ld 64) -> R (upper, W = R^T R) and Rinv; breakdown clamps the pivot
 // and sets flags[1]; R_acc <- R * R_acc if R_acc != nullptr (R_acc starts as identity).
-// f32: factor in float32 (the orthonormalisation inside the power scheme, where only the span
-// matters); otherwise float64.
+// CHOL_F64: factor and inverse in float64 (the float64 path); CHOL_F64_INV_F32: float64 factor,
+// float32 inverse (the mixed path, which applies Rinv in float32); CHOL_F32: both in float32 (the
+// orthonormalisation inside the power scheme, where only the span matters).  R may be null.
+enum CholPrec { CHOL_F64 = 0, CHOL_F64_INV_F32 = 1, CHOL_F32 = 2 };
 void chol_rinv(cudaStream_t st, const double* W, int bi, double tau_rel, double* R,
-               double* Rinv, double* R_acc, int* flags, bool f32 = false);
+               double* Rinv, double* R_acc, int* flags, CholPrec prec);
 void set_identity(cudaStream_t st, double* R, int bi);
 // R_out = Rinv of an upper-triangular R (bi x bi)
 void tri_inv(cudaStream_t st, const double* R, int bi, double* Rinv);
