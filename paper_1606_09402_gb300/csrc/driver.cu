@@ -66,7 +66,10 @@ struct Ctx {
     double* rn = nullptr;   // 64 row norms
     double* state = nullptr;  // E, keep, stop, E_prev
     double* part = nullptr;   // 3 x 1024 reduction partials
-    int* flags = nullptr;     // [0] non-finite, [1] breakdown
+    int* flags = nullptr;     // [0] non-finite, [1] breakdown, [2] grid-barrier timeout,
+                              // [4..5] grid-barrier words of the fused CholeskyQR
+    void* coop_scr = nullptr; // fused CholeskyQR partial Grams
+    size_t coop_bytes = 0;
     double tau = 1e-14;       // Cholesky breakdown threshold (relative to max Gram diagonal)
     Acc acc_gram = ACC_D;     // Grams of panels
     Acc acc_proj = ACC_D;     // projections / updates
@@ -123,7 +126,9 @@ struct Ctx {
         rn = ar.get<double>(MAXB);
         state = ar.get<double>(8);
         part = ar.get<double>(3 * 1024);
-        flags = ar.get<int>(4);
+        flags = ar.get<int>(8);
+        coop_scr = ar.get<char>(int64_t(cholqr_coop_scratch_bytes()));
+        coop_bytes = cholqr_coop_scratch_bytes();
     }
     XOp x(const void* p, int64_t ld) const { return XOp{f64 ? X_F64 : X_F32, p, nullptr, ld}; }
 
@@ -152,8 +157,15 @@ struct Ctx {
     // One CholeskyQR pass: W = P^T P (float64 or float32-pair accumulation), W = R^T R,
     // P <- P R^-1; with acc_r the factor's inverse is kept in Rchain (in order) for the B_i formula.  sketch: the basis only has to span the same space
     // (the power scheme), so the Gram is accumulated and factored in float32.
+    // Fused float32 CholeskyQR passes for the power-scheme orthonormalisation (one launch).
+    bool coop(void* P, int64_t ld, int64_t rows, int bi, int passes) {
+        return cholqr_coop(st, reinterpret_cast<float*>(P), ld, rows, bi, passes, 1e-10, nullptr,
+                           coop_scr, coop_bytes, reinterpret_cast<unsigned*>(flags + 4), flags,
+                           flags + 2);
+    }
     void cholqr(void* P, int64_t ld, int64_t rows, int bi, bool acc_r, bool sketch = false) {
         const bool fast = sketch && !f64;
+        if (fast && !acc_r && coop(P, ld, rows, bi, 1)) return;
         gram(st, P, ld, rows, bi, f64, f64 ? ACC_D : (fast ? ACC_F : acc_gram), W, scr);
         double* ri = Rinv;
         if (acc_r && nchain < 4) ri = Rchain + size_t(nchain++) * MAXB * MAXB;
@@ -170,6 +182,7 @@ struct Ctx {
     // orth(P): CholeskyQR2 (two passes); with acc_r the factors' inverses go to Rchain.
     void cholqr2(void* P, int64_t ld, int64_t rows, int bi, bool acc_r, bool sketch = false) {
         Scope sc(*this, sketch ? PH_ORTHW : PH_CHOLQR);
+        if (sketch && !f64 && !acc_r && coop(P, ld, rows, bi, 2)) return;
         cholqr(P, ld, rows, bi, acc_r, sketch);
         cholqr(P, ld, rows, bi, acc_r, sketch);
     }
@@ -664,7 +677,7 @@ int32_t run_common(AOp& A, const qb_opts* opts, bool fp, void* Q, int64_t ldq, v
     ar.cap = ws_bytes;
     const int64_t l0 = launches_total();
     reserve_all(ar, c, A, p, fp, bf);
-    QB_CUDA(cudaMemsetAsync(c.flags, 0, 4 * sizeof(int), c.st));
+    QB_CUDA(cudaMemsetAsync(c.flags, 0, 8 * sizeof(int), c.st));
     A.prepare(c);
     const double normA2 = A.norm2(c);
     int hf[4];
@@ -705,11 +718,11 @@ int32_t run_common(AOp& A, const qb_opts* opts, bool fp, void* Q, int64_t ldq, v
     if (fp) run_fp(c, A, p, o, bf, Q, ldq, B, ldb, eps2, out);
     else run_ei(c, A, p, o, bf, Q, ldq, B, ldb, eps2, out);
     c.flush_profile();
-    if (A.timed_out(c)) {
+    c.read_flags(hf);
+    if (A.timed_out(c) || hf[2]) {
         fill_info(0);
         return QB_ERR_TIMEOUT;
     }
-    c.read_flags(hf);
     int32_t bits = 0;
     if (hf[1]) bits |= QB_BIT_BREAKDOWN;
     const double floor = std::sqrt(4.0 * u_work / THM3_DELTA) * std::sqrt(normA2);
@@ -1040,7 +1053,7 @@ int32_t qb_fixed_rank_fwd(const qb_dense* A, int64_t k, uint64_t seed, int32_t p
         DenseOp op(*A);
         FixedBufs f;
         fixed_reserve(ar, c, op, k, f, false);
-        QB_CUDA(cudaMemsetAsync(c.flags, 0, 4 * sizeof(int), c.st));
+        QB_CUDA(cudaMemsetAsync(c.flags, 0, 8 * sizeof(int), c.st));
         op.prepare(c);
         fixed_fwd(c, op, k, seed, f, Q, ldq, B, ldb, R, ldr);
         if (op.timed_out(c)) return int32_t(QB_ERR_TIMEOUT);

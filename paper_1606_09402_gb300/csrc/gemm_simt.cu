@@ -442,17 +442,28 @@ k_gram(const T* __restrict__ P, int64_t ldp, int64_t rows, int bi, int64_t rows_
         for (int b = 0; b < 4; ++b) out[(gi * 4 + a) + (gj * 4 + b) * MAXB] = acc[a][b].get();
 }
 
+// One CTA per 32 Gram entries: warp w sums the partials w, w + 8, ... of its 32 entries (lane =
+// entry, coalesced), then the 8 warp sums are added in warp order (deterministic).
 template <class P>
-__global__ void k_gram_reduce(const P* __restrict__ part, int G, int bi, double* __restrict__ W) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= MAXB * MAXB) return;
+__global__ void __launch_bounds__(256) k_gram_reduce(const P* __restrict__ part, int G, int bi,
+                                                     double* __restrict__ W) {
+    __shared__ double sh[8][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int e = blockIdx.x * 32 + lane;
     const int i = e % MAXB, j = e / MAXB;
-    if (i > j) return;
+    const bool need = i <= j && j < bi;
     double s = 0.0;
-    if (j < bi)
-        for (int c = 0; c < G; ++c) s += double(part[int64_t(c) * MAXB * MAXB + e]);
-    W[i + j * MAXB] = s;
-    W[j + i * MAXB] = s;
+    if (need)
+        for (int c = warp; c < G; c += 8) s += double(part[int64_t(c) * MAXB * MAXB + e]);
+    sh[warp][lane] = s;
+    __syncthreads();
+    if (warp == 0 && i <= j) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) t += sh[w][lane];
+        W[i + j * MAXB] = t;
+        W[j + i * MAXB] = t;
+    }
 }
 
 template <class A, class T>
@@ -468,7 +479,7 @@ void launch_gram(cudaStream_t st, const T* P, int64_t ldp, int64_t rows, int bi,
     PT* part = reinterpret_cast<PT*>(scr.part);
     k_gram<A, T><<<unsigned(G), GRAM_THREADS, 0, st>>>(P, ldp, rows, bi, rows_per, part);
     QB_LAUNCHED();
-    k_gram_reduce<PT><<<MAXB * MAXB / 256, 256, 0, st>>>(part, int(G), bi, W);
+    k_gram_reduce<PT><<<MAXB * MAXB / 32, 256, 0, st>>>(part, int(G), bi, W);
     QB_LAUNCHED();
 }
 

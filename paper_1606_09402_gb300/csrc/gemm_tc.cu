@@ -741,30 +741,42 @@ k_tc_prec(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
 // Stream-K fix-up: D tile of unit u = sum of the partial slots of the CTAs that share it, in CTA
 // order.  A unit covered by one CTA was written directly and is skipped.  Grid: (units, BM*BN/256),
 // one output element per thread, so a unit shared by every CTA of the launch is still summed by
-// many CTAs in parallel.
+// many CTAs in parallel; the slot offsets are worked out once per CTA.
 template <int BN>
-__global__ void k_tc_fixup(Params p, int G) {
+__global__ void __launch_bounds__(256) k_tc_fixup(Params p, int G) {
+    __shared__ int64_t base[MAX_SK_CTAS];
+    __shared__ int64_t first_s;
+    __shared__ int count_s;
     const Sched& sc = p.s;
     const int u = blockIdx.x;
     const int64_t total = int64_t(sc.tiles_m) * sc.tiles_n * sc.kb;
-    const int64_t f = int64_t(u) * sc.kb, l = f + sc.kb - 1;
-    auto owner = [&](int64_t x) {
-        int64_t c = (x * G) / total;
-        while (c + 1 < G && sk_begin(total, c + 1, G) <= x) ++c;
-        while (c > 0 && sk_begin(total, c, G) > x) --c;
-        return c;
-    };
-    const int64_t c_first = owner(f), c_last = owner(l);
-    if (c_first == c_last) return;
+    if (threadIdx.x == 0) {
+        auto owner = [&](int64_t x) {
+            int64_t c = (x * G) / total;
+            while (c + 1 < G && sk_begin(total, c + 1, G) <= x) ++c;
+            while (c > 0 && sk_begin(total, c, G) > x) --c;
+            return c;
+        };
+        const int64_t f = int64_t(u) * sc.kb;
+        const int64_t c_first = owner(f), c_last = owner(f + sc.kb - 1);
+        first_s = c_first;
+        count_s = c_first == c_last ? 0 : int(c_last - c_first + 1);
+    }
+    __syncthreads();
+    const int count = count_s;
+    if (count == 0) return;
+    for (int t = threadIdx.x; t < count; t += blockDim.x) {
+        const int64_t c = first_s + t;
+        const int slot = (sk_begin(total, c, G) / sc.kb == u) ? 0 : 1;
+        base[t] = (c * 2 + slot) * BN * BM;
+    }
+    __syncthreads();
     const int e = blockIdx.y * blockDim.x + threadIdx.x;
     if (e >= BM * BN) return;
     const int row = e % BM, col = e / BM;
+    const float* pp = p.part + int64_t(col) * BM + row;
     float s = 0.f;
-    for (int64_t c = c_first; c <= c_last; ++c) {
-        const int64_t b = sk_begin(total, c, G);
-        const int slot = (b / sc.kb == u) ? 0 : 1;
-        s += p.part[((c * 2 + slot) * BN + col) * BM + row];
-    }
+    for (int t = 0; t < count; ++t) s += pp[base[t]];
     const int64_t gr = int64_t((u / sc.tiles_n) * BM) + row;
     const int gc = (u % sc.tiles_n) * BN + col;
     if (gr < p.M && gc < p.N) {

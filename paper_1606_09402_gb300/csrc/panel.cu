@@ -8,122 +8,140 @@ namespace {
 
 constexpr int LDS = MAXB + 1;
 
-// One CTA of 256 threads: W = R^T R (upper R) factored in TF, Rinv = R^-1 formed in TI, optional
-// R_acc <- R R_acc (in TF).
+// Cholesky of a bi x bi Gram W (bi <= 64) by one CTA of 512 threads: W = R^T R (upper R) factored
+// in TF, R^-1 formed in TI.
 // Breakdown: a pivot d <= tau_rel * max_diag(W) (or NaN) is replaced by tau_rel * max_diag (or
 // the smallest normal number) and flags[1] is raised; the column it produces has norm <= 1.
 //
-// Factorisation: right-looking, one barrier per step.  Thread t owns column c = t % 64 of rows
-// 16 (t / 64) .. 16 (t / 64) + 15 of the trailing matrix in registers; step j subtracts
-// W[j][a] W[j][c] / d_j (the unnormalised row j, d_j its pivot) and publishes the finished row
-// j + 1 to shared memory, the owner of its diagonal also its pivot and 1 / pivot, for the next
-// step.  Inverse: each warp solves R x = e_c for 8 columns by back substitution, rows spread over
-// the lanes, x_l broadcast by shuffle (no barriers).
-// Dynamic shared memory: two MAXB x LDS arrays of TF (S: rows of W, then R; X: old R_acc).
+// One elimination sweep gives both factors: W = L D L^T (L unit lower), R = D^1/2 L^T and
+// R^-1 = L^-T D^-1/2.  Step j removes row j from the rows a > j of [W | I] (Gaussian elimination
+// without pivoting, multipliers m_a = W[j][a] / d_j read from the symmetric upper part), so the
+// trailing upper triangle becomes the Schur complement and the right half becomes L^-1.  Thread t
+// owns column t % 64 of rows 8 (t / 64) .. 8 (t / 64) + 7 of both halves in registers; the finished
+// row j + 1 of each half (and its pivot) is published to shared memory for the next step, one
+// barrier per step.  Rows of a warp with no work in a step are skipped with warp-uniform branches.
+constexpr int CLD = MAXB + 4;          // shared row stride: rows stay 16-byte aligned
+constexpr int CHOL_THREADS = 512;
+
 template <class TF, class TI>
-__global__ void __launch_bounds__(256)
-k_chol(const double* __restrict__ W, int bi, double tau_rel, double* __restrict__ Rout,
-       double* __restrict__ Rinv, double* __restrict__ Racc, int* flags) {
-    using T = TF;
-    extern __shared__ double smem[];
-    T (*S)[LDS] = reinterpret_cast<T (*)[LDS]>(smem);
-    T (*X)[LDS] = reinterpret_cast<T (*)[LDS]>(reinterpret_cast<T*>(smem) + MAXB * LDS);
-    __shared__ T dpiv[MAXB];
-    __shared__ T invd[MAXB];
-    __shared__ T idiag[MAXB];
-    __shared__ T dmax_s;
+struct CholShared {
+    TF (*S)[CLD];    // rows of W, then the rows W'[j][.] of the elimination
+    TI (*Li)[CLD];   // rows of L^-1 as they are finished
+    TF* dpiv;        // [MAXB] pivots d_j
+    TF* invd;        // [MAXB] 1 / d_j
+    TF* idiag;       // [MAXB] 1 / sqrt(d_j)
+    TF* dmax;        // [1]
+};
+
+// load(i, j) returns W[i][j] for i <= j < bi.  On return (after a barrier) S rows hold W'[j][.],
+// dpiv / idiag the pivots, and l[k] = L^-1[8 (t / 64) + k][t % 64].
+template <class TF, class TI, class Load>
+__device__ void chol_core(int bi, double tau_rel, int* flags, Load load, CholShared<TF, TI> sh,
+                          TI (&l)[8]) {
+    TF (*S)[CLD] = sh.S;
+    TI (*Li)[CLD] = sh.Li;
     const int tid = threadIdx.x;
     const int c = tid & (MAXB - 1);
-    const int a0 = (tid >> 6) * 16;
-    T s[16];
+    const int a0 = (tid >> 6) * 8;
+    const int cmin = c & 32, cmax = cmin + 31;   // columns of this warp
+    TF s[8];
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
+    for (int k = 0; k < 8; ++k) {
         const int a = a0 + k;
-        s[k] = (a <= c && c < bi) ? T(W[a + c * MAXB]) : T(0);
+        s[k] = (a <= c && c < bi) ? TF(load(a, c)) : TF(0);
+        l[k] = (a == c && a < bi) ? TI(1) : TI(0);
         S[a][c] = s[k];
+        Li[a][c] = l[k];
     }
     __syncthreads();
     if (tid < 32) {
-        T m = T(0);
+        TF m = TF(0);
         for (int i = tid; i < bi; i += 32) m = S[i][i] > m ? S[i][i] : m;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            const T v = __shfl_xor_sync(0xffffffffu, m, o);
+            const TF v = __shfl_xor_sync(0xffffffffu, m, o);
             m = v > m ? v : m;
         }
-        if (tid == 0) dmax_s = m;
+        if (tid == 0) sh.dmax[0] = m;
     }
     __syncthreads();
-    const T dmax = dmax_s;
-    const T tiny = sizeof(T) == 8 ? T(2.2250738585072014e-308) : T(1.1754943508222875e-38);
-    const T floor_piv = T(tau_rel) * dmax > tiny ? T(tau_rel) * dmax : tiny;
+    const TF dmax = sh.dmax[0];
+    const TF tiny = sizeof(TF) == 8 ? TF(2.2250738585072014e-308) : TF(1.1754943508222875e-38);
+    const TF floor_piv = TF(tau_rel) * dmax > tiny ? TF(tau_rel) * dmax : tiny;
     // pivot of row j from its (updated) diagonal value; called by one thread
-    auto pivot = [&](int j, T d) {
-        if (!(d > T(tau_rel) * dmax)) {
+    auto pivot = [&](int j, TF d) {
+        if (!(d > TF(tau_rel) * dmax)) {
             d = floor_piv;
-            atomicOr(flags + 1, 1);
+            if (flags) atomicOr(flags + 1, 1);
         }
-        dpiv[j] = d;
-        invd[j] = T(1) / d;
+        sh.dpiv[j] = d;
+        sh.invd[j] = TF(1) / d;
     };
     if (tid == 0 && bi > 0) pivot(0, S[0][0]);
     __syncthreads();
     for (int j = 0; j < bi; ++j) {
-        const T t = S[j][c] * invd[j];
+        const TF inv = sh.invd[j];
+        const TF t = S[j][c] * inv;
+        const TI u = Li[j][c];
+        const TI inv_i = TI(inv);
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
+        for (int k = 0; k < 8; ++k) {
             const int a = a0 + k;
-            if (a > j && a <= c && c < bi) s[k] = fma(-S[j][a], t, s[k]);
-            if (a == j + 1 && a <= c) {
-                S[a][c] = s[k];
-                if (a == c && a < bi) pivot(a, s[k]);
+            if (a > j) {
+                const TF w = S[j][a];
+                if (a <= cmax && a <= c && c < bi) s[k] = fma(-w, t, s[k]);
+                if (j >= cmin && c <= j) l[k] = fma(-(TI(w) * inv_i), u, l[k]);
+                if (a == j + 1) {
+                    S[a][c] = s[k];
+                    Li[a][c] = l[k];
+                    if (a == c && a < bi) pivot(a, s[k]);
+                }
             }
         }
         __syncthreads();
     }
-    // R in place: R[j][j] = sqrt(d_j), R[j][c] = W'[j][c] / sqrt(d_j)
-    if (tid < bi) idiag[tid] = T(1) / sqrt(dpiv[tid]);
+    if (tid < bi) sh.idiag[tid] = TF(1) / sqrt(sh.dpiv[tid]);
     __syncthreads();
+}
+
+// Standalone: Rinv = R^-1 (and R, R_acc <- R R_acc when given), all MAXB x MAXB column-major.
+template <class TF, class TI>
+__global__ void __launch_bounds__(CHOL_THREADS)
+k_chol(const double* __restrict__ W, int bi, double tau_rel, double* __restrict__ Rout,
+       double* __restrict__ Rinv, double* __restrict__ Racc, int* flags) {
+    extern __shared__ __align__(16) unsigned char chol_smem[];
+    TF (*S)[CLD] = reinterpret_cast<TF (*)[CLD]>(chol_smem);
+    TF (*X)[CLD] = reinterpret_cast<TF (*)[CLD]>(chol_smem + sizeof(TF) * MAXB * CLD);
+    TI (*Li)[CLD] = reinterpret_cast<TI (*)[CLD]>(chol_smem + 2 * sizeof(TF) * MAXB * CLD);
+    __shared__ TF dpiv[MAXB];
+    __shared__ TF invd[MAXB];
+    __shared__ TF idiag[MAXB];
+    __shared__ TF dmax_s;
+    const int tid = threadIdx.x;
+    const int c = tid & (MAXB - 1);
+    const int a0 = (tid >> 6) * 8;
+    TI l[8];
+    chol_core<TF, TI>(bi, tau_rel, flags, [&](int i, int j) { return W[i + j * MAXB]; },
+                      CholShared<TF, TI>{S, Li, dpiv, invd, idiag, &dmax_s}, l);
+    if (Rinv) {
+        // R^-1[c][a] = L^-1[a][c] / sqrt(d_a)
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
+        for (int k = 0; k < 8; ++k) {
+            const int a = a0 + k;
+            Rinv[c + a * MAXB] = (a < bi && c < bi) ? double(l[k] * TI(idiag[a])) : 0.0;
+        }
+    }
+    if (!Rout && !Racc) return;
+    // R in place: R[j][j] = sqrt(d_j), R[j][c] = W'[j][c] / sqrt(d_j); the lower part is zero
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
         const int a = a0 + k;
         if (a < bi && c < bi && a <= c) S[a][c] = a == c ? sqrt(dpiv[a]) : S[a][c] * idiag[a];
     }
     __syncthreads();
-    // inverse in TI: warp w takes columns 8w .. 8w + 7; lane holds rows lane, lane + 32
-    {
-        const int warp = tid >> 5, lane = tid & 31;
-        TI b[8][2];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int col = warp * 8 + q;
-            b[q][0] = (lane == col && col < bi) ? TI(1) : TI(0);
-            b[q][1] = (lane + 32 == col && col < bi) ? TI(1) : TI(0);
-        }
-        const int lmax = min(bi - 1, warp * 8 + 7);   // x_l = 0 for l above the warp's columns
-        for (int l = lmax; l >= 0; --l) {
-            const TI r0 = TI(S[lane][l]), r1 = TI(S[lane + 32][l]);
-            const TI il = TI(idiag[l]);
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const TI x = __shfl_sync(0xffffffffu, l < 32 ? b[q][0] : b[q][1], l & 31) * il;
-                b[q][0] = lane < l ? fma(-r0, x, b[q][0]) : (lane == l ? x : b[q][0]);
-                if (l >= 32)
-                    b[q][1] = lane + 32 < l ? fma(-r1, x, b[q][1]) : (lane + 32 == l ? x : b[q][1]);
-            }
-        }
-        if (Rinv) {
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int col = warp * 8 + q;
-                Rinv[lane + col * MAXB] = double(b[q][0]);
-                Rinv[lane + 32 + col * MAXB] = double(b[q][1]);
-            }
-        }
-    }
     if (Rout) {
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
+        for (int k = 0; k < 8; ++k) {
             const int a = a0 + k;
             Rout[a + c * MAXB] = (a <= c && c < bi) ? double(S[a][c]) : 0.0;
         }
@@ -131,17 +149,219 @@ k_chol(const double* __restrict__ W, int bi, double tau_rel, double* __restrict_
     if (Racc) {
         // Racc <- R * Racc (both upper triangular); X holds the old Racc
         for (int e = tid; e < MAXB * MAXB; e += blockDim.x) {
-            const int i = e % MAXB, j = e / MAXB;
-            X[i][j] = T(Racc[i + j * MAXB]);
+            const int i = e % MAXB, jj = e / MAXB;
+            X[i][jj] = TF(Racc[i + jj * MAXB]);
         }
         __syncthreads();
         for (int e = tid; e < MAXB * MAXB; e += blockDim.x) {
-            const int i = e % MAXB, j = e / MAXB;
-            T acc = T(0);
-            if (i < bi && j < bi)
-                for (int l = i; l <= j; ++l) acc = fma(S[i][l], X[l][j], acc);
-            Racc[i + j * MAXB] = double(acc);
+            const int i = e % MAXB, jj = e / MAXB;
+            TF acc = TF(0);
+            if (i < bi && jj < bi)
+                for (int q = i; q <= jj; ++q) acc = fma(S[i][q], X[q][jj], acc);
+            Racc[i + jj * MAXB] = double(acc);
         }
+    }
+}
+
+// ---------------------------------------------------------------- fused CholeskyQR (float32 panel)
+// One cooperative launch runs `passes` CholeskyQR passes on a float32 rows x bi panel: every CTA
+// keeps its slice of rows in shared memory for the whole call, forms the partial Gram of the slice,
+// the CTAs sum the partials (each CTA an equal share of the entries, in CTA order), every CTA
+// factors the 64 x 64 Gram itself (chol_core; the same arithmetic in every CTA, so the same R),
+// and applies R^-1 to its rows.  The panel is read and written once.  Grid-wide barriers use a
+// global arrive counter and generation word; every wait is bounded and a timeout sets err.
+constexpr int COOP_THREADS = 512;
+constexpr int COOP_ROWS = 512;      // rows per CTA held in shared memory
+constexpr int COOP_MAX_CTAS = 256;
+constexpr int PLD = MAXB + 1;       // shared row stride of the panel slice
+constexpr uint64_t COOP_WAIT_NS = 2000000000ull;
+
+struct CoopArgs {
+    float* P;
+    int64_t ldp, rows, rows_per;
+    int bi, passes;
+    double tau;
+    double* rinv_out;   // passes x (MAXB x MAXB) or null
+    float* part;        // gridDim.x x (MAXB x MAXB) partial Grams
+    float* wred;        // MAXB x MAXB summed Gram
+    unsigned* bar;      // [0] arrivals, [1] generation
+    int* flags;         // flags[1]: breakdown
+    int* err;           // set when a grid barrier wait timed out
+};
+
+__device__ __forceinline__ uint64_t coop_timer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier of a cooperative launch; false when a wait ran out (err set) or err was set.
+__device__ bool coop_sync(unsigned* bar, int* err) {
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = *reinterpret_cast<volatile int*>(err) == 0;
+        if (ok) {
+            volatile unsigned* gen = bar + 1;
+            const unsigned g = *gen;
+            __threadfence();
+            if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+                atomicExch(bar, 0u);
+                __threadfence();
+                atomicAdd(bar + 1, 1u);
+            } else {
+                const uint64_t t0 = coop_timer();
+                while (*gen == g) {
+                    if (coop_timer() - t0 > COOP_WAIT_NS ||
+                        *reinterpret_cast<volatile int*>(err) != 0) {
+                        atomicOr(err, 1);
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            __threadfence();
+        }
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+__global__ void __launch_bounds__(COOP_THREADS, 1) k_cholqr_coop(CoopArgs p) {
+    extern __shared__ __align__(16) unsigned char coop_smem[];
+    float (*Ps)[PLD] = reinterpret_cast<float (*)[PLD]>(coop_smem);
+    unsigned char* rest = coop_smem + sizeof(float) * COOP_ROWS * PLD;
+    float (*S)[CLD] = reinterpret_cast<float (*)[CLD]>(rest);
+    float (*Li)[CLD] = reinterpret_cast<float (*)[CLD]>(rest + sizeof(float) * MAXB * CLD);
+    float (*Rs)[CLD] = reinterpret_cast<float (*)[CLD]>(rest + 2 * sizeof(float) * MAXB * CLD);
+    float* scratch = reinterpret_cast<float*>(rest);   // Gram combine space (S and Li, 2 x 17 KB)
+    __shared__ float dpiv[MAXB], invd[MAXB], idiag[MAXB], dmax_s;
+    __shared__ double red[16][32];
+    const int tid = threadIdx.x;
+    const int G = gridDim.x, cta = blockIdx.x;
+    const int bi = p.bi;
+    const int64_t r0 = int64_t(cta) * p.rows_per;
+    const int64_t r_end = p.rows < r0 + p.rows_per ? p.rows : r0 + p.rows_per;
+    const int nr = r_end > r0 ? int(r_end - r0) : 0;
+    for (int e = tid; e < nr * MAXB; e += COOP_THREADS) {
+        const int r = e % nr, col = e / nr;
+        Ps[r][col] = col < bi ? p.P[r0 + r + int64_t(col) * p.ldp] : 0.f;
+    }
+    // Gram block of thread t < 3 * 136: the (t % 136)-th 4 x 4 block of the upper triangle over
+    // rows t / 136, t / 136 + 3, ...
+    const int blk = tid % 136, grp = tid / 136;
+    int gi = 0, gj = 0;
+    {
+        int t = blk;
+        while (t >= 16 - gi) { t -= 16 - gi; ++gi; }
+        gj = gi + t;
+    }
+    for (int pass = 0; pass < p.passes; ++pass) {
+        __syncthreads();
+        // ---- partial Gram of this slice
+        if (grp < 3) {
+            float acc[4][4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+            for (int r = grp; r < nr; r += 3) {
+                float x[4], y[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    x[q] = Ps[r][gi * 4 + q];
+                    y[q] = Ps[r][gj * 4 + q];
+                }
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(x[a], y[b], acc[a][b]);
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) scratch[(grp * 136 + blk) * 16 + a * 4 + b] = acc[a][b];
+        }
+        __syncthreads();
+        if (tid < 136) {
+            float* out = p.part + int64_t(cta) * MAXB * MAXB;
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const float v = scratch[blk * 16 + q] + scratch[(136 + blk) * 16 + q] +
+                                scratch[(272 + blk) * 16 + q];
+                out[(gi * 4 + q / 4) + (gj * 4 + q % 4) * MAXB] = v;
+            }
+        }
+        if (!coop_sync(p.bar, p.err)) return;
+        // ---- sum the partials: this CTA owns entries [e0, e0 + 32 * nchunk)
+        {
+            const int per = (MAXB * MAXB + G - 1) / G;
+            const int e0 = cta * per, e1 = min(MAXB * MAXB, e0 + per);
+            const int lane = tid & 31, sub = tid >> 5;   // 16 subsets of the partials
+            for (int eb = e0; eb < e1; eb += 32) {
+                const int e = eb + lane;
+                double v = 0.0;
+                if (e < e1 && e % MAXB <= e / MAXB)
+                    for (int q = sub; q < G; q += 16)
+                        v += double(__ldcg(p.part + int64_t(q) * MAXB * MAXB + e));
+                red[sub][lane] = v;
+                __syncthreads();
+                if (sub == 0 && e < e1) {
+                    double t = 0.0;
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) t += red[q][lane];
+                    p.wred[e] = float(t);
+                }
+                __syncthreads();
+            }
+        }
+        if (!coop_sync(p.bar, p.err)) return;
+        // ---- every CTA factors the summed Gram
+        float l[8];
+        chol_core<float, float>(bi, p.tau, cta == 0 ? p.flags : nullptr,
+                                [&](int i, int j) { return __ldcg(p.wred + i + j * MAXB); },
+                                CholShared<float, float>{S, Li, dpiv, invd, idiag, &dmax_s}, l);
+        {
+            const int c = tid & (MAXB - 1), a0 = (tid >> 6) * 8;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int a = a0 + k;
+                const float v = (a < bi && c < bi) ? l[k] * idiag[a] : 0.f;
+                Rs[c][a] = v;                                   // R^-1[c][a]
+                if (cta == 0 && p.rinv_out) p.rinv_out[int64_t(pass) * MAXB * MAXB + c + a * MAXB] = v;
+            }
+        }
+        __syncthreads();
+        // ---- rows <- rows * R^-1, 128 rows at a time (thread: one row, 16 columns)
+        {
+            const int i = tid & 127, c0 = (tid >> 7) * 16;
+            for (int rb = 0; rb < nr; rb += 128) {
+                const int r = rb + i;
+                float acc[16];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) acc[q] = 0.f;
+                if (r < nr) {
+                    for (int q2 = 0; q2 < bi; ++q2) {
+                        const float v = Ps[r][q2];
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) acc[q] = fmaf(v, Rs[q2][c0 + q], acc[q]);
+                    }
+                }
+                __syncthreads();
+                if (r < nr) {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) Ps[r][c0 + q] = acc[q];
+                }
+                __syncthreads();
+            }
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < nr * MAXB; e += COOP_THREADS) {
+        const int r = e % nr, col = e / nr;
+        if (col < bi) p.P[r0 + r + int64_t(col) * p.ldp] = Ps[r][col];
     }
 }
 
@@ -271,7 +491,11 @@ __global__ void k_indicator(double* state, const double* rn, int rows, double ep
 
 }  // namespace
 
-constexpr size_t CHOL_SMEM = sizeof(double) * 2 * MAXB * LDS;
+template <class TF, class TI>
+constexpr size_t chol_smem() {
+    return (2 * sizeof(TF) + sizeof(TI)) * MAXB * CLD;
+}
+constexpr size_t TRI_SMEM = sizeof(double) * 2 * MAXB * LDS;
 
 template <class K>
 void allow_smem(K kernel, size_t bytes) {
@@ -282,20 +506,72 @@ void allow_smem(K kernel, size_t bytes) {
 void chol_rinv(cudaStream_t st, const double* W, int bi, double tau_rel, double* R, double* Rinv,
                double* R_acc, int* flags, CholPrec prec) {
     switch (prec) {
-        case CHOL_F64:
-            allow_smem(k_chol<double, double>, CHOL_SMEM);
-            k_chol<double, double><<<1, 256, CHOL_SMEM, st>>>(W, bi, tau_rel, R, Rinv, R_acc, flags);
+        case CHOL_F64: {
+            constexpr size_t sm = chol_smem<double, double>();
+            allow_smem(k_chol<double, double>, sm);
+            k_chol<double, double><<<1, CHOL_THREADS, sm, st>>>(W, bi, tau_rel, R, Rinv, R_acc, flags);
             break;
-        case CHOL_F64_INV_F32:
-            allow_smem(k_chol<double, float>, CHOL_SMEM);
-            k_chol<double, float><<<1, 256, CHOL_SMEM, st>>>(W, bi, tau_rel, R, Rinv, R_acc, flags);
+        }
+        case CHOL_F64_INV_F32: {
+            constexpr size_t sm = chol_smem<double, float>();
+            allow_smem(k_chol<double, float>, sm);
+            k_chol<double, float><<<1, CHOL_THREADS, sm, st>>>(W, bi, tau_rel, R, Rinv, R_acc, flags);
             break;
-        default:
-            allow_smem(k_chol<float, float>, CHOL_SMEM);
-            k_chol<float, float><<<1, 256, CHOL_SMEM, st>>>(W, bi, tau_rel, R, Rinv, R_acc, flags);
+        }
+        default: {
+            constexpr size_t sm = chol_smem<float, float>();
+            allow_smem(k_chol<float, float>, sm);
+            k_chol<float, float><<<1, CHOL_THREADS, sm, st>>>(W, bi, tau_rel, R, Rinv, R_acc, flags);
             break;
+        }
     }
     QB_LAUNCHED();
+}
+
+size_t cholqr_coop_scratch_bytes() {
+    return size_t(COOP_MAX_CTAS) * MAXB * MAXB * sizeof(float) + MAXB * MAXB * sizeof(float) + 256;
+}
+
+bool cholqr_coop(cudaStream_t st, float* P, int64_t ldp, int64_t rows, int bi, int passes,
+                 double tau, double* rinv_out, void* scratch, size_t scratch_bytes, unsigned* bar,
+                 int* flags, int* err) {
+    static int max_ctas = -1;
+    constexpr size_t sm = sizeof(float) * (COOP_ROWS * PLD + 3 * MAXB * CLD);
+    if (max_ctas < 0) {
+        int dev = 0, coop = 0, per_sm = 0;
+        QB_CUDA(cudaGetDevice(&dev));
+        QB_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+        QB_CUDA(cudaFuncSetAttribute(k_cholqr_coop, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     int(sm)));
+        QB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cholqr_coop, COOP_THREADS,
+                                                               sm));
+        max_ctas = coop ? std::min(per_sm * num_sms(), COOP_MAX_CTAS) : 0;
+    }
+    if (max_ctas <= 0 || bi < 1 || bi > MAXB || rows <= 0 || passes < 1) return false;
+    int G = int(std::min<int64_t>(max_ctas, cdiv(rows, 64)));
+    const int64_t rows_per = cdiv(rows, G);
+    if (rows_per > COOP_ROWS) return false;
+    G = int(cdiv(rows, rows_per));
+    if (scratch_bytes < cholqr_coop_scratch_bytes()) return false;
+    CoopArgs a;
+    a.P = P;
+    a.ldp = ldp;
+    a.rows = rows;
+    a.rows_per = rows_per;
+    a.bi = bi;
+    a.passes = passes;
+    a.tau = tau;
+    a.rinv_out = rinv_out;
+    a.part = reinterpret_cast<float*>(scratch);
+    a.wred = a.part + size_t(COOP_MAX_CTAS) * MAXB * MAXB;
+    a.bar = bar;
+    a.flags = flags;
+    a.err = err;
+    void* args[] = {&a};
+    QB_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(k_cholqr_coop), dim3(G),
+                                        dim3(COOP_THREADS), args, sm, st));
+    QB_LAUNCHED();
+    return true;
 }
 
 void set_identity(cudaStream_t st, double* R, int bi) {
@@ -304,8 +580,8 @@ void set_identity(cudaStream_t st, double* R, int bi) {
 }
 
 void tri_inv(cudaStream_t st, const double* R, int bi, double* Rinv) {
-    allow_smem(k_tri_inv, CHOL_SMEM);
-    k_tri_inv<<<1, 64, CHOL_SMEM, st>>>(R, bi, Rinv);
+    allow_smem(k_tri_inv, TRI_SMEM);
+    k_tri_inv<<<1, 64, TRI_SMEM, st>>>(R, bi, Rinv);
     QB_LAUNCHED();
 }
 

@@ -178,6 +178,14 @@ constexpr int MAXB = 64;
 // float32 inverse (the mixed path, which applies Rinv in float32); CHOL_F32: both in float32 (the
 // orthonormalisation inside the power scheme, where only the span matters).  R may be null.
 enum CholPrec { CHOL_F64 = 0, CHOL_F64_INV_F32 = 1, CHOL_F32 = 2 };
+// `passes` CholeskyQR passes (float32 Gram, float32 Cholesky) on a float32 rows x bi panel in one
+// cooperative launch; rinv_out (nullable) receives each pass's R^-1 (MAXB x MAXB, float64).
+// bar: two zero-initialised words kept across calls; err is set if a grid barrier timed out.
+// Returns false (nothing launched) when the panel does not fit the launch.
+size_t cholqr_coop_scratch_bytes();
+bool cholqr_coop(cudaStream_t st, float* P, int64_t ldp, int64_t rows, int bi, int passes,
+                 double tau, double* rinv_out, void* scratch, size_t scratch_bytes, unsigned* bar,
+                 int* flags, int* err);
 void chol_rinv(cudaStream_t st, const double* W, int bi, double tau_rel, double* R,
                double* Rinv, double* R_acc, int* flags, CholPrec prec);
 void set_identity(cudaStream_t st, double* R, int bi);
