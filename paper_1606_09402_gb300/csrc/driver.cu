@@ -170,7 +170,7 @@ struct Ctx {
         double* ri = Rinv;
         if (acc_r && nchain < 4) ri = Rchain + size_t(nchain++) * MAXB * MAXB;
         chol_rinv(st, W, bi, fast ? 1e-10 : tau, nullptr, ri, nullptr, flags,
-                  f64 ? CHOL_F64 : (fast ? CHOL_F32 : CHOL_F64_INV_F32));
+                  f64 ? CHOL_F64 : (fast ? CHOL_F32 : CHOL_ADAPTIVE));
         apply_rinv(st, f64, P, ld, rows, bi, ri);
     }
     // CholeskyQR pass accumulating the factor: Racc <- R Racc (the fixed-rank map keeps R)

@@ -8,55 +8,118 @@ namespace {
 
 constexpr int LDS = MAXB + 1;
 
-// Cholesky of a bi x bi Gram W (bi <= 64) by one CTA of 512 threads: W = R^T R (upper R) factored
-// in TF, R^-1 formed in TI.
+// Cholesky of a bi x bi Gram W (bi <= 64) by one CTA (at least CHOL_THREADS threads): W = R^T R
+// (upper R) factored in TF, R^-1 formed in TI.
 // Breakdown: a pivot d <= tau_rel * max_diag(W) (or NaN) is replaced by tau_rel * max_diag (or
 // the smallest normal number) and flags[1] is raised; the column it produces has norm <= 1.
 //
 // One elimination sweep gives both factors: W = L D L^T (L unit lower), R = D^1/2 L^T and
 // R^-1 = L^-T D^-1/2.  Step j removes row j from the rows a > j of [W | I] (Gaussian elimination
 // without pivoting, multipliers m_a = W[j][a] / d_j read from the symmetric upper part), so the
-// trailing upper triangle becomes the Schur complement and the right half becomes L^-1.  Thread t
-// owns column t % 64 of rows 8 (t / 64) .. 8 (t / 64) + 7 of both halves in registers; the finished
-// row j + 1 of each half (and its pivot) is published to shared memory for the next step, one
-// barrier per step.  Rows of a warp with no work in a step are skipped with warp-uniform branches.
+// trailing upper triangle becomes the Schur complement and the right half becomes L^-1.
+//
+// Work split: the 64 x 64 matrices are cut into 4 x 4 tiles held in registers.  Threads 0..135
+// own the upper tiles of W in row-major order (so the tiles that are finished form a prefix and
+// whole warps drop out), threads 160..295 the lower tiles of L^-1.  After step j the owners of
+// row j + 1 publish it (W in TF and in TI, L^-1 in TI) to shared memory, the owner of its diagonal
+// also its pivot; one barrier per step.
 constexpr int CLD = MAXB + 4;          // shared row stride: rows stay 16-byte aligned
-constexpr int CHOL_THREADS = 512;
+constexpr int CHOL_THREADS = 320;
+constexpr int CHOL_TILES = 136;        // 4 x 4 tiles in a triangle of the 16 x 16 tile grid
+constexpr int CHOL_L0 = 160;           // first thread of the L^-1 tiles
 
 template <class TF, class TI>
 struct CholShared {
-    TF (*S)[CLD];    // rows of W, then the rows W'[j][.] of the elimination
+    TF (*S)[CLD];    // rows W'[j][.] of the elimination as they are finished (TF)
+    TI (*Sf)[CLD];   // the same rows in TI (multipliers of the L^-1 update)
     TI (*Li)[CLD];   // rows of L^-1 as they are finished
     TF* dpiv;        // [MAXB] pivots d_j
     TF* invd;        // [MAXB] 1 / d_j
     TF* idiag;       // [MAXB] 1 / sqrt(d_j)
+    TF* diag0;       // [MAXB] diagonal of W
     TF* dmax;        // [1]
+    int* weak;       // [1] set when some pivot fell below weak_rel * W[j][j]
 };
 
-// load(i, j) returns W[i][j] for i <= j < bi.  On return (after a barrier) S rows hold W'[j][.],
-// dpiv / idiag the pivots, and l[k] = L^-1[8 (t / 64) + k][t % 64].
+// tile t of a triangle of the 16 x 16 tile grid, row-major: (ti, tj) with ti <= tj
+__device__ __forceinline__ void tri_tile(int t, int& ti, int& tj) {
+    ti = 0;
+    while (t >= 16 - ti) { t -= 16 - ti; ++ti; }
+    tj = ti + t;
+}
+
+template <class T>
+__device__ __forceinline__ void ld4(const T* p, T (&v)[4]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = p[q];
+}
+template <>
+__device__ __forceinline__ void ld4<float>(const float* p, float (&v)[4]) {
+    const float4 x = *reinterpret_cast<const float4*>(p);
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+}
+template <class T>
+__device__ __forceinline__ void st4(T* p, const T (&v)[4]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) p[q] = v[q];
+}
+template <>
+__device__ __forceinline__ void st4<float>(float* p, const float (&v)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+
+// load(i, j) returns W[i][j] for i <= j < bi.  On return (after a barrier) S rows hold W'[j][.]
+// in their upper part, dpiv / idiag the pivots, and an L^-1 tile owner (threadIdx.x in
+// [CHOL_L0, CHOL_L0 + 136)) has in l[r][q] the entry L^-1[4 lr + r][4 lc + q] (lr >= lc).
+// weak_rel > 0: *sh.weak is set when a pivot d_j < weak_rel * W[j][j] (a conditioning test).
+//
+// The tile updates need no per-element predicates: the multiplier of a row a <= j is zero, the
+// entries of row j beyond bi are zero, row j of L^-1 is zero beyond column j, and the lower part
+// of the diagonal tiles of W (which picks up rounding garbage) is never read.
 template <class TF, class TI, class Load>
-__device__ void chol_core(int bi, double tau_rel, int* flags, Load load, CholShared<TF, TI> sh,
-                          TI (&l)[8]) {
+__device__ void chol_core(int bi, double tau_rel, double weak_rel, int* flags, Load load,
+                          CholShared<TF, TI> sh, TI (&l)[4][4], int& lr, int& lc) {
     TF (*S)[CLD] = sh.S;
+    TI (*Sf)[CLD] = sh.Sf;
     TI (*Li)[CLD] = sh.Li;
     const int tid = threadIdx.x;
-    const int c = tid & (MAXB - 1);
-    const int a0 = (tid >> 6) * 8;
-    const int cmin = c & 32, cmax = cmin + 31;   // columns of this warp
-    TF s[8];
+    const bool wown = tid < CHOL_TILES;
+    const bool lown = tid >= CHOL_L0 && tid < CHOL_L0 + CHOL_TILES;
+    int wi = 0, wj = 0;                // W tile (rows 4 wi.., cols 4 wj..), wi <= wj
+    if (wown) tri_tile(tid, wi, wj);
+    lr = 0;
+    lc = 0;                            // L^-1 tile (rows 4 lr.., cols 4 lc..), lr >= lc
+    if (lown) tri_tile(tid - CHOL_L0, lc, lr);
+    TF w[4][4];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        const int a = a0 + k;
-        s[k] = (a <= c && c < bi) ? TF(load(a, c)) : TF(0);
-        l[k] = (a == c && a < bi) ? TI(1) : TI(0);
-        S[a][c] = s[k];
-        Li[a][c] = l[k];
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int a = 4 * wi + r, c = 4 * wj + q;
+            w[r][q] = (wown && a <= c && c < bi) ? TF(load(a, c)) : TF(0);
+            const int la = 4 * lr + r, lcc = 4 * lc + q;
+            l[r][q] = (lown && la == lcc && la < bi) ? TI(1) : TI(0);
+        }
+    if (wown) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            TI f[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) f[q] = TI(w[r][q]);
+            st4(&S[4 * wi + r][4 * wj], w[r]);
+            st4(&Sf[4 * wi + r][4 * wj], f);
+            if (wi == wj) sh.diag0[4 * wi + r] = w[r][r];
+        }
     }
+    if (lown) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) st4(&Li[4 * lr + r][4 * lc], l[r]);
+    }
+    if (tid == 0) sh.weak[0] = 0;
     __syncthreads();
     if (tid < 32) {
         TF m = TF(0);
-        for (int i = tid; i < bi; i += 32) m = S[i][i] > m ? S[i][i] : m;
+        for (int i = tid; i < bi; i += 32) m = sh.diag0[i] > m ? sh.diag0[i] : m;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             const TF v = __shfl_xor_sync(0xffffffffu, m, o);
@@ -70,8 +133,10 @@ __device__ void chol_core(int bi, double tau_rel, int* flags, Load load, CholSha
     const TF floor_piv = TF(tau_rel) * dmax > tiny ? TF(tau_rel) * dmax : tiny;
     // pivot of row j from its (updated) diagonal value; called by one thread
     auto pivot = [&](int j, TF d) {
+        if (!(d >= TF(weak_rel) * sh.diag0[j])) sh.weak[0] = 1;
         if (!(d > TF(tau_rel) * dmax)) {
             d = floor_piv;
+            sh.weak[0] = 1;
             if (flags) atomicOr(flags + 1, 1);
         }
         sh.dpiv[j] = d;
@@ -80,23 +145,55 @@ __device__ void chol_core(int bi, double tau_rel, int* flags, Load load, CholSha
     if (tid == 0 && bi > 0) pivot(0, S[0][0]);
     __syncthreads();
     for (int j = 0; j < bi; ++j) {
-        const TF inv = sh.invd[j];
-        const TF t = S[j][c] * inv;
-        const TI u = Li[j][c];
-        const TI inv_i = TI(inv);
+        const int jn = j + 1;
+        if (wown && 4 * wi + 3 > j) {
+            // W'[a][c] -= W'[j][a] * (W'[j][c] / d_j) for j < a <= c
+            const TF inv = sh.invd[j];
+            TF m[4], t[4];
+            ld4(&S[j][4 * wi], m);
+            ld4(&S[j][4 * wj], t);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int a = a0 + k;
-            if (a > j) {
-                const TF w = S[j][a];
-                if (a <= cmax && a <= c && c < bi) s[k] = fma(-w, t, s[k]);
-                if (j >= cmin && c <= j) l[k] = fma(-(TI(w) * inv_i), u, l[k]);
-                if (a == j + 1) {
-                    S[a][c] = s[k];
-                    Li[a][c] = l[k];
-                    if (a == c && a < bi) pivot(a, s[k]);
+            for (int r = 0; r < 4; ++r) m[r] = 4 * wi + r > j ? m[r] : TF(0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) t[q] *= inv;
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) w[r][q] = fma(-m[r], t[q], w[r][q]);
+            if ((jn >> 2) == wi) {
+                const int r = jn & 3;
+                TF v[4];
+                TI f[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    v[q] = r == 0 ? w[0][q] : r == 1 ? w[1][q] : r == 2 ? w[2][q] : w[3][q];
+                    f[q] = TI(v[q]);
                 }
+                st4(&S[jn][4 * wj], v);
+                st4(&Sf[jn][4 * wj], f);
+                if (wi == wj && jn < bi) pivot(jn, r == 0 ? v[0] : r == 1 ? v[1] : r == 2 ? v[2] : v[3]);
             }
+        }
+        if (lown && 4 * lr + 3 > j && 4 * lc <= j) {
+            // L^-1[a][c] -= (W'[j][a] / d_j) * L^-1[j][c] for a > j >= c
+            const TI inv = TI(sh.invd[j]);
+            TI m[4], u[4];
+            ld4(&Sf[j][4 * lr], m);
+            ld4(&Li[j][4 * lc], u);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) m[r] = 4 * lr + r > j ? m[r] * inv : TI(0);
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) l[r][q] = fma(-m[r], u[q], l[r][q]);
+        }
+        if (lown && (jn >> 2) == lr) {
+            const int r = jn & 3;
+            TI v[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                v[q] = r == 0 ? l[0][q] : r == 1 ? l[1][q] : r == 2 ? l[2][q] : l[3][q];
+            st4(&Li[jn][4 * lc], v);
         }
         __syncthreads();
     }
@@ -104,46 +201,44 @@ __device__ void chol_core(int bi, double tau_rel, int* flags, Load load, CholSha
     __syncthreads();
 }
 
-// Standalone: Rinv = R^-1 (and R, R_acc <- R R_acc when given), all MAXB x MAXB column-major.
+// Rinv = R^-1 (and R, R_acc <- R R_acc when given), all MAXB x MAXB column-major, from the state
+// chol_core leaves.  X: MAXB x CLD scratch of TF.
 template <class TF, class TI>
-__global__ void __launch_bounds__(CHOL_THREADS)
-k_chol(const double* __restrict__ W, int bi, double tau_rel, double* __restrict__ Rout,
-       double* __restrict__ Rinv, double* __restrict__ Racc, int* flags) {
-    extern __shared__ __align__(16) unsigned char chol_smem[];
-    TF (*S)[CLD] = reinterpret_cast<TF (*)[CLD]>(chol_smem);
-    TF (*X)[CLD] = reinterpret_cast<TF (*)[CLD]>(chol_smem + sizeof(TF) * MAXB * CLD);
-    TI (*Li)[CLD] = reinterpret_cast<TI (*)[CLD]>(chol_smem + 2 * sizeof(TF) * MAXB * CLD);
-    __shared__ TF dpiv[MAXB];
-    __shared__ TF invd[MAXB];
-    __shared__ TF idiag[MAXB];
-    __shared__ TF dmax_s;
+__device__ void chol_outputs(int bi, const TI (&l)[4][4], int lr, int lc, TF (*S)[CLD],
+                             TF (*X)[CLD], const TF* dpiv, const TF* idiag, double* Rout,
+                             double* Rinv, double* Racc) {
     const int tid = threadIdx.x;
-    const int c = tid & (MAXB - 1);
-    const int a0 = (tid >> 6) * 8;
-    TI l[8];
-    chol_core<TF, TI>(bi, tau_rel, flags, [&](int i, int j) { return W[i + j * MAXB]; },
-                      CholShared<TF, TI>{S, Li, dpiv, invd, idiag, &dmax_s}, l);
     if (Rinv) {
-        // R^-1[c][a] = L^-1[a][c] / sqrt(d_a)
+        // R^-1[c][a] = L^-1[a][c] / sqrt(d_a); strictly lower tiles of R^-1 are zero
+        for (int e = tid; e < MAXB * MAXB; e += blockDim.x)
+            if (((e % MAXB) >> 2) > ((e / MAXB) >> 2)) Rinv[e] = 0.0;
+        if (tid >= CHOL_L0 && tid < CHOL_L0 + CHOL_TILES) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int a = a0 + k;
-            Rinv[c + a * MAXB] = (a < bi && c < bi) ? double(l[k] * TI(idiag[a])) : 0.0;
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int a = 4 * lr + r, c = 4 * lc + q;
+                    Rinv[c + a * MAXB] = (a < bi && c < bi) ? double(l[r][q] * TI(idiag[a])) : 0.0;
+                }
         }
     }
     if (!Rout && !Racc) return;
-    // R in place: R[j][j] = sqrt(d_j), R[j][c] = W'[j][c] / sqrt(d_j); the lower part is zero
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        const int a = a0 + k;
-        if (a < bi && c < bi && a <= c) S[a][c] = a == c ? sqrt(dpiv[a]) : S[a][c] * idiag[a];
+    // R: R[j][j] = sqrt(d_j), R[j][c] = W'[j][c] / sqrt(d_j) (c > j), zero elsewhere
+    for (int e = tid; e < MAXB * MAXB; e += blockDim.x) {
+        const int a = e / MAXB, c = e % MAXB;
+        X[a][c] = (a < bi && c < bi && a <= c) ? (a == c ? sqrt(dpiv[a]) : S[a][c] * idiag[a])
+                                               : TF(0);
+    }
+    __syncthreads();
+    for (int e = tid; e < MAXB * MAXB; e += blockDim.x) {
+        const int a = e / MAXB, c = e % MAXB;
+        S[a][c] = X[a][c];
     }
     __syncthreads();
     if (Rout) {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int a = a0 + k;
-            Rout[a + c * MAXB] = (a <= c && c < bi) ? double(S[a][c]) : 0.0;
+        for (int e = tid; e < MAXB * MAXB; e += blockDim.x) {
+            const int a = e % MAXB, c = e / MAXB;
+            Rout[a + c * MAXB] = double(S[a][c]);
         }
     }
     if (Racc) {
@@ -161,6 +256,54 @@ k_chol(const double* __restrict__ W, int bi, double tau_rel, double* __restrict_
             Racc[i + jj * MAXB] = double(acc);
         }
     }
+}
+
+// Pivot test of the adaptive factorisation: a float32 factor is kept when every pivot keeps at
+// least this fraction of its column's squared norm (kappa of the panel below about 100, so the
+// float32 factor leaves the first CholeskyQR pass orthogonal to ~64 u32 kappa^2 < 0.04 and the
+// second pass restores it); otherwise the panel is refactored in float64.
+constexpr double CHOL_WEAK_REL = 1e-4;
+
+// Standalone factorisation.  ADAPT: float32 first, float64 (TF) when a pivot is weak.
+template <class TF, class TI, bool ADAPT>
+__global__ void __launch_bounds__(CHOL_THREADS)
+k_chol(const double* __restrict__ W, int bi, double tau_rel, double* __restrict__ Rout,
+       double* __restrict__ Rinv, double* __restrict__ Racc, int* flags) {
+    extern __shared__ __align__(16) unsigned char chol_smem[];
+    TF (*S)[CLD] = reinterpret_cast<TF (*)[CLD]>(chol_smem);
+    TF (*X)[CLD] = reinterpret_cast<TF (*)[CLD]>(chol_smem + sizeof(TF) * MAXB * CLD);
+    TI (*Sf)[CLD] = reinterpret_cast<TI (*)[CLD]>(chol_smem + 2 * sizeof(TF) * MAXB * CLD);
+    TI (*Li)[CLD] = reinterpret_cast<TI (*)[CLD]>(chol_smem + (2 * sizeof(TF) + sizeof(TI)) * MAXB * CLD);
+    __shared__ TF dpiv[MAXB];
+    __shared__ TF invd[MAXB];
+    __shared__ TF idiag[MAXB];
+    __shared__ TF diag0[MAXB];
+    __shared__ TF dmax_s;
+    __shared__ int weak;
+    auto ldw = [&](int i, int j) { return W[i + j * MAXB]; };
+    TI l[4][4];
+    int lr, lc;
+    if (ADAPT) {
+        // float32 attempt in the same shared memory (float views of S, X; TI is float here)
+        float (*Sg)[CLD] = reinterpret_cast<float (*)[CLD]>(chol_smem);
+        float (*Xg)[CLD] = reinterpret_cast<float (*)[CLD]>(chol_smem + sizeof(float) * MAXB * CLD);
+        __shared__ float fpiv[MAXB], finvd[MAXB], fidiag[MAXB], fdiag0[MAXB], fdmax;
+        float lf[4][4];
+        chol_core<float, float>(bi, tau_rel, CHOL_WEAK_REL, nullptr, ldw,
+                                CholShared<float, float>{Sg, reinterpret_cast<float (*)[CLD]>(Sf),
+                                                         reinterpret_cast<float (*)[CLD]>(Li),
+                                                         fpiv, finvd, fidiag, fdiag0, &fdmax, &weak},
+                                lf, lr, lc);
+        if (!weak) {
+            chol_outputs<float, float>(bi, lf, lr, lc, Sg, Xg, fpiv, fidiag, Rout, Rinv, Racc);
+            return;
+        }
+        __syncthreads();
+    }
+    chol_core<TF, TI>(bi, tau_rel, 0.0, flags, ldw,
+                      CholShared<TF, TI>{S, Sf, Li, dpiv, invd, idiag, diag0, &dmax_s, &weak}, l,
+                      lr, lc);
+    chol_outputs<TF, TI>(bi, l, lr, lc, S, X, dpiv, idiag, Rout, Rinv, Racc);
 }
 
 // ---------------------------------------------------------------- fused CholeskyQR (float32 panel)
@@ -234,10 +377,12 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) k_cholqr_coop(CoopArgs p) {
     float (*Ps)[PLD] = reinterpret_cast<float (*)[PLD]>(coop_smem);
     unsigned char* rest = coop_smem + sizeof(float) * COOP_ROWS * PLD;
     float (*S)[CLD] = reinterpret_cast<float (*)[CLD]>(rest);
-    float (*Li)[CLD] = reinterpret_cast<float (*)[CLD]>(rest + sizeof(float) * MAXB * CLD);
-    float (*Rs)[CLD] = reinterpret_cast<float (*)[CLD]>(rest + 2 * sizeof(float) * MAXB * CLD);
-    float* scratch = reinterpret_cast<float*>(rest);   // Gram combine space (S and Li, 2 x 17 KB)
-    __shared__ float dpiv[MAXB], invd[MAXB], idiag[MAXB], dmax_s;
+    float (*Sf)[CLD] = reinterpret_cast<float (*)[CLD]>(rest + sizeof(float) * MAXB * CLD);
+    float (*Li)[CLD] = reinterpret_cast<float (*)[CLD]>(rest + 2 * sizeof(float) * MAXB * CLD);
+    float (*Rs)[CLD] = reinterpret_cast<float (*)[CLD]>(rest + 3 * sizeof(float) * MAXB * CLD);
+    float* scratch = reinterpret_cast<float*>(rest);   // Gram combine space (S and Sf, 2 x 17 KB)
+    __shared__ float dpiv[MAXB], invd[MAXB], idiag[MAXB], diag0[MAXB], dmax_s;
+    __shared__ int weak_s;
     __shared__ double red[16][32];
     const int tid = threadIdx.x;
     const int G = gridDim.x, cta = blockIdx.x;
@@ -319,19 +464,32 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) k_cholqr_coop(CoopArgs p) {
         }
         if (!coop_sync(p.bar, p.err)) return;
         // ---- every CTA factors the summed Gram
-        float l[8];
-        chol_core<float, float>(bi, p.tau, cta == 0 ? p.flags : nullptr,
+        float l[4][4];
+        int lr, lc;
+        chol_core<float, float>(bi, p.tau, 0.0, cta == 0 ? p.flags : nullptr,
                                 [&](int i, int j) { return __ldcg(p.wred + i + j * MAXB); },
-                                CholShared<float, float>{S, Li, dpiv, invd, idiag, &dmax_s}, l);
-        {
-            const int c = tid & (MAXB - 1), a0 = (tid >> 6) * 8;
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int a = a0 + k;
-                const float v = (a < bi && c < bi) ? l[k] * idiag[a] : 0.f;
-                Rs[c][a] = v;                                   // R^-1[c][a]
-                if (cta == 0 && p.rinv_out) p.rinv_out[int64_t(pass) * MAXB * MAXB + c + a * MAXB] = v;
+                                CholShared<float, float>{S, Sf, Li, dpiv, invd, idiag, diag0,
+                                                         &dmax_s, &weak_s},
+                                l, lr, lc);
+        // R^-1[c][a] = L^-1[a][c] / sqrt(d_a); strictly lower tiles are zero
+        double* ro = (cta == 0 && p.rinv_out) ? p.rinv_out + int64_t(pass) * MAXB * MAXB : nullptr;
+        for (int e = tid; e < MAXB * MAXB; e += COOP_THREADS) {
+            const int i = e % MAXB, jj = e / MAXB;
+            if ((i >> 2) > (jj >> 2)) {
+                Rs[i][jj] = 0.f;
+                if (ro) ro[e] = 0.0;
             }
+        }
+        if (tid >= CHOL_L0 && tid < CHOL_L0 + CHOL_TILES) {
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int a = 4 * lr + r, c = 4 * lc + q;
+                    const float v = (a < bi && c < bi) ? l[r][q] * idiag[a] : 0.f;
+                    Rs[c][a] = v;
+                    if (ro) ro[c + a * MAXB] = v;
+                }
         }
         __syncthreads();
         // ---- rows <- rows * R^-1, 128 rows at a time (thread: one row, 16 columns)
@@ -493,7 +651,7 @@ __global__ void k_indicator(double* state, const double* rn, int rows, double ep
 
 template <class TF, class TI>
 constexpr size_t chol_smem() {
-    return (2 * sizeof(TF) + sizeof(TI)) * MAXB * CLD;
+    return (2 * sizeof(TF) + 2 * sizeof(TI)) * MAXB * CLD;
 }
 constexpr size_t TRI_SMEM = sizeof(double) * 2 * MAXB * LDS;
 
@@ -508,20 +666,30 @@ void chol_rinv(cudaStream_t st, const double* W, int bi, double tau_rel, double*
     switch (prec) {
         case CHOL_F64: {
             constexpr size_t sm = chol_smem<double, double>();
-            allow_smem(k_chol<double, double>, sm);
-            k_chol<double, double><<<1, CHOL_THREADS, sm, st>>>(W, bi, tau_rel, R, Rinv, R_acc, flags);
+            allow_smem(k_chol<double, double, false>, sm);
+            k_chol<double, double, false><<<1, CHOL_THREADS, sm, st>>>(W, bi, tau_rel, R, Rinv,
+                                                                       R_acc, flags);
             break;
         }
         case CHOL_F64_INV_F32: {
             constexpr size_t sm = chol_smem<double, float>();
-            allow_smem(k_chol<double, float>, sm);
-            k_chol<double, float><<<1, CHOL_THREADS, sm, st>>>(W, bi, tau_rel, R, Rinv, R_acc, flags);
+            allow_smem(k_chol<double, float, false>, sm);
+            k_chol<double, float, false><<<1, CHOL_THREADS, sm, st>>>(W, bi, tau_rel, R, Rinv,
+                                                                      R_acc, flags);
+            break;
+        }
+        case CHOL_ADAPTIVE: {
+            constexpr size_t sm = chol_smem<double, float>();
+            allow_smem(k_chol<double, float, true>, sm);
+            k_chol<double, float, true><<<1, CHOL_THREADS, sm, st>>>(W, bi, tau_rel, R, Rinv,
+                                                                     R_acc, flags);
             break;
         }
         default: {
             constexpr size_t sm = chol_smem<float, float>();
-            allow_smem(k_chol<float, float>, sm);
-            k_chol<float, float><<<1, CHOL_THREADS, sm, st>>>(W, bi, tau_rel, R, Rinv, R_acc, flags);
+            allow_smem(k_chol<float, float, false>, sm);
+            k_chol<float, float, false><<<1, CHOL_THREADS, sm, st>>>(W, bi, tau_rel, R, Rinv,
+                                                                     R_acc, flags);
             break;
         }
     }
@@ -536,7 +704,7 @@ bool cholqr_coop(cudaStream_t st, float* P, int64_t ldp, int64_t rows, int bi, i
                  double tau, double* rinv_out, void* scratch, size_t scratch_bytes, unsigned* bar,
                  int* flags, int* err) {
     static int max_ctas = -1;
-    constexpr size_t sm = sizeof(float) * (COOP_ROWS * PLD + 3 * MAXB * CLD);
+    constexpr size_t sm = sizeof(float) * (COOP_ROWS * PLD + 4 * MAXB * CLD);
     if (max_ctas < 0) {
         int dev = 0, coop = 0, per_sm = 0;
         QB_CUDA(cudaGetDevice(&dev));

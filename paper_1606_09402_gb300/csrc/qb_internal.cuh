@@ -176,8 +176,10 @@ constexpr int MAXB = 64;
 // and sets flags[1]; R_acc <- R * R_acc if R_acc != nullptr (R_acc starts as identity).
 // CHOL_F64: factor and inverse in float64 (the float64 path); CHOL_F64_INV_F32: float64 factor,
 // float32 inverse (the mixed path, which applies Rinv in float32); CHOL_F32: both in float32 (the
-// orthonormalisation inside the power scheme, where only the span matters).  R may be null.
-enum CholPrec { CHOL_F64 = 0, CHOL_F64_INV_F32 = 1, CHOL_F32 = 2 };
+// orthonormalisation inside the power scheme, where only the span matters); CHOL_ADAPTIVE: float32
+// when every pivot keeps >= 1e-4 of its column's squared norm, else as CHOL_F64_INV_F32.
+// R may be null.
+enum CholPrec { CHOL_F64 = 0, CHOL_F64_INV_F32 = 1, CHOL_F32 = 2, CHOL_ADAPTIVE = 3 };
 // `passes` CholeskyQR passes (float32 Gram, float32 Cholesky) on a float32 rows x bi panel in one
 // cooperative launch; rinv_out (nullable) receives each pass's R^-1 (MAXB x MAXB, float64).
 // bar: two zero-initialised words kept across calls; err is set if a grid barrier timed out.
