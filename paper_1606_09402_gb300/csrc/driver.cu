@@ -78,6 +78,10 @@ struct Ctx {
     // tensor-core projections for the power-scheme orthonormalisation (mixed path)
     void* tcs = nullptr;
     size_t tcs_bytes = 0;
+    // three-term bf16 shadows of Q (m x cap) and B^T (n x cap) for the tensor-core projections
+    bf16* qs[3] = {nullptr, nullptr, nullptr};
+    bf16* bs[3] = {nullptr, nullptr, nullptr};
+    int64_t ldqs = 0, ldbs = 0;
     bf16* xb_hi = nullptr;    // bf16 shadow of the panels finished so far (hi, lo)
     bf16* xb_lo = nullptr;
     int64_t xb_ld = 0;
@@ -158,10 +162,11 @@ struct Ctx {
     // P <- P R^-1; with acc_r the factor's inverse is kept in Rchain (in order) for the B_i formula.  sketch: the basis only has to span the same space
     // (the power scheme), so the Gram is accumulated and factored in float32.
     // Fused float32 CholeskyQR passes for the power-scheme orthonormalisation (one launch).
-    bool coop(void* P, int64_t ld, int64_t rows, int bi, int passes) {
+    bool coop(void* P, int64_t ld, int64_t rows, int bi, int passes, bf16* out_hi = nullptr,
+              bf16* out_lo = nullptr, int64_t ldo = 0) {
         return cholqr_coop(st, reinterpret_cast<float*>(P), ld, rows, bi, passes, 1e-10, nullptr,
                            coop_scr, coop_bytes, reinterpret_cast<unsigned*>(flags + 4), flags,
-                           flags + 2);
+                           flags + 2, out_hi, out_lo, ldo);
     }
     void cholqr(void* P, int64_t ld, int64_t rows, int bi, bool acc_r, bool sketch = false) {
         const bool fast = sketch && !f64;
@@ -194,6 +199,75 @@ struct Ctx {
         tn(k, bi, rows, 1.0, Q, ldq, P, ldp, 0.0, T, k, sketch ? ACC_F : acc_fine);
         nn(rows, bi, k, -1.0, Q, ldq, T, k, 1.0, P, ldp, acc_proj);
     }
+    // ---- products with the current Q (m x k, ld ldq) and B (k x n row-major = n x k column-major,
+    // ld ldb); tensor cores (float32 accuracy) when the three-term shadows exist, SIMT otherwise.
+    bool tcg() const { return qs[0] != nullptr; }
+    const bf16* const* qsp() const { return qs; }
+    // T (k x bi, ld ldt) = Q^T X + beta T, X m x bi
+    void qt_x(int64_t k, int bi, const void* Q, int64_t ldq, int64_t m, const void* X, int64_t ldx,
+              double beta, void* T, int64_t ldt, Acc acc) {
+        if (k <= 0) return;
+        if (tcg()) {
+            tc_prec_gemm(st, false, qs, 3, ldqs, k, m, reinterpret_cast<const float*>(X), ldx, bi,
+                         1.f, float(beta), reinterpret_cast<float*>(T), ldt, tcs, tcs_bytes);
+            return;
+        }
+        tn(k, bi, m, 1.0, Q, ldq, X, ldx, beta, T, ldt, acc);
+    }
+    // Y (m x bi) += alpha Q T, T k x bi
+    void q_t(int64_t k, int bi, const void* Q, int64_t ldq, int64_t m, double alpha, const void* T,
+             int64_t ldt, void* Y, int64_t ldy, Acc acc) {
+        if (k <= 0) return;
+        if (tcg()) {
+            tc_prec_gemm(st, true, qs, 3, ldqs, m, k, reinterpret_cast<const float*>(T), ldt, bi,
+                         float(alpha), 1.f, reinterpret_cast<float*>(Y), ldy, tcs, tcs_bytes);
+            return;
+        }
+        nn(m, bi, k, alpha, Q, ldq, T, ldt, 1.0, Y, ldy, acc);
+    }
+    // T (k x bi) = B X + beta T, X n x bi
+    void b_x(int64_t k, int bi, const void* B, int64_t ldb, int64_t n, const void* X, int64_t ldx,
+             double beta, void* T, int64_t ldt, Acc acc) {
+        if (k <= 0) return;
+        if (tcg()) {
+            tc_prec_gemm(st, false, bs, 3, ldbs, k, n, reinterpret_cast<const float*>(X), ldx, bi,
+                         1.f, float(beta), reinterpret_cast<float*>(T), ldt, tcs, tcs_bytes);
+            return;
+        }
+        tn(k, bi, n, 1.0, B, ldb, X, ldx, beta, T, ldt, acc);
+    }
+    // Z (n x bi) += alpha B^T T, T k x bi
+    void bt_t(int64_t k, int bi, const void* B, int64_t ldb, int64_t n, double alpha, const void* T,
+              int64_t ldt, void* Z, int64_t ldz, Acc acc) {
+        if (k <= 0) return;
+        if (tcg()) {
+            tc_prec_gemm(st, true, bs, 3, ldbs, n, k, reinterpret_cast<const float*>(T), ldt, bi,
+                         float(alpha), 1.f, reinterpret_cast<float*>(Z), ldz, tcs, tcs_bytes);
+            return;
+        }
+        nn(n, bi, k, alpha, B, ldb, T, ldt, 1.0, Z, ldz, acc);
+    }
+    // re-orthogonalise P (m x bi) against Q: P -= Q (Q^T P); T: k x bi scratch
+    void reorth_q(int64_t k, const void* Q, int64_t ldq, int64_t m, void* P, int64_t ldp, int bi,
+                  void* T) {
+        if (k <= 0) return;
+        if (!tcg()) {
+            project_out(Q, ldq, k, P, ldp, m, bi, T);
+            return;
+        }
+        Scope sc(*this, PH_PROJ);
+        qt_x(k, bi, Q, ldq, m, P, ldp, 0.0, T, k, acc_fine);
+        q_t(k, bi, Q, ldq, m, -1.0, T, k, P, ldp, acc_proj);
+    }
+    // a block is final: record its three-term shadows (Q_i: m x bi at column k; B_i^T: n x bi)
+    void shadow(int64_t k, int bi, const void* Qi, int64_t ldq, int64_t m, const void* BiT,
+                int64_t ldb, int64_t n) {
+        if (!tcg()) return;
+        split3_bf16(st, reinterpret_cast<const float*>(Qi), ldq, m, bi, qs[0] + k * ldqs,
+                    qs[1] + k * ldqs, qs[2] + k * ldqs, ldqs);
+        split3_bf16(st, reinterpret_cast<const float*>(BiT), ldb, n, bi, bs[0] + k * ldbs,
+                    bs[1] + k * ldbs, bs[2] + k * ldbs, ldbs);
+    }
     // Orthonormalise the rows x w matrix X (column-major) panel by panel for the power scheme:
     // block Gram-Schmidt with re-orthogonalisation, CholeskyQR per panel of width b.  Only the
     // span matters here, so the mixed path works in float32 throughout.  T: w x b scratch.
@@ -220,16 +294,26 @@ struct Ctx {
         for (int64_t j0 = 0; j0 < w; j0 += b) {
             const int bj = int(std::min<int64_t>(b, w - j0));
             char* Pj = col(X, ld, j0);
+            // the last orthonormalisation of the panel also writes its bf16 shadow when fused
+            bf16* shi = tc ? xb_hi + j0 * xb_ld : nullptr;
+            bf16* slo = tc && lo ? lo + j0 * xb_ld : nullptr;
+            const bool again = j0 > 0 && (reorth || f64);
+            bool shadow = false;
+            auto fused = [&](int passes, bf16* h) {
+                Scope sc(*this, PH_ORTHW);
+                return !f64 && coop(Pj, ld, rows, bj, passes, h, slo, xb_ld);
+            };
             project(j0, Pj, bj);
-            cholqr2(Pj, ld, rows, bj, false, true);
-            if (j0 > 0 && (reorth || f64)) {
+            if (fused(2, again ? nullptr : shi)) shadow = !again;
+            else cholqr2(Pj, ld, rows, bj, false, true);
+            if (again) {
                 project(j0, Pj, bj);
                 if (f64) cholqr2(Pj, ld, rows, bj, false, true);
+                else if (fused(1, shi)) shadow = true;
                 else cholqr(Pj, ld, rows, bj, false, true);
             }
-            if (tc)
-                split_bf16(st, reinterpret_cast<const float*>(Pj), ld, rows, bj,
-                           xb_hi + j0 * xb_ld, lo ? lo + j0 * xb_ld : nullptr, xb_ld);
+            if (tc && !shadow)
+                split_bf16(st, reinterpret_cast<const float*>(Pj), ld, rows, bj, shi, slo, xb_ld);
         }
     }
     struct Step { double E; int keep; int stop; };
@@ -481,10 +565,17 @@ void reserve_all(Arena& ar, Ctx& c, AOp& A, const Plan& p, bool fp, Bufs& bf) {
         bf.Tw = ar.get<char>(p.lt * p.b * es);
     }
     A.reserve(ar, c, wmax);
-    if (fp && p.P > 0 && A.tc_scratch(&c.tcs, &c.tcs_bytes)) {
-        c.xb_ld = align_up(std::max(p.m, p.n), 8);
-        c.xb_hi = ar.get<bf16>(c.xb_ld * p.lt);
-        c.xb_lo = ar.get<bf16>(c.xb_ld * p.lt);
+    if (!c.f64 && A.tc_scratch(&c.tcs, &c.tcs_bytes)) {
+        if (fp && p.P > 0) {
+            c.xb_ld = align_up(std::max(p.m, p.n), 8);
+            c.xb_hi = ar.get<bf16>(c.xb_ld * p.lt);
+            c.xb_lo = ar.get<bf16>(c.xb_ld * p.lt);
+        }
+        const int64_t cap = std::max<int64_t>(p.cap, 1);
+        c.ldqs = align_up(p.m, 8);
+        c.ldbs = align_up(p.n, 8);
+        for (int t = 0; t < 3; ++t) c.qs[t] = ar.get<bf16>(c.ldqs * cap);
+        for (int t = 0; t < 3; ++t) c.bs[t] = ar.get<bf16>(c.ldbs * cap);
     }
 }
 
@@ -517,8 +608,8 @@ void run_ei(Ctx& c, AOp& A, const Plan& p, const qb_opts& o, Bufs& bf, void* Q, 
         out.passes += 1;
         if (k > 0) {
             Ctx::Scope sp(c, PH_PROJ);
-            c.tn(k, bi, n, 1.0, B, ldb, bf.Om, n, 0.0, bf.T1, k, c.acc_proj);      // B Omega_i
-            c.nn(m, bi, k, -1.0, Q, ldq, bf.T1, k, 1.0, Y, ldq, c.acc_proj);      // Y -= Q (.)
+            c.b_x(k, bi, B, ldb, n, bf.Om, n, 0.0, bf.T1, k, c.acc_proj);          // B Omega_i
+            c.q_t(k, bi, Q, ldq, m, -1.0, bf.T1, k, Y, ldq, c.acc_proj);          // Y -= Q (.)
         }
         for (int it = 0; it < p.P; ++it) {
             c.cholqr2(Y, ldq, m, bi, false);                                      // Y = orth(Y)
@@ -526,27 +617,30 @@ void run_ei(Ctx& c, AOp& A, const Plan& p, const qb_opts& o, Bufs& bf, void* Q, 
             A.apply_t(c, Y, ldq, bi, bf.Z, n, 1);                                 // Z = A^T Y
             out.passes += 1;
             if (k > 0) {
-                c.tn(k, bi, m, 1.0, Q, ldq, Y, ldq, 0.0, bf.T1, k, c.acc_proj);   // Q^T Y
-                c.nn(n, bi, k, -1.0, B, ldb, bf.T1, k, 1.0, bf.Z, n, c.acc_proj); // Z -= B^T (.)
+                Ctx::Scope sp(c, PH_PROJ);
+                c.qt_x(k, bi, Q, ldq, m, Y, ldq, 0.0, bf.T1, k, c.acc_proj);      // Q^T Y
+                c.bt_t(k, bi, B, ldb, n, -1.0, bf.T1, k, bf.Z, n, c.acc_proj);    // Z -= B^T (.)
             }
             c.cholqr2(bf.Z, n, n, bi, false);                                     // Z = orth(Z)
             A.round_operand(c, bf.Z, n, n, bi);
             A.apply(c, bf.Z, n, bi, Y, ldq);                                      // Y = A Z
             out.passes += 1;
             if (k > 0) {
-                c.tn(k, bi, n, 1.0, B, ldb, bf.Z, n, 0.0, bf.T1, k, c.acc_proj);  // B Z
-                c.nn(m, bi, k, -1.0, Q, ldq, bf.T1, k, 1.0, Y, ldq, c.acc_proj);  // Y -= Q (.)
+                Ctx::Scope sp(c, PH_PROJ);
+                c.b_x(k, bi, B, ldb, n, bf.Z, n, 0.0, bf.T1, k, c.acc_proj);      // B Z
+                c.q_t(k, bi, Q, ldq, m, -1.0, bf.T1, k, Y, ldq, c.acc_proj);      // Y -= Q (.)
             }
         }
         c.cholqr2(Y, ldq, m, bi, false);                                          // Q_i = orth(Y)
         if (k > 0) {                                                              // re-orthogonalise
-            c.project_out(Q, ldq, k, Y, ldq, m, bi, bf.T1);
+            c.reorth_q(k, Q, ldq, m, Y, ldq, bi, bf.T1);
             c.cholqr2(Y, ldq, m, bi, false);
         }
         // B_i = Q_i^T A, written as rows k.. of B (= column-major n x bi with ld ldb)
         char* Bs = c.col(B, ldb, k);
         A.apply_t(c, Y, ldq, bi, Bs, ldb, 3);
         out.passes += 1;
+        c.shadow(k, bi, Y, ldq, m, Bs, ldb, n);
         const Ctx::Step s = c.indicator_step(Bs, ldb, bi, n, eps2, o.row_by_row);
         out.blocks += 1;
         out.E = s.E;
@@ -611,8 +705,8 @@ void run_fp(Ctx& c, AOp& A, const Plan& p, const qb_opts& o, Bufs& bf, void* Q, 
             c.copy_cols_(c.col(bf.G, m, c0), m, m, bi, bf.Ys, m);
             if (k > 0) {
                 Ctx::Scope sc(c, PH_PROJ);
-                c.tn(k, bi, n, 1.0, B, ldb, Om_i, n, 0.0, bf.T1, k, c.acc_proj);
-                c.nn(m, bi, k, -1.0, Q, ldq, bf.T1, k, 1.0, bf.Ys, m, c.acc_proj);
+                c.b_x(k, bi, B, ldb, n, Om_i, n, 0.0, bf.T1, k, c.acc_proj);
+                c.q_t(k, bi, Q, ldq, m, -1.0, bf.T1, k, bf.Ys, m, c.acc_proj);
             }
             // [Q_i, R_i] = qr(Y_i) in the slot of Q_i; the inverses of the factors go to Rchain
             char* Qi = c.col(Q, ldq, k);
@@ -621,7 +715,7 @@ void run_fp(Ctx& c, AOp& A, const Plan& p, const qb_opts& o, Bufs& bf, void* Q, 
             c.cholqr2(Qi, ldq, m, bi, true);
             if (k > 0) {
                 // [Q_i, R~_i] = qr(Q_i - Q (Q^T Q_i)), R_i = R~_i R_i
-                c.project_out(Q, ldq, k, Qi, ldq, m, bi, bf.C2);
+                c.reorth_q(k, Q, ldq, m, Qi, ldq, bi, bf.C2);
                 c.cholqr2(Qi, ldq, m, bi, true);
             }
             char* Bs = c.col(B, ldb, k);
@@ -632,8 +726,8 @@ void run_fp(Ctx& c, AOp& A, const Plan& p, const qb_opts& o, Bufs& bf, void* Q, 
                 c.copy_cols_(c.col(bf.H, n, c0), n, n, bi, S, n);
                 if (k > 0) {
                     c.copy_cols_(bf.T1, k, k, bi, bf.C2, k);                          // C2 = B Omega_i
-                    c.tn(k, bi, m, 1.0, Q, ldq, bf.Ys, m, 1.0, bf.C2, k, c.acc_fine); // += Q^T Y_i
-                    c.nn(n, bi, k, -1.0, B, ldb, bf.C2, k, 1.0, S, n, c.acc_fine);    // S^T -= B^T C2
+                    c.qt_x(k, bi, Q, ldq, m, bf.Ys, m, 1.0, bf.C2, k, c.acc_fine);    // += Q^T Y_i
+                    c.bt_t(k, bi, B, ldb, n, -1.0, bf.C2, k, S, n, c.acc_fine);       // S^T -= B^T C2
                 }
                 // B_i = R_i^-T S  <=>  B_i^T = S^T R_i^-1, R_i = R~_2 R~_1 R_2 R_1 (the four
                 // CholeskyQR factors): apply R_1^-1, R_2^-1, R~_1^-1, R~_2^-1 in turn
@@ -641,6 +735,7 @@ void run_fp(Ctx& c, AOp& A, const Plan& p, const qb_opts& o, Bufs& bf, void* Q, 
                     apply_rinv(c.st, c.f64, S, n, n, bi, c.Rchain + size_t(f) * MAXB * MAXB);
                 c.copy_cols_(S, n, n, bi, Bs, ldb);
             }
+            c.shadow(k, bi, Qi, ldq, m, Bs, ldb, n);
             const Ctx::Step s = c.indicator_step(Bs, ldb, bi, n, eps2, o.row_by_row);
             out.blocks += 1;
             out.E = s.E;

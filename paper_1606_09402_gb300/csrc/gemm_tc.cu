@@ -466,6 +466,18 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
 // A_lo V_mid: 2^-18) accumulate in tensor memory over PREC_CHUNK k-blocks, where their bias is
 // scaled down by those factors.  A_lo V_lo (2^-27) is dropped.
 constexpr int PREC_CHUNK = 8;
+constexpr int PREC_EPI = 8;                          // epilogue warps
+constexpr int PREC_THREADS = 64 + 32 * PREC_EPI;     // TMA warp, MMA warp, epilogue warps
+
+// Lower-order products (i, j) of A term i and V term j (weight 2^-9 (i + j)): every pair with
+// i + j <= 2 except the leading (0, 0).
+__host__ __device__ constexpr int prec_nsmall(int na, int nb) {
+    int c = 0;
+    for (int i = 0; i < na; ++i)
+        for (int j = 0; j < nb; ++j)
+            if (i + j >= 1 && i + j <= 2) ++c;
+    return c;
+}
 
 template <int BN, int NA, int NB>
 struct PCfg {
@@ -474,17 +486,18 @@ struct PCfg {
     static constexpr int STAGE = NA * A_TILE + NB * B_TILE;
     static constexpr int STAGES = (200 * 1024) / STAGE < 8 ? (200 * 1024) / STAGE : 8;
     static constexpr int SMEM = STAGES * STAGE + 1024 + 512;
-    static constexpr int NSMALL = (NA == 2 ? 1 : 0) + (NB == 3 ? (NA == 2 ? 3 : 2) : 0);
+    static constexpr int NSMALL = prec_nsmall(NA, NB);
     static constexpr int SMALL_COLS = NSMALL > 0 ? 2 * BN : 0;   // double-buffered chain
     static constexpr int NSLOT = (512 - SMALL_COLS) / BN < 8 ? (512 - SMALL_COLS) / BN : 8;
     static constexpr int TMEM_COLS = 512;
 };
 
-template <int BN, int NA, int NB>
-__global__ void __launch_bounds__(NUM_THREADS, 1)
+template <int BN, bool TRANS, int NA, int NB>
+__global__ void __launch_bounds__(PREC_THREADS, 1)
 k_tc_prec(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
-          const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1,
-          const __grid_constant__ CUtensorMap mB2, Params p) {
+          const __grid_constant__ CUtensorMap mA2, const __grid_constant__ CUtensorMap mB0,
+          const __grid_constant__ CUtensorMap mB1, const __grid_constant__ CUtensorMap mB2,
+          Params p) {
     using C = PCfg<BN, NA, NB>;
     static_assert(C::STAGES >= 2, "precise pass needs two stages");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -507,11 +520,11 @@ k_tc_prec(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(sfull + b, 1);
-            mbar_init(sempty + b, 128);
+            mbar_init(sempty + b, PREC_EPI * 32);
         }
         for (int b = 0; b < C::NSLOT; ++b) {
             mbar_init(bfull + b, 1);
-            mbar_init(bempty + b, 128);
+            mbar_init(bempty + b, PREC_EPI * 32);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -572,24 +585,28 @@ k_tc_prec(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
                 mbar_expect_tx(full + stage, uint32_t(C::STAGE));
                 unsigned char* st = smem + stage * C::STAGE;
                 const int k = kb * BK;
-                tma_load_2d(st, &mA0, full + stage, r0, k);
-                tma_load_2d(st + C::A_TILE / 2, &mA0, full + stage, r0 + 64, k);
-                if (NA > 1) {
-                    tma_load_2d(st + C::A_TILE, &mA1, full + stage, r0, k);
-                    tma_load_2d(st + C::A_TILE + C::A_TILE / 2, &mA1, full + stage, r0 + 64, k);
+#pragma unroll
+                for (int i = 0; i < NA; ++i) {
+                    const CUtensorMap* m = i == 0 ? &mA0 : (i == 1 ? &mA1 : &mA2);
+                    unsigned char* d = st + i * C::A_TILE;
+                    if (TRANS) {
+                        tma_load_2d(d, m, full + stage, r0, k);
+                        tma_load_2d(d + C::A_TILE / 2, m, full + stage, r0 + 64, k);
+                    } else {
+                        tma_load_2d(d, m, full + stage, k, r0);
+                    }
                 }
                 unsigned char* sb = st + NA * C::A_TILE;
-                tma_load_2d(sb, &mB0, full + stage, k, c0);
-                if (NB > 1) {
-                    tma_load_2d(sb + C::B_TILE, &mB1, full + stage, k, c0);
-                    tma_load_2d(sb + 2 * C::B_TILE, &mB2, full + stage, k, c0);
-                }
+#pragma unroll
+                for (int j = 0; j < NB; ++j)
+                    tma_load_2d(sb + j * C::B_TILE, j == 0 ? &mB0 : (j == 1 ? &mB1 : &mB2),
+                                full + stage, k, c0);
                 if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
             }
         }
     } else if (warp == 1 && lane == 0) {
         // ---------------------------------------------------------- MMA issuer
-        constexpr uint32_t idesc = idesc_bf16(BN, true);
+        constexpr uint32_t idesc = idesc_bf16(BN, TRANS);
         int stage = 0;
         uint32_t phase = 0;
         int slot = 0;
@@ -616,32 +633,34 @@ k_tc_prec(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
                     const uint32_t sbb = sa + NA * C::A_TILE;
 #pragma unroll
                     for (int kk = 0; kk < BK / UMMA_K; ++kk) {
-                        const uint64_t a_hi = sdesc(sa + kk * (UMMA_K * 128), C::A_TILE / 2, 1024);
-                        const uint64_t a_lo =
-                            sdesc(sa + (NA - 1) * C::A_TILE + kk * (UMMA_K * 128), C::A_TILE / 2, 1024);
-                        const uint64_t v_hi = sdesc(sbb + kk * (UMMA_K * 2), 16, 1024);
-                        const uint64_t v_mid =
-                            sdesc(sbb + (NB > 1 ? 1 : 0) * C::B_TILE + kk * (UMMA_K * 2), 16, 1024);
-                        const uint64_t v_lo =
-                            sdesc(sbb + (NB > 1 ? 2 : 0) * C::B_TILE + kk * (UMMA_K * 2), 16, 1024);
+                        uint64_t da[NA], db[NB];
+#pragma unroll
+                        for (int i = 0; i < NA; ++i)
+                            da[i] = TRANS ? sdesc(sa + i * C::A_TILE + kk * (UMMA_K * 128),
+                                                  C::A_TILE / 2, 1024)
+                                          : sdesc(sa + i * C::A_TILE + kk * (UMMA_K * 2), 16, 1024);
+#pragma unroll
+                        for (int j = 0; j < NB; ++j)
+                            db[j] = sdesc(sbb + j * C::B_TILE + kk * (UMMA_K * 2), 16, 1024);
                         // leading product into a fresh slot
                         ok = mbar_wait(bempty + slot, ((slot_ph >> slot) & 1u) ^ 1u, p.err);
                         if (!ok) break;
                         tc_fence_after();
-                        tc_mma(tm_big + uint32_t(slot * BN), a_hi, v_hi, idesc, 0u);
+                        tc_mma(tm_big + uint32_t(slot * BN), da[0], db[0], idesc, 0u);
                         tc_commit(bfull + slot);
                         slot_ph ^= 1u << slot;
                         if (++slot == C::NSLOT) slot = 0;
-                        // lower-order products, smallest first
-                        const uint32_t acc0 = (kb > c0 || kk > 0) ? 1u : 0u;
-                        if (NB == 3) {
-                            tc_mma(acc_s, a_hi, v_lo, idesc, acc0);
-                            if (NA == 2) tc_mma(acc_s, a_lo, v_mid, idesc, 1u);
-                            tc_mma(acc_s, a_hi, v_mid, idesc, 1u);
-                            if (NA == 2) tc_mma(acc_s, a_lo, v_hi, idesc, 1u);
-                        } else if (NA == 2) {
-                            tc_mma(acc_s, a_lo, v_hi, idesc, acc0);
-                        }
+                        // lower-order products, smallest weight first
+                        uint32_t acc = (kb > c0 || kk > 0) ? 1u : 0u;
+#pragma unroll
+                        for (int w = 2; w >= 1; --w)
+#pragma unroll
+                            for (int i = 0; i < NA; ++i) {
+                                const int j = w - i;
+                                if (j < 0 || j >= NB) continue;
+                                tc_mma(acc_s, da[i], db[j], idesc, acc);
+                                acc = 1u;
+                            }
                     }
                     if (!ok) break;
                     tc_commit(empty + stage);
@@ -657,9 +676,14 @@ k_tc_prec(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
         }
     } else if (warp >= 2) {
         // ---------------------------------------------------------- epilogue
+        // PREC_EPI warps: lane quarter q = warp % 4 (the tensor-memory lanes a warp may read),
+        // column half h of the tile.
+        constexpr int HC = BN / 2;
         const int q = warp & 3;
+        const int h = (warp - 2) >> 2;
         const int row = q * 32 + lane;
         const uint32_t lane_off = uint32_t(q * 32) << 16;
+        const uint32_t col_off = uint32_t(h * HC);
         int slot = 0;
         uint32_t slot_ph = 0;
         int sbuf = 0;
@@ -668,12 +692,14 @@ k_tc_prec(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
         bool first = true;
         Seg sg;
         while (ok && next_seg(pos, sg, first)) {
-            const int r0 = (sg.u / sc.tiles_n) * BM, c0 = (sg.u % sc.tiles_n) * BN;
+            const int r0 = (sg.u / sc.tiles_n) * BM, c0 = (sg.u % sc.tiles_n) * BN + h * HC;
             const int64_t gr = int64_t(r0) + row;
-            float* pslot = sg.slot >= 0 ? p.part + ((int64_t(cta) * 2 + sg.slot) * BN) * BM : nullptr;
-            float accr[BN];
+            float* pslot = sg.slot >= 0
+                               ? p.part + ((int64_t(cta) * 2 + sg.slot) * BN + h * HC) * BM
+                               : nullptr;
+            float accr[HC];
 #pragma unroll
-            for (int j = 0; j < BN; ++j) accr[j] = 0.f;
+            for (int j = 0; j < HC; ++j) accr[j] = 0.f;
             for (int k0 = sg.k0; k0 < sg.k1 && ok; k0 += PREC_CHUNK) {
                 const int k1 = min(sg.k1, k0 + PREC_CHUNK);
                 for (int kb = k0; kb < k1 && ok; ++kb) {
@@ -682,11 +708,11 @@ k_tc_prec(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
                         if (!ok) break;
                         tc_fence_after();
 #pragma unroll
-                        for (int cc = 0; cc < BN; cc += 64) {
-                            float v[64];
-                            tmem_ld64(tm_big + lane_off + uint32_t(slot * BN + cc), v);
+                        for (int cc = 0; cc < HC; cc += 32) {
+                            float v[32];
+                            tmem_ld32(tm_big + lane_off + uint32_t(slot * BN) + col_off + uint32_t(cc), v);
 #pragma unroll
-                            for (int j = 0; j < 64; ++j) accr[cc + j] += v[j];
+                            for (int j = 0; j < 32; ++j) accr[cc + j] += v[j];
                         }
                         tc_fence_before();
                         mbar_arrive(bempty + slot);
@@ -700,11 +726,11 @@ k_tc_prec(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
                     if (!ok) break;
                     tc_fence_after();
 #pragma unroll
-                    for (int cc = 0; cc < BN; cc += 64) {
-                        float v[64];
-                        tmem_ld64(tm_small + lane_off + uint32_t(sbuf * BN + cc), v);
+                    for (int cc = 0; cc < HC; cc += 32) {
+                        float v[32];
+                        tmem_ld32(tm_small + lane_off + uint32_t(sbuf * BN) + col_off + uint32_t(cc), v);
 #pragma unroll
-                        for (int j = 0; j < 64; ++j) accr[cc + j] += v[j];
+                        for (int j = 0; j < 32; ++j) accr[cc + j] += v[j];
                     }
                     tc_fence_before();
                     mbar_arrive(sempty + sbuf);
@@ -715,10 +741,10 @@ k_tc_prec(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
             if (!ok) break;
             if (pslot) {
 #pragma unroll
-                for (int j = 0; j < BN; ++j) pslot[int64_t(j) * BM + row] = accr[j];
+                for (int j = 0; j < HC; ++j) pslot[int64_t(j) * BM + row] = accr[j];
             } else if (gr < p.M) {
 #pragma unroll
-                for (int j = 0; j < BN; ++j) {
+                for (int j = 0; j < HC; ++j) {
                     const int gc = c0 + j;
                     if (gc < p.N) {
                         float* o = p.D + gr + int64_t(gc) * p.ldd;
@@ -895,13 +921,13 @@ void run_bn(int bn, cudaStream_t st, const CUtensorMap& a0, const CUtensorMap& a
     else run<256, TRANS, NA, NB>(st, a0, a1, b0, b1, p, G);
 }
 
-template <int BN, int NA, int NB>
-void run_prec(cudaStream_t st, const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& b0,
-              const CUtensorMap& b1, const CUtensorMap& b2, Params p, int G) {
+template <int BN, bool TRANS, int NA, int NB>
+void run_prec(cudaStream_t st, const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& a2,
+              const CUtensorMap& b0, const CUtensorMap& b1, const CUtensorMap& b2, Params p, int G) {
     using C = PCfg<BN, NA, NB>;
-    auto kern = k_tc_prec<BN, NA, NB>;
+    auto kern = k_tc_prec<BN, TRANS, NA, NB>;
     QB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
-    kern<<<G, NUM_THREADS, C::SMEM, st>>>(a0, a1, b0, b1, b2, p);
+    kern<<<G, PREC_THREADS, C::SMEM, st>>>(a0, a1, a2, b0, b1, b2, p);
     QB_LAUNCHED();
     if (p.s.streamk) {
         const dim3 grid(unsigned(p.s.tiles_m * p.s.tiles_n), unsigned(BM * BN / 256));
@@ -910,12 +936,12 @@ void run_prec(cudaStream_t st, const CUtensorMap& a0, const CUtensorMap& a1, con
     }
 }
 
-template <int NA, int NB>
+template <bool TRANS, int NA, int NB>
 void run_prec_bn(int bn, cudaStream_t st, const CUtensorMap& a0, const CUtensorMap& a1,
-                 const CUtensorMap& b0, const CUtensorMap& b1, const CUtensorMap& b2, Params p,
-                 int G) {
-    if (bn == 64) run_prec<64, NA, NB>(st, a0, a1, b0, b1, b2, p, G);
-    else run_prec<128, NA, NB>(st, a0, a1, b0, b1, b2, p, G);
+                 const CUtensorMap& a2, const CUtensorMap& b0, const CUtensorMap& b1,
+                 const CUtensorMap& b2, Params p, int G) {
+    if (bn == 64) run_prec<64, TRANS, NA, NB>(st, a0, a1, a2, b0, b1, b2, p, G);
+    else run_prec<128, TRANS, NA, NB>(st, a0, a1, a2, b0, b1, b2, p, G);
 }
 
 struct Scratch {
@@ -949,8 +975,15 @@ Sched make_sched(int64_t M, int64_t N, int64_t K, int bn, int G) {
     s.tiles_n = int(cdiv(N, bn));
     s.kb = int(cdiv(K, BK));
     const int64_t units = int64_t(s.tiles_m) * s.tiles_n;
-    // raster when there are enough units for ~8 waves; stream-K otherwise
-    s.streamk = units < 8LL * G ? 1 : 0;
+    // Stream-K balances the k-blocks exactly but costs a fix-up launch and partial-tile traffic
+    // (worth about 8 k-blocks); raster runs whole units in ceil(units / G) waves.  Take stream-K
+    // below ~8 waves when it is the shorter of the two.  With several column tiles, raster CTAs
+    // of one row tile walk k together and share each A tile through L2, while stream-K CTAs sit
+    // at unrelated k positions and read A once per column tile: raster then, unless there is
+    // less than one wave of units.
+    const int64_t waves = (units + G - 1) / G;
+    s.streamk = (units < 8LL * G && (units * s.kb) / G + 8 < waves * s.kb &&
+                 (s.tiles_n == 1 || units < G)) ? 1 : 0;
     return s;
 }
 
@@ -1059,14 +1092,82 @@ void tc_trans(cudaStream_t st, const bf16* A_hi, const bf16* A_lo, int64_t lda, 
     }
     const CUtensorMap a1 = A_lo ? make_map(A_lo, n, m, lda, 64, BK) : a0;
     if (mode == 2) {
-        if (A_lo) run_prec_bn<2, 1>(bn, st, a0, a1, b0, b0, b0, p, G);
-        else run_prec_bn<1, 1>(bn, st, a0, a0, b0, b0, b0, p, G);
+        if (A_lo) run_prec_bn<true, 2, 1>(bn, st, a0, a1, a1, b0, b0, b0, p, G);
+        else run_prec_bn<true, 1, 1>(bn, st, a0, a0, a0, b0, b0, b0, p, G);
         return;
     }
     const CUtensorMap b1 = make_map(s.vmid, m, w, ldo, BK, bn);
     const CUtensorMap b2 = make_map(s.vlo, m, w, ldo, BK, bn);
-    if (A_lo) run_prec_bn<2, 3>(bn, st, a0, a1, b0, b1, b2, p, G);
-    else run_prec_bn<1, 3>(bn, st, a0, a0, b0, b1, b2, p, G);
+    if (A_lo) run_prec_bn<true, 2, 3>(bn, st, a0, a1, a1, b0, b1, b2, p, G);
+    else run_prec_bn<true, 1, 3>(bn, st, a0, a0, a0, b0, b1, b2, p, G);
+}
+
+// D (M x N, column-major, ldd) = alpha op(A) V + beta D with A given exactly by na bf16 terms
+// (shared leading dimension lda, 16-byte aligned) and V float32 column-major K x N (ldv), split
+// exactly into three bf16 terms on the fly; N <= 64.
+//   trans = false: A is M rows x K columns row-major (op(A) = A; the "TN" product X^T V for a
+//                  column-major K x M matrix X);
+//   trans = true : A is K rows x M columns row-major (op(A) = A^T; the "NN" product X V for a
+//                  column-major M x K matrix X).
+// Leading product per MMA in registers (round-to-nearest), lower-order products with weight
+// >= 2^-18 in a tensor-memory chain; float32-level accuracy.
+void tc_prec_gemm(cudaStream_t st, bool trans, const bf16* const* A, int na, int64_t lda,
+                  int64_t M, int64_t K, const float* V, int64_t ldv, int64_t N, float alpha,
+                  float beta, float* D, int64_t ldd, void* scratch, size_t scratch_bytes) {
+    if (M <= 0 || N <= 0) return;
+    if (na < 1 || na > 3 || N > 64 || lda % 8 != 0)
+        throw Error{QB_ERR_INVALID_ARG, "tc_prec_gemm shape"};
+    Scratch s = carve(scratch, scratch_bytes, K, N);
+    const int64_t ldo = align_up(std::max<int64_t>(K, 1), 8);
+    if (K > 0) {
+        k_split3_bf16<<<unsigned(cdiv(K * N, 256)), 256, 0, st>>>(V, ldv, K, N, s.vhi, s.vmid, s.vlo,
+                                                                  ldo);
+        QB_LAUNCHED();
+    }
+    const int bn = 64;
+    Params p{};
+    p.M = int(M);
+    p.N = int(N);
+    p.K = int(std::max<int64_t>(K, 1));
+    p.chunk = 1;
+    p.alpha = alpha;
+    p.beta = beta;
+    int G = num_sms();
+    p.s = make_sched(M, N, std::max<int64_t>(K, 1), bn, G);
+    G = grid_size(p.s, G);
+    p.D = D;
+    p.ldd = ldd;
+    p.part = s.part;
+    p.err = s.err;
+    if (p.s.streamk && size_t(G) * 2 * bn * BM * sizeof(float) > s.part_bytes)
+        throw Error{QB_ERR_WORKSPACE, "tensor-core partials"};
+    const int64_t Kd = std::max<int64_t>(K, 1);
+    CUtensorMap am[3];
+    for (int i = 0; i < 3; ++i) {
+        const bf16* ai = A[std::min(i, na - 1)];
+        am[i] = trans ? make_map(ai, M, Kd, lda, 64, BK) : make_map(ai, Kd, M, lda, BK, BM);
+    }
+    const CUtensorMap b0 = make_map(s.vhi, Kd, N, ldo, BK, bn);
+    const CUtensorMap b1 = make_map(s.vmid, Kd, N, ldo, BK, bn);
+    const CUtensorMap b2 = make_map(s.vlo, Kd, N, ldo, BK, bn);
+    if (trans) {
+        if (na == 3) run_prec<64, true, 3, 3>(st, am[0], am[1], am[2], b0, b1, b2, p, G);
+        else if (na == 2) run_prec<64, true, 2, 3>(st, am[0], am[1], am[2], b0, b1, b2, p, G);
+        else run_prec<64, true, 1, 3>(st, am[0], am[1], am[2], b0, b1, b2, p, G);
+    } else {
+        if (na == 3) run_prec<64, false, 3, 3>(st, am[0], am[1], am[2], b0, b1, b2, p, G);
+        else if (na == 2) run_prec<64, false, 2, 3>(st, am[0], am[1], am[2], b0, b1, b2, p, G);
+        else run_prec<64, false, 1, 3>(st, am[0], am[1], am[2], b0, b1, b2, p, G);
+    }
+}
+
+// Three exact bf16 terms of a float32 column-major block (hi + mid + lo == X).
+void split3_bf16(cudaStream_t st, const float* X, int64_t ldx, int64_t rows, int64_t cols, bf16* hi,
+                 bf16* mid, bf16* lo, int64_t ldo) {
+    if (rows <= 0 || cols <= 0) return;
+    k_split3_bf16<<<unsigned(cdiv(rows * cols, 256)), 256, 0, st>>>(X, ldx, rows, cols, hi, mid, lo,
+                                                                    ldo);
+    QB_LAUNCHED();
 }
 
 // T (j0 x bw, col-major, ldt) = X^T P for X column-major rows x j0 held as bf16 hi [+ lo] (ldx),

@@ -330,6 +330,9 @@ struct CoopArgs {
     unsigned* bar;      // [0] arrivals, [1] generation
     int* flags;         // flags[1]: breakdown
     int* err;           // set when a grid barrier wait timed out
+    bf16* out_hi;       // optional bf16 copy of the result: hi = bf16(P) ...
+    bf16* out_lo;       // ... lo = bf16(P - hi) (nullable)
+    int64_t ldo;
 };
 
 __device__ __forceinline__ uint64_t coop_timer() {
@@ -519,7 +522,14 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) k_cholqr_coop(CoopArgs p) {
     __syncthreads();
     for (int e = tid; e < nr * MAXB; e += COOP_THREADS) {
         const int r = e % nr, col = e / nr;
-        if (col < bi) p.P[r0 + r + int64_t(col) * p.ldp] = Ps[r][col];
+        if (col >= bi) continue;
+        const float v = Ps[r][col];
+        p.P[r0 + r + int64_t(col) * p.ldp] = v;
+        if (p.out_hi) {
+            const bf16 h = __float2bfloat16_rn(v);
+            p.out_hi[r0 + r + int64_t(col) * p.ldo] = h;
+            if (p.out_lo) p.out_lo[r0 + r + int64_t(col) * p.ldo] = __float2bfloat16_rn(v - __bfloat162float(h));
+        }
     }
 }
 
@@ -702,7 +712,7 @@ size_t cholqr_coop_scratch_bytes() {
 
 bool cholqr_coop(cudaStream_t st, float* P, int64_t ldp, int64_t rows, int bi, int passes,
                  double tau, double* rinv_out, void* scratch, size_t scratch_bytes, unsigned* bar,
-                 int* flags, int* err) {
+                 int* flags, int* err, bf16* out_hi, bf16* out_lo, int64_t ldo) {
     static int max_ctas = -1;
     constexpr size_t sm = sizeof(float) * (COOP_ROWS * PLD + 4 * MAXB * CLD);
     if (max_ctas < 0) {
@@ -735,6 +745,9 @@ bool cholqr_coop(cudaStream_t st, float* P, int64_t ldp, int64_t rows, int bi, i
     a.bar = bar;
     a.flags = flags;
     a.err = err;
+    a.out_hi = out_hi;
+    a.out_lo = out_hi ? out_lo : nullptr;
+    a.ldo = ldo;
     void* args[] = {&a};
     QB_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(k_cholqr_coop), dim3(G),
                                         dim3(COOP_THREADS), args, sm, st));

@@ -134,6 +134,15 @@ void split_bf16(cudaStream_t st, const float* V, int64_t ldv, int64_t rows, int6
 void tc_trans(cudaStream_t st, const bf16* A_hi, const bf16* A_lo, int64_t lda, int64_t m,
               int64_t n, const float* V, int64_t ldv, int64_t w, float* Z, int64_t ldz, int mode,
               void* scratch, size_t scratch_bytes);
+// D (M x N <= 64, col-major) = alpha op(A) V + beta D on the tensor cores at float32 accuracy:
+// A as na exact bf16 terms (trans = false: A row-major M x K; trans = true: A row-major K x M,
+// op(A) = A^T), V float32 column-major K x N split exactly into three bf16 terms on the fly.
+void tc_prec_gemm(cudaStream_t st, bool trans, const bf16* const* A, int na, int64_t lda,
+                  int64_t M, int64_t K, const float* V, int64_t ldv, int64_t N, float alpha,
+                  float beta, float* D, int64_t ldd, void* scratch, size_t scratch_bytes);
+// hi + mid + lo == X exactly (three bf16 terms of a float32 column-major block)
+void split3_bf16(cudaStream_t st, const float* X, int64_t ldx, int64_t rows, int64_t cols, bf16* hi,
+                 bf16* mid, bf16* lo, int64_t ldo);
 // X <- bf16(X) (pairs 1) or bf16(X) + bf16(X - bf16(X)) (pairs 2), elementwise, in place
 void round_bf16_inplace(cudaStream_t st, float* X, int64_t ldx, int64_t rows, int64_t cols,
                         int pairs);
@@ -183,11 +192,13 @@ enum CholPrec { CHOL_F64 = 0, CHOL_F64_INV_F32 = 1, CHOL_F32 = 2, CHOL_ADAPTIVE 
 // `passes` CholeskyQR passes (float32 Gram, float32 Cholesky) on a float32 rows x bi panel in one
 // cooperative launch; rinv_out (nullable) receives each pass's R^-1 (MAXB x MAXB, float64).
 // bar: two zero-initialised words kept across calls; err is set if a grid barrier timed out.
+// out_hi (nullable): also write bf16(P) there (ld ldo), and bf16(P - bf16(P)) to out_lo when given.
 // Returns false (nothing launched) when the panel does not fit the launch.
 size_t cholqr_coop_scratch_bytes();
 bool cholqr_coop(cudaStream_t st, float* P, int64_t ldp, int64_t rows, int bi, int passes,
                  double tau, double* rinv_out, void* scratch, size_t scratch_bytes, unsigned* bar,
-                 int* flags, int* err);
+                 int* flags, int* err, bf16* out_hi = nullptr, bf16* out_lo = nullptr,
+                 int64_t ldo = 0);
 void chol_rinv(cudaStream_t st, const double* W, int bi, double tau_rel, double* R,
                double* Rinv, double* R_acc, int* flags, CholPrec prec);
 void set_identity(cudaStream_t st, double* R, int bi);
