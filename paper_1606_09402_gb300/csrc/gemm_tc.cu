@@ -171,6 +171,33 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int bn, bool a_mn) {
            (uint32_t(bn >> 3) << 17) | (uint32_t(BM >> 4) << 24);
 }
 
+// Output row gr of a tile: D[gr][c0 + j] = alpha v[j] (+ beta D[gr][c0 + j]) for the NV columns
+// below n.  With beta != 0 the old values are all loaded before any store is issued (the loads do
+// not wait on one another; a load-modify-store per column would serialise them).
+template <int NV>
+__device__ __forceinline__ void store_row(float* D, int64_t ldd, int64_t gr, int c0, int n,
+                                          float alpha, float beta, const float* v) {
+    static_assert(NV % 32 == 0, "groups of 32 columns");
+    float* base = D + gr + int64_t(c0) * ldd;
+    const int nv = n - c0 < NV ? n - c0 : NV;
+    if (beta != 0.f) {
+#pragma unroll
+        for (int g = 0; g < NV; g += 32) {
+            float old[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                old[j] = g + j < nv ? __ldcg(base + int64_t(g + j) * ldd) : 0.f;
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (g + j < nv) base[int64_t(g + j) * ldd] = fmaf(alpha, v[g + j], beta * old[j]);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < NV; ++j)
+            if (j < nv) base[int64_t(j) * ldd] = alpha * v[j];
+    }
+}
+
 // ---------------------------------------------------------------- schedule
 struct Sched {
     int tiles_m, tiles_n, kb;   // units = tiles_m * tiles_n, k-blocks per unit
@@ -390,14 +417,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
 #pragma unroll
                         for (int j = 0; j < 32; ++j) slot[int64_t(cc + j) * BM + row] = v[j];
                     } else if (gr < p.M) {
-#pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            const int gc = c0 + cc + j;
-                            if (gc < p.N) {
-                                float* o = p.D + gr + int64_t(gc) * p.ldd;
-                                *o = p.beta != 0.f ? fmaf(p.alpha, v[j], p.beta * *o) : p.alpha * v[j];
-                            }
-                        }
+                        store_row<32>(p.D, p.ldd, gr, c0 + cc, p.N, p.alpha, p.beta, v);
                     }
                 }
                 tc_fence_before();
@@ -433,14 +453,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
 #pragma unroll
                     for (int j = 0; j < BN; ++j) slot[int64_t(j) * BM + row] = accr[j];
                 } else if (gr < p.M) {
-#pragma unroll
-                    for (int j = 0; j < BN; ++j) {
-                        const int gc = c0 + j;
-                        if (gc < p.N) {
-                            float* o = p.D + gr + int64_t(gc) * p.ldd;
-                            *o = p.beta != 0.f ? fmaf(p.alpha, accr[j], p.beta * *o) : p.alpha * accr[j];
-                        }
-                    }
+                    store_row<BN>(p.D, p.ldd, gr, c0, p.N, p.alpha, p.beta, accr);
                 }
             }
         }
@@ -743,14 +756,7 @@ k_tc_prec(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
 #pragma unroll
                 for (int j = 0; j < HC; ++j) pslot[int64_t(j) * BM + row] = accr[j];
             } else if (gr < p.M) {
-#pragma unroll
-                for (int j = 0; j < HC; ++j) {
-                    const int gc = c0 + j;
-                    if (gc < p.N) {
-                        float* o = p.D + gr + int64_t(gc) * p.ldd;
-                        *o = p.beta != 0.f ? fmaf(p.alpha, accr[j], p.beta * *o) : p.alpha * accr[j];
-                    }
-                }
+                store_row<HC>(p.D, p.ldd, gr, c0, p.N, p.alpha, p.beta, accr);
             }
         }
     }
