@@ -164,9 +164,20 @@ struct Ctx {
     // Fused float32 CholeskyQR passes for the power-scheme orthonormalisation (one launch).
     bool coop(void* P, int64_t ld, int64_t rows, int bi, int passes, bf16* out_hi = nullptr,
               bf16* out_lo = nullptr, int64_t ldo = 0) {
-        return cholqr_coop(st, reinterpret_cast<float*>(P), ld, rows, bi, passes, 1e-10, nullptr,
-                           coop_scr, coop_bytes, reinterpret_cast<unsigned*>(flags + 4), flags,
-                           flags + 2, out_hi, out_lo, ldo);
+        return cholqr_coop(st, reinterpret_cast<float*>(P), ld, rows, bi, passes, false, 1e-10,
+                           nullptr, coop_scr, coop_bytes, reinterpret_cast<unsigned*>(flags + 4),
+                           flags, flags + 2, out_hi, out_lo, ldo);
+    }
+    // Fused CholeskyQR2 of a Q_i panel on the mixed path (adaptive factor); with acc_r the two
+    // inverses go to the next Rchain slots.
+    bool coop_precise(void* P, int64_t ld, int64_t rows, int bi, bool acc_r) {
+        if (f64 || (acc_r && nchain > 2)) return false;
+        double* ro = acc_r ? Rchain + size_t(nchain) * MAXB * MAXB : nullptr;
+        if (!cholqr_coop(st, reinterpret_cast<float*>(P), ld, rows, bi, 2, true, tau, ro, coop_scr,
+                         coop_bytes, reinterpret_cast<unsigned*>(flags + 4), flags, flags + 2))
+            return false;
+        if (acc_r) nchain += 2;
+        return true;
     }
     void cholqr(void* P, int64_t ld, int64_t rows, int bi, bool acc_r, bool sketch = false) {
         const bool fast = sketch && !f64;
@@ -188,6 +199,7 @@ struct Ctx {
     void cholqr2(void* P, int64_t ld, int64_t rows, int bi, bool acc_r, bool sketch = false) {
         Scope sc(*this, sketch ? PH_ORTHW : PH_CHOLQR);
         if (sketch && !f64 && !acc_r && coop(P, ld, rows, bi, 2)) return;
+        if (!sketch && coop_precise(P, ld, rows, bi, acc_r)) return;
         cholqr(P, ld, rows, bi, acc_r, sketch);
         cholqr(P, ld, rows, bi, acc_r, sketch);
     }

@@ -770,10 +770,11 @@ k_tc_prec(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
     }
 }
 
-// Stream-K fix-up: D tile of unit u = sum of the partial slots of the CTAs that share it, in CTA
-// order.  A unit covered by one CTA was written directly and is skipped.  Grid: (units, BM*BN/256),
-// one output element per thread, so a unit shared by every CTA of the launch is still summed by
-// many CTAs in parallel; the slot offsets are worked out once per CTA.
+// Stream-K fix-up: D tile of unit u = sum of the partial slots of the CTAs that share it, in a
+// fixed order (four interleaved sums over the CTAs in order, then combined).  A unit covered by
+// one CTA was written directly and is skipped.  Grid: (units, BM*BN/256), one output element per
+// thread, so a unit shared by every CTA of the launch is still summed by many CTAs in parallel;
+// the slot offsets are worked out once per CTA.
 template <int BN>
 __global__ void __launch_bounds__(256) k_tc_fixup(Params p, int G) {
     __shared__ int64_t base[MAX_SK_CTAS];
@@ -807,8 +808,18 @@ __global__ void __launch_bounds__(256) k_tc_fixup(Params p, int G) {
     if (e >= BM * BN) return;
     const int row = e % BM, col = e / BM;
     const float* pp = p.part + int64_t(col) * BM + row;
-    float s = 0.f;
-    for (int t = 0; t < count; ++t) s += pp[base[t]];
+    // four interleaved partial sums keep several loads in flight; fixed combination order
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    int t = 0;
+    for (; t + 4 <= count; t += 4) {
+        const float a0 = pp[base[t]], a1 = pp[base[t + 1]], a2 = pp[base[t + 2]], a3 = pp[base[t + 3]];
+        s0 += a0;
+        s1 += a1;
+        s2 += a2;
+        s3 += a3;
+    }
+    for (; t < count; ++t) s0 += pp[base[t]];
+    const float s = (s0 + s1) + (s2 + s3);
     const int64_t gr = int64_t((u / sc.tiles_n) * BM) + row;
     const int gc = (u % sc.tiles_n) * BN + col;
     if (gr < p.M && gc < p.N) {

@@ -24,6 +24,11 @@ constexpr int LDS = MAXB + 1;
 // row j + 1 publish it (W in TF and in TI, L^-1 in TI) to shared memory, the owner of its diagonal
 // also its pivot; one barrier per step.
 constexpr int CLD = MAXB + 4;          // shared row stride: rows stay 16-byte aligned
+// Pivot test of the adaptive factorisation: a float32 factor is kept when every pivot keeps at
+// least this fraction of its column's squared norm (kappa of the panel below about 100, so the
+// float32 factor leaves the first CholeskyQR pass orthogonal to ~64 u32 kappa^2 < 0.04 and the
+// second pass restores it); otherwise the panel is refactored in float64.
+constexpr double CHOL_WEAK_REL = 1e-4;
 constexpr int CHOL_THREADS = 320;
 constexpr int CHOL_TILES = 136;        // 4 x 4 tiles in a triangle of the 16 x 16 tile grid
 constexpr int CHOL_L0 = 160;           // first thread of the L^-1 tiles
@@ -258,11 +263,6 @@ __device__ void chol_outputs(int bi, const TI (&l)[4][4], int lr, int lc, TF (*S
     }
 }
 
-// Pivot test of the adaptive factorisation: a float32 factor is kept when every pivot keeps at
-// least this fraction of its column's squared norm (kappa of the panel below about 100, so the
-// float32 factor leaves the first CholeskyQR pass orthogonal to ~64 u32 kappa^2 < 0.04 and the
-// second pass restores it); otherwise the panel is refactored in float64.
-constexpr double CHOL_WEAK_REL = 1e-4;
 
 // Standalone factorisation.  ADAPT: float32 first, float64 (TF) when a pivot is weak.
 template <class TF, class TI, bool ADAPT>
@@ -310,14 +310,24 @@ k_chol(const double* __restrict__ W, int bi, double tau_rel, double* __restrict_
 // One cooperative launch runs `passes` CholeskyQR passes on a float32 rows x bi panel: every CTA
 // keeps its slice of rows in shared memory for the whole call, forms the partial Gram of the slice,
 // the CTAs sum the partials (each CTA an equal share of the entries, in CTA order), every CTA
-// factors the 64 x 64 Gram itself (chol_core; the same arithmetic in every CTA, so the same R),
-// and applies R^-1 to its rows.  The panel is read and written once.  Grid-wide barriers use a
-// global arrive counter and generation word; every wait is bounded and a timeout sets err.
+// factors the 64 x 64 Gram itself (the same arithmetic in every CTA, so the same R), and applies
+// R^-1 to its rows.  The panel is read and written once.  Grid-wide barriers use a global arrive
+// counter and generation word; every wait is bounded and a timeout sets err.
+//
+// PRECISE = false (power scheme, only the span matters): float32 Gram and factor.
+// PRECISE = true (Q_i of the randQB loops): the Gram is summed in two levels (float32 over 8 rows,
+// then a float32 pair) and factored in float32 when every pivot keeps >= CHOL_WEAK_REL of its
+// column's squared norm (the panel's kappa is then below ~100 and a float32-accurate Gram is
+// enough); otherwise the Gram is formed again with exact products and float32-pair sums and
+// factored in float64, as the unfused path does.
 constexpr int COOP_THREADS = 512;
-constexpr int COOP_ROWS = 512;      // rows per CTA held in shared memory
+constexpr int COOP_ROWS = 480;      // rows per CTA held in shared memory
 constexpr int COOP_MAX_CTAS = 256;
 constexpr int PLD = MAXB + 1;       // shared row stride of the panel slice
 constexpr uint64_t COOP_WAIT_NS = 2000000000ull;
+// dynamic shared memory: panel slice, then S (float64 size), Sf, Li, Rs
+constexpr size_t COOP_SMEM = sizeof(float) * COOP_ROWS * PLD + sizeof(double) * MAXB * CLD +
+                             3 * sizeof(float) * MAXB * CLD;
 
 struct CoopArgs {
     float* P;
@@ -325,8 +335,8 @@ struct CoopArgs {
     int bi, passes;
     double tau;
     double* rinv_out;   // passes x (MAXB x MAXB) or null
-    float* part;        // gridDim.x x (MAXB x MAXB) partial Grams
-    float* wred;        // MAXB x MAXB summed Gram
+    double* part;       // gridDim.x x (MAXB x MAXB) partial Grams
+    double* wred;       // MAXB x MAXB summed Gram
     unsigned* bar;      // [0] arrivals, [1] generation
     int* flags;         // flags[1]: breakdown
     int* err;           // set when a grid barrier wait timed out
@@ -375,16 +385,34 @@ __device__ bool coop_sync(unsigned* bar, int* err) {
     return ok_s != 0;
 }
 
+// float32 pair accumulation of exact products (the float32-pair Gram)
+__device__ __forceinline__ void df_add(float& hi, float& lo, float a, float b) {
+    const float p = a * b;
+    const float e = fmaf(a, b, -p);
+    const float s = hi + p;
+    const float bb = s - hi;
+    lo += ((hi - (s - bb)) + (p - bb)) + e;
+    hi = s;
+}
+__device__ __forceinline__ void df_add_sum(float& hi, float& lo, float v) {
+    const float s = hi + v;
+    const float bb = s - hi;
+    lo += (hi - (s - bb)) + (v - bb);
+    hi = s;
+}
+
+template <bool PRECISE>
 __global__ void __launch_bounds__(COOP_THREADS, 1) k_cholqr_coop(CoopArgs p) {
     extern __shared__ __align__(16) unsigned char coop_smem[];
     float (*Ps)[PLD] = reinterpret_cast<float (*)[PLD]>(coop_smem);
     unsigned char* rest = coop_smem + sizeof(float) * COOP_ROWS * PLD;
-    float (*S)[CLD] = reinterpret_cast<float (*)[CLD]>(rest);
-    float (*Sf)[CLD] = reinterpret_cast<float (*)[CLD]>(rest + sizeof(float) * MAXB * CLD);
-    float (*Li)[CLD] = reinterpret_cast<float (*)[CLD]>(rest + 2 * sizeof(float) * MAXB * CLD);
-    float (*Rs)[CLD] = reinterpret_cast<float (*)[CLD]>(rest + 3 * sizeof(float) * MAXB * CLD);
-    float* scratch = reinterpret_cast<float*>(rest);   // Gram combine space (S and Sf, 2 x 17 KB)
-    __shared__ float dpiv[MAXB], invd[MAXB], idiag[MAXB], diag0[MAXB], dmax_s;
+    unsigned char* sreg = rest;                                           // S (float or double)
+    float (*Sf)[CLD] = reinterpret_cast<float (*)[CLD]>(rest + sizeof(double) * MAXB * CLD);
+    float (*Li)[CLD] = reinterpret_cast<float (*)[CLD]>(rest + (sizeof(double) + sizeof(float)) * MAXB * CLD);
+    float (*Rs)[CLD] = reinterpret_cast<float (*)[CLD]>(rest + (sizeof(double) + 2 * sizeof(float)) * MAXB * CLD);
+    double* scratch = reinterpret_cast<double*>(rest);   // Gram combine space (S and Sf regions)
+    __shared__ float fpiv[MAXB], finvd[MAXB], fidiag[MAXB], fdiag0[MAXB], fdmax;
+    __shared__ double dpiv[MAXB], dinvd[MAXB], didiag[MAXB], ddiag0[MAXB], ddmax;
     __shared__ int weak_s;
     __shared__ double red[16][32];
     const int tid = threadIdx.x;
@@ -406,15 +434,16 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) k_cholqr_coop(CoopArgs p) {
         while (t >= 16 - gi) { t -= 16 - gi; ++gi; }
         gj = gi + t;
     }
-    for (int pass = 0; pass < p.passes; ++pass) {
+    // partial Gram of the slice into p.part[cta]; mode 0 float32, 1 two-level, 2 exact products
+    auto gram = [&](int mode) {
         __syncthreads();
-        // ---- partial Gram of this slice
         if (grp < 3) {
-            float acc[4][4];
+            float hi[4][4], lo[4][4], ch[4][4];
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+                for (int b = 0; b < 4; ++b) hi[a][b] = lo[a][b] = ch[a][b] = 0.f;
+            int cnt = 0;
             for (int r = grp; r < nr; r += 3) {
                 float x[4], y[4];
 #pragma unroll
@@ -422,58 +451,98 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) k_cholqr_coop(CoopArgs p) {
                     x[q] = Ps[r][gi * 4 + q];
                     y[q] = Ps[r][gj * 4 + q];
                 }
+                if (mode == 2) {
 #pragma unroll
-                for (int a = 0; a < 4; ++a)
+                    for (int a = 0; a < 4; ++a)
 #pragma unroll
-                    for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(x[a], y[b], acc[a][b]);
+                        for (int b = 0; b < 4; ++b) df_add(hi[a][b], lo[a][b], x[a], y[b]);
+                } else {
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) ch[a][b] = fmaf(x[a], y[b], ch[a][b]);
+                    if (mode == 1 && ++cnt == 8) {
+                        cnt = 0;
+#pragma unroll
+                        for (int a = 0; a < 4; ++a)
+#pragma unroll
+                            for (int b = 0; b < 4; ++b) {
+                                df_add_sum(hi[a][b], lo[a][b], ch[a][b]);
+                                ch[a][b] = 0.f;
+                            }
+                    }
+                }
             }
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int b = 0; b < 4; ++b) scratch[(grp * 136 + blk) * 16 + a * 4 + b] = acc[a][b];
+                for (int b = 0; b < 4; ++b) {
+                    const double v = mode == 0 ? double(ch[a][b])
+                                               : double(hi[a][b]) + double(lo[a][b]) + double(ch[a][b]);
+                    scratch[(grp * 136 + blk) * 16 + a * 4 + b] = v;
+                }
         }
         __syncthreads();
         if (tid < 136) {
-            float* out = p.part + int64_t(cta) * MAXB * MAXB;
+            double* out = p.part + int64_t(cta) * MAXB * MAXB;
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
-                const float v = scratch[blk * 16 + q] + scratch[(136 + blk) * 16 + q] +
-                                scratch[(272 + blk) * 16 + q];
+                const double v = scratch[blk * 16 + q] + scratch[(136 + blk) * 16 + q] +
+                                 scratch[(272 + blk) * 16 + q];
                 out[(gi * 4 + q / 4) + (gj * 4 + q % 4) * MAXB] = v;
             }
         }
-        if (!coop_sync(p.bar, p.err)) return;
-        // ---- sum the partials: this CTA owns entries [e0, e0 + 32 * nchunk)
-        {
-            const int per = (MAXB * MAXB + G - 1) / G;
-            const int e0 = cta * per, e1 = min(MAXB * MAXB, e0 + per);
-            const int lane = tid & 31, sub = tid >> 5;   // 16 subsets of the partials
-            for (int eb = e0; eb < e1; eb += 32) {
-                const int e = eb + lane;
-                double v = 0.0;
-                if (e < e1 && e % MAXB <= e / MAXB)
-                    for (int q = sub; q < G; q += 16)
-                        v += double(__ldcg(p.part + int64_t(q) * MAXB * MAXB + e));
-                red[sub][lane] = v;
-                __syncthreads();
-                if (sub == 0 && e < e1) {
-                    double t = 0.0;
+    };
+    // sum the partials: this CTA owns an equal share of the upper entries
+    auto reduce = [&]() {
+        const int per = (MAXB * MAXB + G - 1) / G;
+        const int e0 = cta * per, e1 = min(MAXB * MAXB, e0 + per);
+        const int lane = tid & 31, sub = tid >> 5;   // 16 subsets of the partials
+        for (int eb = e0; eb < e1; eb += 32) {
+            const int e = eb + lane;
+            double v = 0.0;
+            if (e < e1 && e % MAXB <= e / MAXB)
+                for (int q = sub; q < G; q += 16) v += __ldcg(p.part + int64_t(q) * MAXB * MAXB + e);
+            red[sub][lane] = v;
+            __syncthreads();
+            if (sub == 0 && e < e1) {
+                double t = 0.0;
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) t += red[q][lane];
-                    p.wred[e] = float(t);
-                }
-                __syncthreads();
+                for (int q = 0; q < 16; ++q) t += red[q][lane];
+                p.wred[e] = t;
             }
+            __syncthreads();
         }
+    };
+    auto ldw = [&](int i, int j) { return __ldcg(p.wred + i + j * MAXB); };
+    for (int pass = 0; pass < p.passes; ++pass) {
+        gram(PRECISE ? 1 : 0);
+        if (!coop_sync(p.bar, p.err)) return;
+        reduce();
         if (!coop_sync(p.bar, p.err)) return;
         // ---- every CTA factors the summed Gram
         float l[4][4];
         int lr, lc;
-        chol_core<float, float>(bi, p.tau, 0.0, cta == 0 ? p.flags : nullptr,
-                                [&](int i, int j) { return __ldcg(p.wred + i + j * MAXB); },
-                                CholShared<float, float>{S, Sf, Li, dpiv, invd, idiag, diag0,
-                                                         &dmax_s, &weak_s},
+        float (*Sfl)[CLD] = reinterpret_cast<float (*)[CLD]>(sreg);
+        chol_core<float, float>(bi, p.tau, PRECISE ? CHOL_WEAK_REL : 0.0,
+                                (cta == 0 && !PRECISE) ? p.flags : nullptr, ldw,
+                                CholShared<float, float>{Sfl, Sf, Li, fpiv, finvd, fidiag, fdiag0,
+                                                         &fdmax, &weak_s},
                                 l, lr, lc);
+        bool dbl = false;
+        if (PRECISE && weak_s) {
+            // ill-conditioned panel: exact-product Gram, float64 factor
+            dbl = true;
+            gram(2);
+            if (!coop_sync(p.bar, p.err)) return;
+            reduce();
+            if (!coop_sync(p.bar, p.err)) return;
+            double (*Sd)[CLD] = reinterpret_cast<double (*)[CLD]>(sreg);
+            chol_core<double, float>(bi, p.tau, 0.0, cta == 0 ? p.flags : nullptr, ldw,
+                                     CholShared<double, float>{Sd, Sf, Li, dpiv, dinvd, didiag,
+                                                               ddiag0, &ddmax, &weak_s},
+                                     l, lr, lc);
+        }
         // R^-1[c][a] = L^-1[a][c] / sqrt(d_a); strictly lower tiles are zero
         double* ro = (cta == 0 && p.rinv_out) ? p.rinv_out + int64_t(pass) * MAXB * MAXB : nullptr;
         for (int e = tid; e < MAXB * MAXB; e += COOP_THREADS) {
@@ -489,7 +558,8 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) k_cholqr_coop(CoopArgs p) {
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const int a = 4 * lr + r, c = 4 * lc + q;
-                    const float v = (a < bi && c < bi) ? l[r][q] * idiag[a] : 0.f;
+                    const float id = dbl ? float(didiag[a < MAXB ? a : 0]) : fidiag[a < MAXB ? a : 0];
+                    const float v = (a < bi && c < bi) ? l[r][q] * id : 0.f;
                     Rs[c][a] = v;
                     if (ro) ro[c + a * MAXB] = v;
                 }
@@ -707,26 +777,27 @@ void chol_rinv(cudaStream_t st, const double* W, int bi, double tau_rel, double*
 }
 
 size_t cholqr_coop_scratch_bytes() {
-    return size_t(COOP_MAX_CTAS) * MAXB * MAXB * sizeof(float) + MAXB * MAXB * sizeof(float) + 256;
+    return size_t(COOP_MAX_CTAS) * MAXB * MAXB * sizeof(double) + MAXB * MAXB * sizeof(double) + 256;
 }
 
 bool cholqr_coop(cudaStream_t st, float* P, int64_t ldp, int64_t rows, int bi, int passes,
-                 double tau, double* rinv_out, void* scratch, size_t scratch_bytes, unsigned* bar,
-                 int* flags, int* err, bf16* out_hi, bf16* out_lo, int64_t ldo) {
-    static int max_ctas = -1;
-    constexpr size_t sm = sizeof(float) * (COOP_ROWS * PLD + 4 * MAXB * CLD);
-    if (max_ctas < 0) {
+                 bool precise, double tau, double* rinv_out, void* scratch, size_t scratch_bytes,
+                 unsigned* bar, int* flags, int* err, bf16* out_hi, bf16* out_lo, int64_t ldo) {
+    static int max_ctas[2] = {-1, -1};
+    const int v = precise ? 1 : 0;
+    auto kern = precise ? k_cholqr_coop<true> : k_cholqr_coop<false>;
+    if (max_ctas[v] < 0) {
         int dev = 0, coop = 0, per_sm = 0;
         QB_CUDA(cudaGetDevice(&dev));
         QB_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
-        QB_CUDA(cudaFuncSetAttribute(k_cholqr_coop, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     int(sm)));
-        QB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cholqr_coop, COOP_THREADS,
-                                                               sm));
-        max_ctas = coop ? std::min(per_sm * num_sms(), COOP_MAX_CTAS) : 0;
+        QB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     int(COOP_SMEM)));
+        QB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, COOP_THREADS,
+                                                               COOP_SMEM));
+        max_ctas[v] = coop ? std::min(per_sm * num_sms(), COOP_MAX_CTAS) : 0;
     }
-    if (max_ctas <= 0 || bi < 1 || bi > MAXB || rows <= 0 || passes < 1) return false;
-    int G = int(std::min<int64_t>(max_ctas, cdiv(rows, 64)));
+    if (max_ctas[v] <= 0 || bi < 1 || bi > MAXB || rows <= 0 || passes < 1) return false;
+    int G = int(std::min<int64_t>(max_ctas[v], cdiv(rows, 64)));
     const int64_t rows_per = cdiv(rows, G);
     if (rows_per > COOP_ROWS) return false;
     G = int(cdiv(rows, rows_per));
@@ -740,7 +811,7 @@ bool cholqr_coop(cudaStream_t st, float* P, int64_t ldp, int64_t rows, int bi, i
     a.passes = passes;
     a.tau = tau;
     a.rinv_out = rinv_out;
-    a.part = reinterpret_cast<float*>(scratch);
+    a.part = reinterpret_cast<double*>(scratch);
     a.wred = a.part + size_t(COOP_MAX_CTAS) * MAXB * MAXB;
     a.bar = bar;
     a.flags = flags;
@@ -749,8 +820,8 @@ bool cholqr_coop(cudaStream_t st, float* P, int64_t ldp, int64_t rows, int bi, i
     a.out_lo = out_hi ? out_lo : nullptr;
     a.ldo = ldo;
     void* args[] = {&a};
-    QB_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(k_cholqr_coop), dim3(G),
-                                        dim3(COOP_THREADS), args, sm, st));
+    QB_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(kern), dim3(G), dim3(COOP_THREADS),
+                                        args, COOP_SMEM, st));
     QB_LAUNCHED();
     return true;
 }
