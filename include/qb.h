@@ -110,6 +110,12 @@ typedef struct {
 /* qb_opts.flags: record CUDA events around the phases of the call (adds a synchronisation at the
  * end); read the device milliseconds with qb_profile_last(). */
 #define QB_FLAG_PROFILE 2
+/* qb_opts.flags (randQB_FP): form each Omega batch of l~ columns in one go, 2 + 2P passes over A
+ * per batch as Algorithm 4 is written.  By default the batch is formed in chunks of 512 columns
+ * as the blocked loop reaches them (P <= 1): the same Q and B up to rounding (orth is
+ * column-causal), the columns after the stopping block are never formed, at 2 + 2P passes per
+ * chunk.  With P > 1 the batch is always formed in one go. */
+#define QB_FLAG_WHOLE_BATCH 4
 
 typedef struct {
     int64_t rank;        /* columns of Q / rows of B that are valid */

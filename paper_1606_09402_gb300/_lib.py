@@ -26,7 +26,7 @@ QB_BIT_TOL_FLOOR = 2
 QB_BIT_NOT_CONVERGED = 4
 
 QB_F64, QB_F32, QB_BF16, QB_BF16X2 = 0, 1, 2, 3
-QB_FLAG_SIMT_APASS, QB_FLAG_PROFILE = 1, 2
+QB_FLAG_SIMT_APASS, QB_FLAG_PROFILE, QB_FLAG_WHOLE_BATCH = 1, 2, 4
 PHASES = ("omega", "sketch", "trans", "power_orth", "projections", "cholqr2", "fp_b_formula",
           "indicator")
 QB_PREC_FP64, QB_PREC_MIXED = 0, 1

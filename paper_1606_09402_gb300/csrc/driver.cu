@@ -49,7 +49,8 @@ namespace {
 constexpr double U64 = 1.1102230246251565e-16;   // 2^-53
 constexpr double U32 = 5.9604644775390625e-08;   // 2^-24
 constexpr double THM3_DELTA = 0.01;
-constexpr int64_t H_CHUNK = 512;   // randQB_FP: columns of H = A^T G formed at a time
+constexpr int64_t H_CHUNK = 512;    // randQB_FP: columns of H = A^T G formed at a time
+constexpr int64_t FP_CHUNK = 512;   // randQB_FP: Omega columns carried through the power scheme together
 
 // ------------------------------------------------------------------------------------ context
 struct Ctx {
@@ -82,8 +83,10 @@ struct Ctx {
     bf16* qs[3] = {nullptr, nullptr, nullptr};
     bf16* bs[3] = {nullptr, nullptr, nullptr};
     int64_t ldqs = 0, ldbs = 0;
-    bf16* xb_hi = nullptr;    // bf16 shadow of the panels finished so far (hi, lo)
-    bf16* xb_lo = nullptr;
+    // bf16 shadows of the power-scheme panels finished so far: set 0 for G (hi), set 1 for Omega
+    // (hi, lo); separate, because the chunks of a batch alternate between the two orthonormalisations
+    bf16* xb_hi[2] = {nullptr, nullptr};
+    bf16* xb_lo[2] = {nullptr, nullptr};
     int64_t xb_ld = 0;
     bool prof = false;        // QB_FLAG_PROFILE: CUDA events around the phases of the loop
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> events;
@@ -288,9 +291,15 @@ struct Ctx {
     // against a bf16 shadow of the finished panels: bf16 only for G (one pass; any well-conditioned
     // basis will do), bf16 hi + lo with three products for Omega (its residual overlap with earlier
     // panels leaks sigma_1^2-sized terms into the B_i formula).
-    void orth_wide(void* X, int64_t ld, int64_t rows, int64_t w, int b, void* T, bool reorth = true) {
-        const bool tc = !f64 && xb_hi && rows % 8 == 0 && rows <= xb_ld;
-        bf16* lo = reorth ? xb_lo : nullptr;
+    // Panels from column j_begin on are orthonormalised against all columns before them (the
+    // columns before j_begin are already final): the result is column-causal, the first k columns
+    // depend only on the first k input columns.
+    void orth_wide(void* X, int64_t ld, int64_t rows, int64_t w, int b, void* T, bool reorth = true,
+                   int64_t j_begin = 0) {
+        const int set = reorth ? 1 : 0;
+        bf16* hi = xb_hi[set];
+        const bool tc = !f64 && hi && rows % 8 == 0 && rows <= xb_ld;
+        bf16* lo = reorth ? xb_lo[set] : nullptr;
         auto project = [&](int64_t j0, char* Pj, int bj) {
             if (j0 <= 0) return;
             if (!tc) {
@@ -298,16 +307,16 @@ struct Ctx {
                 return;
             }
             Scope sc(*this, PH_ORTHW);
-            tc_xtp(st, xb_hi, lo, xb_ld, rows, j0, reinterpret_cast<const float*>(Pj), ld, bj,
+            tc_xtp(st, hi, lo, xb_ld, rows, j0, reinterpret_cast<const float*>(Pj), ld, bj,
                    reinterpret_cast<float*>(T), j0, tcs, tcs_bytes);
-            tc_p_minus_xt(st, xb_hi, lo, xb_ld, rows, j0, reinterpret_cast<const float*>(T), j0,
+            tc_p_minus_xt(st, hi, lo, xb_ld, rows, j0, reinterpret_cast<const float*>(T), j0,
                           bj, reinterpret_cast<float*>(Pj), ld, tcs, tcs_bytes);
         };
-        for (int64_t j0 = 0; j0 < w; j0 += b) {
+        for (int64_t j0 = j_begin; j0 < w; j0 += b) {
             const int bj = int(std::min<int64_t>(b, w - j0));
             char* Pj = col(X, ld, j0);
             // the last orthonormalisation of the panel also writes its bf16 shadow when fused
-            bf16* shi = tc ? xb_hi + j0 * xb_ld : nullptr;
+            bf16* shi = tc ? hi + j0 * xb_ld : nullptr;
             bf16* slo = tc && lo ? lo + j0 * xb_ld : nullptr;
             const bool again = j0 > 0 && (reorth || f64);
             bool shadow = false;
@@ -554,7 +563,9 @@ void setup_ctx(Ctx& c, bool f64) {
 struct Bufs {
     char* Om = nullptr;   // n x lt
     char* Z = nullptr;    // n x b (EI power) or n x b S (FP)
-    char* G = nullptr;    // m x lt (FP)
+    char* G = nullptr;    // m x lt (FP): G = A Omega of the processed Omega
+    char* Gp = nullptr;   // m x lt (FP, P > 0): the power scheme's orthonormal G; kept apart
+                          // from G because later chunks project against its earlier columns
     char* H = nullptr;    // n x lt (FP)
     char* Ys = nullptr;   // m x b (FP)
     char* T1 = nullptr;   // cap x lt
@@ -572,6 +583,7 @@ void reserve_all(Arena& ar, Ctx& c, AOp& A, const Plan& p, bool fp, Bufs& bf) {
     bf.C2 = ar.get<char>(std::max<int64_t>(p.cap, 1) * p.b * es);
     if (fp) {
         bf.G = ar.get<char>(p.m * p.lt * es);
+        if (p.P > 0) bf.Gp = ar.get<char>(p.m * p.lt * es);
         bf.H = ar.get<char>(p.n * p.lt * es);
         bf.Ys = ar.get<char>(p.m * p.b * es);
         bf.Tw = ar.get<char>(p.lt * p.b * es);
@@ -580,8 +592,9 @@ void reserve_all(Arena& ar, Ctx& c, AOp& A, const Plan& p, bool fp, Bufs& bf) {
     if (!c.f64 && A.tc_scratch(&c.tcs, &c.tcs_bytes)) {
         if (fp && p.P > 0) {
             c.xb_ld = align_up(std::max(p.m, p.n), 8);
-            c.xb_hi = ar.get<bf16>(c.xb_ld * p.lt);
-            c.xb_lo = ar.get<bf16>(c.xb_ld * p.lt);
+            c.xb_hi[0] = ar.get<bf16>(c.xb_ld * p.lt);
+            c.xb_hi[1] = ar.get<bf16>(c.xb_ld * p.lt);
+            c.xb_lo[1] = ar.get<bf16>(c.xb_ld * p.lt);
         }
         const int64_t cap = std::max<int64_t>(p.cap, 1);
         c.ldqs = align_up(p.m, 8);
@@ -667,92 +680,109 @@ void run_fp(Ctx& c, AOp& A, const Plan& p, const qb_opts& o, Bufs& bf, void* Q, 
             void* B, int64_t ldb, double eps2, RunOut& out) {
     const int64_t m = p.m, n = p.n;
     const int omega_dt = c.f64 ? QB_F64 : QB_F32;
+    // chunks need every earlier column at the same power iteration as the chunk's own: with one
+    // iteration the earlier chunks' G and Omega panels are exactly that; with more, the whole batch
+    const bool whole = (o.flags & QB_FLAG_WHOLE_BATCH) != 0 || p.P > 1;
     int64_t k = 0;
     int64_t q = 0;
     bool stop = false;
     while (k < p.cap && !stop) {
         const int64_t w = std::min<int64_t>(p.lt, p.cap - k);
         const int64_t col0 = q * p.lt;
-        out.omega_cols = col0 + w;
-        omega_gen(c.st, n, col0, w, o.seed, omega_dt, bf.Om, n);                 // Omega = randn(n, l~)
-        A.round_operand(c, bf.Om, n, n, w);
-        for (int it = 0; it < p.P; ++it) {                                       // power scheme
-            A.apply(c, bf.Om, n, w, bf.G, m);                                     // G = A Omega
-            out.passes += 1;
-            if (k > 0) {
-                c.tn(k, w, n, 1.0, B, ldb, bf.Om, n, 0.0, bf.T1, k, c.acc_proj);
-                c.nn(m, w, k, -1.0, Q, ldq, bf.T1, k, 1.0, bf.G, m, c.acc_proj);
-            }
-            // G only has to be a well-conditioned basis for the next application of A^T: one
-            // Gram-Schmidt pass per panel on the mixed path
-            c.orth_wide(bf.G, m, m, w, p.b, bf.Tw, false);                        // G = orth(.)
-            A.round_operand(c, bf.G, m, m, w);
-            A.apply_t(c, bf.G, m, w, bf.Om, n, 1);                                // Omega = A^T G
-            out.passes += 1;
-            if (k > 0) {
-                c.tn(k, w, m, 1.0, Q, ldq, bf.G, m, 0.0, bf.T1, k, c.acc_proj);
-                c.nn(n, w, k, -1.0, B, ldb, bf.T1, k, 1.0, bf.Om, n, c.acc_proj);
-            }
-            c.orth_wide(bf.Om, n, n, w, p.b, bf.Tw);                              // Omega = orth(.)
-            // The B_i formula cancels the components of H_i = A^T G_i along singular vectors
-            // already in Q; a bf16-rounded Omega (2^-9) would leak sigma_1^2-sized terms into
-            // every H_i, so the processed Omega keeps two bf16 terms (16 bits).
-            A.round_operand(c, bf.Om, n, n, w, 2);
-        }
-        A.apply(c, bf.Om, n, w, bf.G, m, p.P > 0 ? 2 : 1);                        // G = A Omega
-        out.passes += 1;
-        // H = A^T G for the stored G, in the precision the B_i formula needs, formed in chunks of
-        // H_CHUNK columns as the loop reaches them (the loop usually stops well before l~)
-        int64_t h_done = 0;
-        for (int64_t c0 = 0; c0 < w && !stop; c0 += p.b) {
-            const int bi = int(std::min<int64_t>(p.b, w - c0));
-            if (c0 + bi > h_done) {
-                const int64_t hw = std::min<int64_t>(std::max<int64_t>(H_CHUNK, bi), w - h_done);
-                A.apply_t(c, c.col(bf.G, m, h_done), m, hw, c.col(bf.H, n, h_done), n, 3);
-                if (h_done > 0) out.passes += 1;
-                h_done += hw;
-            }
-            const char* Om_i = c.col(bf.Om, n, c0);
-            // Y_i = G_i - Q (B Omega_i), kept for the B_i formula
-            c.copy_cols_(c.col(bf.G, m, c0), m, m, bi, bf.Ys, m);
-            if (k > 0) {
-                Ctx::Scope sc(c, PH_PROJ);
-                c.b_x(k, bi, B, ldb, n, Om_i, n, 0.0, bf.T1, k, c.acc_proj);
-                c.q_t(k, bi, Q, ldq, m, -1.0, bf.T1, k, bf.Ys, m, c.acc_proj);
-            }
-            // [Q_i, R_i] = qr(Y_i) in the slot of Q_i; the inverses of the factors go to Rchain
-            char* Qi = c.col(Q, ldq, k);
-            c.copy_cols_(bf.Ys, m, m, bi, Qi, ldq);
-            c.nchain = 0;
-            c.cholqr2(Qi, ldq, m, bi, true);
-            if (k > 0) {
-                // [Q_i, R~_i] = qr(Q_i - Q (Q^T Q_i)), R_i = R~_i R_i
-                c.reorth_q(k, Q, ldq, m, Qi, ldq, bi, bf.C2);
-                c.cholqr2(Qi, ldq, m, bi, true);
-            }
-            char* Bs = c.col(B, ldb, k);
-            {
-                Ctx::Scope scb(c, PH_BFORM);
-                // S^T = H_i - B^T (Q^T Y_i + B Omega_i), i.e. S = H_i^T - Y_i^T Q B - Omega_i^T B^T B
-                char* S = bf.Z;
-                c.copy_cols_(c.col(bf.H, n, c0), n, n, bi, S, n);
-                if (k > 0) {
-                    c.copy_cols_(bf.T1, k, k, bi, bf.C2, k);                          // C2 = B Omega_i
-                    c.qt_x(k, bi, Q, ldq, m, bf.Ys, m, 1.0, bf.C2, k, c.acc_fine);    // += Q^T Y_i
-                    c.bt_t(k, bi, B, ldb, n, -1.0, bf.C2, k, S, n, c.acc_fine);       // S^T -= B^T C2
+        const int64_t kb = k;   // Q, B at the start of the batch: the implicit residual A - Q B
+        // The batch's l~ columns are processed in chunks of FP_CHUNK columns, each carried
+        // through the power scheme, G = A Omega and H = A^T G before the blocked loop reaches
+        // it.  orth is column-causal (panel Gram-Schmidt / CholeskyQR), so every column comes out
+        // as in Algorithm 4 on the whole batch; the chunks after the stopping block are never
+        // formed.  QB_FLAG_WHOLE_BATCH forms the whole batch at once (2 + 2P passes over A).
+        const int64_t chunk = whole ? w : std::min<int64_t>(FP_CHUNK, w);
+        for (int64_t cc = 0; cc < w && !stop; cc += chunk) {
+            const int64_t cw = std::min<int64_t>(chunk, w - cc);
+            char* Om_c = c.col(bf.Om, n, cc);
+            char* G_c = c.col(bf.G, m, cc);
+            char* Gp_c = p.P > 0 ? c.col(bf.Gp, m, cc) : nullptr;
+            out.omega_cols = col0 + cc + cw;
+            omega_gen(c.st, n, col0 + cc, cw, o.seed, omega_dt, Om_c, n);   // Omega = randn(n, l~)
+            A.round_operand(c, Om_c, n, n, cw);
+            for (int it = 0; it < p.P; ++it) {                                // power scheme
+                A.apply(c, Om_c, n, cw, Gp_c, m);                             // G = A Omega
+                out.passes += 1;
+                if (kb > 0) {
+                    c.tn(kb, cw, n, 1.0, B, ldb, Om_c, n, 0.0, bf.T1, kb, c.acc_proj);
+                    c.nn(m, cw, kb, -1.0, Q, ldq, bf.T1, kb, 1.0, Gp_c, m, c.acc_proj);
                 }
-                // B_i = R_i^-T S  <=>  B_i^T = S^T R_i^-1, R_i = R~_2 R~_1 R_2 R_1 (the four
-                // CholeskyQR factors): apply R_1^-1, R_2^-1, R~_1^-1, R~_2^-1 in turn
-                for (int f = 0; f < c.nchain; ++f)
-                    apply_rinv(c.st, c.f64, S, n, n, bi, c.Rchain + size_t(f) * MAXB * MAXB);
-                c.copy_cols_(S, n, n, bi, Bs, ldb);
+                // G only has to be a well-conditioned basis for the next application of A^T:
+                // one Gram-Schmidt pass per panel on the mixed path
+                c.orth_wide(bf.Gp, m, m, cc + cw, p.b, bf.Tw, false, cc);      // G = orth(.)
+                A.round_operand(c, Gp_c, m, m, cw);
+                A.apply_t(c, Gp_c, m, cw, Om_c, n, 1);                        // Omega = A^T G
+                out.passes += 1;
+                if (kb > 0) {
+                    c.tn(kb, cw, m, 1.0, Q, ldq, Gp_c, m, 0.0, bf.T1, kb, c.acc_proj);
+                    c.nn(n, cw, kb, -1.0, B, ldb, bf.T1, kb, 1.0, Om_c, n, c.acc_proj);
+                }
+                c.orth_wide(bf.Om, n, n, cc + cw, p.b, bf.Tw, true, cc);       // Omega = orth(.)
+                // The B_i formula cancels the components of H_i = A^T G_i along singular vectors
+                // already in Q; a bf16-rounded Omega (2^-9) would leak sigma_1^2-sized terms into
+                // every H_i, so the processed Omega keeps two bf16 terms (16 bits).
+                A.round_operand(c, Om_c, n, n, cw, 2);
             }
-            c.shadow(k, bi, Qi, ldq, m, Bs, ldb, n);
-            const Ctx::Step s = c.indicator_step(Bs, ldb, bi, n, eps2, o.row_by_row);
-            out.blocks += 1;
-            out.E = s.E;
-            k += s.keep;
-            if (s.stop) { stop = true; out.converged = true; }
+            A.apply(c, Om_c, n, cw, G_c, m, p.P > 0 ? 2 : 1);                 // G = A Omega
+            out.passes += 1;
+            // H = A^T G for the stored G, in the precision the B_i formula needs, formed in
+            // pieces of at most H_CHUNK columns as the loop reaches them
+            int64_t h_done = cc;
+            for (int64_t c0 = cc; c0 < cc + cw && !stop; c0 += p.b) {
+                const int bi = int(std::min<int64_t>(p.b, cc + cw - c0));
+                if (c0 + bi > h_done) {
+                    const int64_t hw =
+                        std::min<int64_t>(std::max<int64_t>(H_CHUNK, bi), cc + cw - h_done);
+                    A.apply_t(c, c.col(bf.G, m, h_done), m, hw, c.col(bf.H, n, h_done), n, 3);
+                    if (h_done > cc) out.passes += 1;   // the first H rides on G's pass (Remark 4.2)
+                    h_done += hw;
+                }
+                const char* Om_i = c.col(bf.Om, n, c0);
+                // Y_i = G_i - Q (B Omega_i), kept for the B_i formula
+                c.copy_cols_(c.col(bf.G, m, c0), m, m, bi, bf.Ys, m);
+                if (k > 0) {
+                    Ctx::Scope sc(c, PH_PROJ);
+                    c.b_x(k, bi, B, ldb, n, Om_i, n, 0.0, bf.T1, k, c.acc_proj);
+                    c.q_t(k, bi, Q, ldq, m, -1.0, bf.T1, k, bf.Ys, m, c.acc_proj);
+                }
+                // [Q_i, R_i] = qr(Y_i) in the slot of Q_i; the inverses of the factors go to Rchain
+                char* Qi = c.col(Q, ldq, k);
+                c.copy_cols_(bf.Ys, m, m, bi, Qi, ldq);
+                c.nchain = 0;
+                c.cholqr2(Qi, ldq, m, bi, true);
+                if (k > 0) {
+                    // [Q_i, R~_i] = qr(Q_i - Q (Q^T Q_i)), R_i = R~_i R_i
+                    c.reorth_q(k, Q, ldq, m, Qi, ldq, bi, bf.C2);
+                    c.cholqr2(Qi, ldq, m, bi, true);
+                }
+                char* Bs = c.col(B, ldb, k);
+                {
+                    Ctx::Scope scb(c, PH_BFORM);
+                    // S^T = H_i - B^T (Q^T Y_i + B Omega_i), i.e. S = H_i^T - Y_i^T Q B - Omega_i^T B^T B
+                    char* S = bf.Z;
+                    c.copy_cols_(c.col(bf.H, n, c0), n, n, bi, S, n);
+                    if (k > 0) {
+                        c.copy_cols_(bf.T1, k, k, bi, bf.C2, k);                      // C2 = B Omega_i
+                        c.qt_x(k, bi, Q, ldq, m, bf.Ys, m, 1.0, bf.C2, k, c.acc_fine); // += Q^T Y_i
+                        c.bt_t(k, bi, B, ldb, n, -1.0, bf.C2, k, S, n, c.acc_fine);    // S^T -= B^T C2
+                    }
+                    // B_i = R_i^-T S  <=>  B_i^T = S^T R_i^-1, R_i = R~_2 R~_1 R_2 R_1 (the four
+                    // CholeskyQR factors): apply R_1^-1, R_2^-1, R~_1^-1, R~_2^-1 in turn
+                    for (int f = 0; f < c.nchain; ++f)
+                        apply_rinv(c.st, c.f64, S, n, n, bi, c.Rchain + size_t(f) * MAXB * MAXB);
+                    c.copy_cols_(S, n, n, bi, Bs, ldb);
+                }
+                c.shadow(k, bi, Qi, ldq, m, Bs, ldb, n);
+                const Ctx::Step s = c.indicator_step(Bs, ldb, bi, n, eps2, o.row_by_row);
+                out.blocks += 1;
+                out.E = s.E;
+                k += s.keep;
+                if (s.stop) { stop = true; out.converged = true; }
+            }
         }
         ++q;
     }

@@ -148,6 +148,42 @@ def test_indicator_matches_direct_residual():
         assert oracle.orth_loss(Qh) <= 1e-12
 
 
+# ----------------------------------------------------------------------------- FP chunks vs whole batch
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_fp_chunked_matches_whole_batch(prec):
+    """The default randQB_FP forms the Omega batch in 512-column chunks as the loop reaches them;
+    orth is column-causal, so Q, B must equal the whole-batch evaluation (QB_FLAG_WHOLE_BATCH,
+    Algorithm 4 as written) up to rounding, and (float64) the oracle's."""
+    m, n, b = 2000, 1500, 32
+    sigma = synth.sigma_exp(1500, 150.0, 1e-6)
+    A = synth.dense_from_spectrum(m, n, sigma, seed=404)
+    tol = 1e-2
+    Ad = torch.tensor(A, device="cuda")
+    kw = dict(P=1, seed=21)
+    if prec == "mixed":
+        hi, lo, norms = qb.quantize_bf16x2(Ad)
+        args = (hi, tol, b)
+        kw.update(prec="mixed", a_lo=lo, src_norm2=norms[0])
+    else:
+        args = (Ad, tol, b)
+    Qc, Bc, ic = qb.qb_fp_dense(*args, **kw)
+    Qw, Bw, iw = qb.qb_fp_dense(*args, flags=4, **kw)     # QB_FLAG_WHOLE_BATCH
+    assert ic.rank > 512            # the loop crossed at least one chunk boundary
+    assert ic.converged and iw.converged
+    assert ic.omega_cols < iw.omega_cols == min(50 * b, n)
+    nA = np.linalg.norm(A)
+    if prec == "fp64":
+        assert ic.rank == iw.rank
+        diff = np.linalg.norm(_qb(Qc, Bc) - _qb(Qw, Bw)) / nA
+        assert diff <= fp_parity_bound(sigma, ic.rank), diff
+        ref = oracle.randqb_fp(A, tol, b, seed=21, P=1)
+        assert ic.rank == ref.rank
+    else:
+        assert abs(ic.rank - iw.rank) <= 2
+        for Q, B in ((Qc, Bc), (Qw, Bw)):
+            assert np.linalg.norm(A - _qb(Q, B)) / nA < tol
+
+
 # ----------------------------------------------------------------------------- mixed precision
 @pytest.fixture(scope="module")
 def A_mixed():
