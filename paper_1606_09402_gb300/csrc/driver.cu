@@ -365,7 +365,8 @@ struct AOp {
     virtual void apply(Ctx& c, const void* X, int64_t ldx, int64_t w, void* Y, int64_t ldy,
                        int pairs = 1) = 0;
     // Y (n x w) = A^T X (X: m x w).  mode 1: sketch precision; mode 2: full A with an operand
-    // already rounded by round_operand(); mode 3: full A and full-precision operand (B_i = Q_i^T A)
+    // already rounded by round_operand(); mode 3: full A and full-precision operand (B_i = Q_i^T A);
+    // mode 4: full A with an operand rounded to two bf16 terms (round_operand(.., 2))
     virtual void apply_t(Ctx& c, const void* X, int64_t ldx, int64_t w, void* Y, int64_t ldy,
                          int mode) = 0;
     // Round an operand of the coming passes to the precision the passes consume (bf16 on the
@@ -729,6 +730,9 @@ void run_fp(Ctx& c, AOp& A, const Plan& p, const qb_opts& o, Bufs& bf, void* Q, 
             }
             A.apply(c, Om_c, n, cw, G_c, m, p.P > 0 ? 2 : 1);                 // G = A Omega
             out.passes += 1;
+            // The B_i formula needs H = A^T G exactly for the G it uses, not G = A Omega exactly:
+            // keep G as two-term bf16 values (16 bits) so the precise pass takes four products
+            A.round_operand(c, G_c, m, m, cw, 2);
             // H = A^T G for the stored G, in the precision the B_i formula needs, formed in
             // pieces of at most H_CHUNK columns as the loop reaches them
             int64_t h_done = cc;
@@ -737,7 +741,7 @@ void run_fp(Ctx& c, AOp& A, const Plan& p, const qb_opts& o, Bufs& bf, void* Q, 
                 if (c0 + bi > h_done) {
                     const int64_t hw =
                         std::min<int64_t>(std::max<int64_t>(H_CHUNK, bi), cc + cw - h_done);
-                    A.apply_t(c, c.col(bf.G, m, h_done), m, hw, c.col(bf.H, n, h_done), n, 3);
+                    A.apply_t(c, c.col(bf.G, m, h_done), m, hw, c.col(bf.H, n, h_done), n, 4);
                     if (h_done > cc) out.passes += 1;   // the first H rides on G's pass (Remark 4.2)
                     h_done += hw;
                 }

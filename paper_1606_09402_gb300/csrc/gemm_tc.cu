@@ -1073,14 +1073,16 @@ void tc_trans(cudaStream_t st, const bf16* A_hi, const bf16* A_lo, int64_t lda, 
               int64_t n, const float* V, int64_t ldv, int64_t w, float* Z, int64_t ldz, int mode,
               void* scratch, size_t scratch_bytes) {
     if (n <= 0 || w <= 0) return;
-    if (mode < 1 || mode > 3) throw Error{QB_ERR_INVALID_ARG, "tc_trans mode"};
+    if (mode < 1 || mode > 4) throw Error{QB_ERR_INVALID_ARG, "tc_trans mode"};
     Scratch s = carve(scratch, scratch_bytes, m, w);
     const int64_t ldo = align_up(m, 8);
     if (mode == 3) {
         k_split3_bf16<<<unsigned(cdiv(m * w, 256)), 256, 0, st>>>(V, ldv, m, w, s.vhi, s.vmid,
                                                                   s.vlo, ldo);
     } else {
-        k_split_bf16<<<unsigned(cdiv(m * w, 256)), 256, 0, st>>>(V, ldv, m, w, s.vhi, nullptr, ldo);
+        // mode 4: V holds two-term bf16 values, V = hi + (V - hi) exactly
+        k_split_bf16<<<unsigned(cdiv(m * w, 256)), 256, 0, st>>>(V, ldv, m, w, s.vhi,
+                                                                 mode == 4 ? s.vmid : nullptr, ldo);
     }
     QB_LAUNCHED();
     const int bn = mode == 1 ? pick_bn(w, pick_chunk(1, w) != SINGLE_CHAIN) : (w <= 64 ? 64 : 128);
@@ -1114,6 +1116,11 @@ void tc_trans(cudaStream_t st, const bf16* A_hi, const bf16* A_lo, int64_t lda, 
         return;
     }
     const CUtensorMap b1 = make_map(s.vmid, m, w, ldo, BK, bn);
+    if (mode == 4) {
+        if (A_lo) run_prec_bn<true, 2, 2>(bn, st, a0, a1, a1, b0, b1, b1, p, G);
+        else run_prec_bn<true, 1, 2>(bn, st, a0, a0, a0, b0, b1, b1, p, G);
+        return;
+    }
     const CUtensorMap b2 = make_map(s.vlo, m, w, ldo, BK, bn);
     if (A_lo) run_prec_bn<true, 2, 3>(bn, st, a0, a1, a1, b0, b1, b2, p, G);
     else run_prec_bn<true, 1, 3>(bn, st, a0, a0, a0, b0, b1, b2, p, G);

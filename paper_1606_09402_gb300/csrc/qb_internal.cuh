@@ -109,8 +109,9 @@ void trans_precise(cudaStream_t st, const bf16* Ahi, const bf16* Alo, int64_t ld
 //   trans : Z (n x w, col-major, float) = A^T V with V float column-major m x w:
 //           mode 1: A_hi^T bf16(V), float32 tensor-core accumulation (sketch precision);
 //           mode 2: (A_hi [+ A_lo])^T bf16(V) (exact operand for bf16-valued V);
-//           mode 3: (A_hi [+ A_lo])^T V with V = V_hi + V_mid + V_lo split exactly on the fly.
-//           Modes 2 and 3 sum the leading product per MMA in registers (round-to-nearest).
+//           mode 3: (A_hi [+ A_lo])^T V with V = V_hi + V_mid + V_lo split exactly on the fly;
+//           mode 4: (A_hi [+ A_lo])^T V for V holding two-term bf16 values (V = hi + lo exactly).
+//           Modes 2-4 sum the leading product per MMA in registers (round-to-nearest).
 bool tc_available();
 // scratch layout starts with a 256-byte error area: word 0 is set when a bounded wait timed out
 size_t tc_scratch_bytes(int64_t m, int64_t n, int64_t w);
