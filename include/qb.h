@@ -185,7 +185,9 @@ int32_t qb_fp_csr(const qb_csr* A, const qb_opts* opts, void* Q, int64_t ldq, vo
  *                    (H = A^T G of Algorithm 4, B_i^T = A^T Q_i of Algorithm 2).  For a bf16x2 A:
  *                    precise = 0: A_hi^T bf16(V) (sketch precision);
  *                    precise = 1: (A_hi + A_lo)^T V, V split exactly into three bf16 terms;
- *                    precise = 2: (A_hi + A_lo)^T bf16(V).
+ *                    precise = 2: (A_hi + A_lo)^T bf16(V);
+ *                    precise = 3: (A_hi + A_lo)^T (V_hi + V_lo), V_hi = bf16(V),
+ *                                 V_lo = bf16(V - V_hi) (exact for V with 16 significant bits).
  *                    With precise != 0 the leading product A_hi^T V_hi is summed per MMA in
  *                    float32 registers with round-to-nearest (the precision the indicator
  *                    needs; a single tensor-core accumulation chain would bias it toward zero).

@@ -64,6 +64,7 @@ struct Ctx {
     double* Racc = nullptr;
     double* Rchain = nullptr; // 4 x (64 x 64): inverses of the CholeskyQR factors of one block
     int nchain = 0;
+    bool chain_fused = false;   // the last Rchain slot holds a product formed by coop_precise
     double* rn = nullptr;   // 64 row norms
     double* state = nullptr;  // E, keep, stop, E_prev
     double* part = nullptr;   // 3 x 1024 reduction partials
@@ -168,18 +169,24 @@ struct Ctx {
     bool coop(void* P, int64_t ld, int64_t rows, int bi, int passes, bf16* out_hi = nullptr,
               bf16* out_lo = nullptr, int64_t ldo = 0) {
         return cholqr_coop(st, reinterpret_cast<float*>(P), ld, rows, bi, passes, false, 1e-10,
-                           nullptr, coop_scr, coop_bytes, reinterpret_cast<unsigned*>(flags + 4),
-                           flags, flags + 2, out_hi, out_lo, ldo);
+                           nullptr, nullptr, coop_scr, coop_bytes,
+                           reinterpret_cast<unsigned*>(flags + 4), flags, flags + 2, out_hi,
+                           out_lo, ldo);
     }
-    // Fused CholeskyQR2 of a Q_i panel on the mixed path (adaptive factor); with acc_r the two
-    // inverses go to the next Rchain slots.
+    // Fused CholeskyQR2 of a Q_i panel on the mixed path (adaptive factor).  With acc_r the
+    // product of the inverses joins the Rchain: multiplied into the last slot when that slot came
+    // from this path too (the slots are applied in order, so a product of consecutive ones is the
+    // same), else into a new slot.
     bool coop_precise(void* P, int64_t ld, int64_t rows, int bi, bool acc_r) {
-        if (f64 || (acc_r && nchain > 2)) return false;
-        double* ro = acc_r ? Rchain + size_t(nchain) * MAXB * MAXB : nullptr;
-        if (!cholqr_coop(st, reinterpret_cast<float*>(P), ld, rows, bi, 2, true, tau, ro, coop_scr,
-                         coop_bytes, reinterpret_cast<unsigned*>(flags + 4), flags, flags + 2))
+        if (f64 || (acc_r && nchain >= 4)) return false;
+        const bool merge = acc_r && nchain > 0 && chain_fused;
+        double* slot = acc_r ? Rchain + size_t(merge ? nchain - 1 : nchain) * MAXB * MAXB : nullptr;
+        if (!cholqr_coop(st, reinterpret_cast<float*>(P), ld, rows, bi, 2, true, tau,
+                         merge ? slot : nullptr, slot, coop_scr, coop_bytes,
+                         reinterpret_cast<unsigned*>(flags + 4), flags, flags + 2))
             return false;
-        if (acc_r) nchain += 2;
+        if (acc_r && !merge) ++nchain;
+        if (acc_r) chain_fused = true;
         return true;
     }
     void cholqr(void* P, int64_t ld, int64_t rows, int bi, bool acc_r, bool sketch = false) {
@@ -187,7 +194,10 @@ struct Ctx {
         if (fast && !acc_r && coop(P, ld, rows, bi, 1)) return;
         gram(st, P, ld, rows, bi, f64, f64 ? ACC_D : (fast ? ACC_F : acc_gram), W, scr);
         double* ri = Rinv;
-        if (acc_r && nchain < 4) ri = Rchain + size_t(nchain++) * MAXB * MAXB;
+        if (acc_r && nchain < 4) {
+            ri = Rchain + size_t(nchain++) * MAXB * MAXB;
+            chain_fused = false;
+        }
         chol_rinv(st, W, bi, fast ? 1e-10 : tau, nullptr, ri, nullptr, flags,
                   f64 ? CHOL_F64 : (fast ? CHOL_F32 : CHOL_ADAPTIVE));
         apply_rinv(st, f64, P, ld, rows, bi, ri);
@@ -757,6 +767,7 @@ void run_fp(Ctx& c, AOp& A, const Plan& p, const qb_opts& o, Bufs& bf, void* Q, 
                 char* Qi = c.col(Q, ldq, k);
                 c.copy_cols_(bf.Ys, m, m, bi, Qi, ldq);
                 c.nchain = 0;
+                c.chain_fused = false;
                 c.cholqr2(Qi, ldq, m, bi, true);
                 if (k > 0) {
                     // [Q_i, R~_i] = qr(Q_i - Q (Q^T Q_i)), R_i = R~_i R_i
@@ -1139,7 +1150,9 @@ static int32_t apass(const qb_dense* A, bool trans, const void* V, int64_t ldv, 
         DenseOp op(*A);
         op.reserve(ar, c, std::max<int64_t>(w, 1));
         op.prepare(c);
-        if (trans) op.apply_t(c, V, ldv, w, Y, ldy, precise == 0 ? 1 : (precise == 2 ? 2 : 3));
+        if (trans)
+            op.apply_t(c, V, ldv, w, Y, ldy,
+                       precise == 0 ? 1 : (precise == 2 ? 2 : (precise == 3 ? 4 : 3)));
         else op.apply(c, V, ldv, w, Y, ldy, 1);
         if (op.timed_out(c)) return int32_t(QB_ERR_TIMEOUT);
         return int32_t(QB_OK);

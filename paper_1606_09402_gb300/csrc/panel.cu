@@ -321,20 +321,21 @@ k_chol(const double* __restrict__ W, int bi, double tau_rel, double* __restrict_
 // enough); otherwise the Gram is formed again with exact products and float32-pair sums and
 // factored in float64, as the unfused path does.
 constexpr int COOP_THREADS = 512;
-constexpr int COOP_ROWS = 480;      // rows per CTA held in shared memory
+constexpr int COOP_ROWS = 440;      // rows per CTA held in shared memory
 constexpr int COOP_MAX_CTAS = 256;
 constexpr int PLD = MAXB + 1;       // shared row stride of the panel slice
 constexpr uint64_t COOP_WAIT_NS = 2000000000ull;
 // dynamic shared memory: panel slice, then S (float64 size), Sf, Li, Rs
 constexpr size_t COOP_SMEM = sizeof(float) * COOP_ROWS * PLD + sizeof(double) * MAXB * CLD +
-                             3 * sizeof(float) * MAXB * CLD;
+                             4 * sizeof(float) * MAXB * CLD;
 
 struct CoopArgs {
     float* P;
     int64_t ldp, rows, rows_per;
     int bi, passes;
     double tau;
-    double* rinv_out;   // passes x (MAXB x MAXB) or null
+    const double* rinv_prev;  // MAXB x MAXB or null (identity)
+    double* rinv_out;   // rinv_prev R_1^-1 ... R_passes^-1 (MAXB x MAXB) or null
     double* part;       // gridDim.x x (MAXB x MAXB) partial Grams
     double* wred;       // MAXB x MAXB summed Gram
     unsigned* bar;      // [0] arrivals, [1] generation
@@ -410,7 +411,16 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) k_cholqr_coop(CoopArgs p) {
     float (*Sf)[CLD] = reinterpret_cast<float (*)[CLD]>(rest + sizeof(double) * MAXB * CLD);
     float (*Li)[CLD] = reinterpret_cast<float (*)[CLD]>(rest + (sizeof(double) + sizeof(float)) * MAXB * CLD);
     float (*Rs)[CLD] = reinterpret_cast<float (*)[CLD]>(rest + (sizeof(double) + 2 * sizeof(float)) * MAXB * CLD);
+    float (*Pc)[CLD] = reinterpret_cast<float (*)[CLD]>(rest + (sizeof(double) + 3 * sizeof(float)) * MAXB * CLD);
     double* scratch = reinterpret_cast<double*>(rest);   // Gram combine space (S and Sf regions)
+    // CTA 0 keeps the running product rinv_prev R_1^-1 R_2^-1 ... of the passes
+    const bool chain = blockIdx.x == 0 && p.rinv_out != nullptr;
+    if (chain) {
+        for (int e = threadIdx.x; e < MAXB * MAXB; e += COOP_THREADS) {
+            const int i = e % MAXB, j = e / MAXB;
+            Pc[i][j] = p.rinv_prev ? float(p.rinv_prev[e]) : (i == j ? 1.f : 0.f);
+        }
+    }
     __shared__ float fpiv[MAXB], finvd[MAXB], fidiag[MAXB], fdiag0[MAXB], fdmax;
     __shared__ double dpiv[MAXB], dinvd[MAXB], didiag[MAXB], ddiag0[MAXB], ddmax;
     __shared__ int weak_s;
@@ -544,13 +554,9 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) k_cholqr_coop(CoopArgs p) {
                                      l, lr, lc);
         }
         // R^-1[c][a] = L^-1[a][c] / sqrt(d_a); strictly lower tiles are zero
-        double* ro = (cta == 0 && p.rinv_out) ? p.rinv_out + int64_t(pass) * MAXB * MAXB : nullptr;
         for (int e = tid; e < MAXB * MAXB; e += COOP_THREADS) {
             const int i = e % MAXB, jj = e / MAXB;
-            if ((i >> 2) > (jj >> 2)) {
-                Rs[i][jj] = 0.f;
-                if (ro) ro[e] = 0.0;
-            }
+            if ((i >> 2) > (jj >> 2)) Rs[i][jj] = 0.f;
         }
         if (tid >= CHOL_L0 && tid < CHOL_L0 + CHOL_TILES) {
 #pragma unroll
@@ -559,12 +565,25 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) k_cholqr_coop(CoopArgs p) {
                 for (int q = 0; q < 4; ++q) {
                     const int a = 4 * lr + r, c = 4 * lc + q;
                     const float id = dbl ? float(didiag[a < MAXB ? a : 0]) : fidiag[a < MAXB ? a : 0];
-                    const float v = (a < bi && c < bi) ? l[r][q] * id : 0.f;
-                    Rs[c][a] = v;
-                    if (ro) ro[c + a * MAXB] = v;
+                    Rs[c][a] = (a < bi && c < bi) ? l[r][q] * id : 0.f;
                 }
         }
         __syncthreads();
+        if (chain) {
+            // Pc <- Pc R^-1 (thread: row i, 8 consecutive columns)
+            const int i = tid & 63, c0 = (tid >> 6) * 8;
+            float acc[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) acc[q] = 0.f;
+            for (int l2 = 0; l2 < MAXB; ++l2) {
+                const float v = Pc[i][l2];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) acc[q] = fmaf(v, Rs[l2][c0 + q], acc[q]);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < 8; ++q) Pc[i][c0 + q] = acc[q];
+        }
         // ---- rows <- rows * R^-1, 128 rows at a time (thread: one row, 16 columns)
         {
             const int i = tid & 127, c0 = (tid >> 7) * 16;
@@ -590,6 +609,10 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) k_cholqr_coop(CoopArgs p) {
         }
     }
     __syncthreads();
+    if (chain) {
+        for (int e = tid; e < MAXB * MAXB; e += COOP_THREADS)
+            p.rinv_out[e] = double(Pc[e % MAXB][e / MAXB]);
+    }
     for (int e = tid; e < nr * MAXB; e += COOP_THREADS) {
         const int r = e % nr, col = e / nr;
         if (col >= bi) continue;
@@ -781,8 +804,9 @@ size_t cholqr_coop_scratch_bytes() {
 }
 
 bool cholqr_coop(cudaStream_t st, float* P, int64_t ldp, int64_t rows, int bi, int passes,
-                 bool precise, double tau, double* rinv_out, void* scratch, size_t scratch_bytes,
-                 unsigned* bar, int* flags, int* err, bf16* out_hi, bf16* out_lo, int64_t ldo) {
+                 bool precise, double tau, const double* rinv_prev, double* rinv_out,
+                 void* scratch, size_t scratch_bytes, unsigned* bar, int* flags, int* err,
+                 bf16* out_hi, bf16* out_lo, int64_t ldo) {
     static int max_ctas[2] = {-1, -1};
     const int v = precise ? 1 : 0;
     auto kern = precise ? k_cholqr_coop<true> : k_cholqr_coop<false>;
@@ -810,6 +834,7 @@ bool cholqr_coop(cudaStream_t st, float* P, int64_t ldp, int64_t rows, int bi, i
     a.bi = bi;
     a.passes = passes;
     a.tau = tau;
+    a.rinv_prev = rinv_prev;
     a.rinv_out = rinv_out;
     a.part = reinterpret_cast<double*>(scratch);
     a.wred = a.part + size_t(COOP_MAX_CTAS) * MAXB * MAXB;

@@ -193,15 +193,16 @@ enum CholPrec { CHOL_F64 = 0, CHOL_F64_INV_F32 = 1, CHOL_F32 = 2, CHOL_ADAPTIVE 
 // `passes` CholeskyQR passes on a float32 rows x bi panel in one cooperative launch; precise =
 // false: float32 Gram and factor (power scheme); precise = true: two-level Gram and float32 factor,
 // exact-product Gram and float64 factor for a panel with weak pivots.  rinv_out (nullable)
-// receives each pass's R^-1 (MAXB x MAXB, float64).
+// receives rinv_prev R_1^-1 ... R_passes^-1 (MAXB x MAXB, float64; rinv_prev null = identity; the
+// two may be the same buffer).
 // bar: two zero-initialised words kept across calls; err is set if a grid barrier timed out.
 // out_hi (nullable): also write bf16(P) there (ld ldo), and bf16(P - bf16(P)) to out_lo when given.
 // Returns false (nothing launched) when the panel does not fit the launch.
 size_t cholqr_coop_scratch_bytes();
 bool cholqr_coop(cudaStream_t st, float* P, int64_t ldp, int64_t rows, int bi, int passes,
-                 bool precise, double tau, double* rinv_out, void* scratch, size_t scratch_bytes,
-                 unsigned* bar, int* flags, int* err, bf16* out_hi = nullptr,
-                 bf16* out_lo = nullptr, int64_t ldo = 0);
+                 bool precise, double tau, const double* rinv_prev, double* rinv_out,
+                 void* scratch, size_t scratch_bytes, unsigned* bar, int* flags, int* err,
+                 bf16* out_hi = nullptr, bf16* out_lo = nullptr, int64_t ldo = 0);
 void chol_rinv(cudaStream_t st, const double* W, int bi, double tau_rel, double* R,
                double* Rinv, double* R_acc, int* flags, CholPrec prec);
 void set_identity(cudaStream_t st, double* R, int bi);
