@@ -478,7 +478,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
 // The lower-order products (A_lo V_hi, A_hi V_mid: 2^-9 of the leading one; A_hi V_lo,
 // A_lo V_mid: 2^-18) accumulate in tensor memory over PREC_CHUNK k-blocks, where their bias is
 // scaled down by those factors.  A_lo V_lo (2^-27) is dropped.
-constexpr int PREC_CHUNK = 8;
+constexpr int PREC_CHUNK = 16;
 constexpr int PREC_EPI = 8;                          // epilogue warps
 constexpr int PREC_THREADS = 64 + 32 * PREC_EPI;     // TMA warp, MMA warp, epilogue warps
 
@@ -500,7 +500,10 @@ struct PCfg {
     static constexpr int STAGES = (200 * 1024) / STAGE < 8 ? (200 * 1024) / STAGE : 8;
     static constexpr int SMEM = STAGES * STAGE + 1024 + 512;
     static constexpr int NSMALL = prec_nsmall(NA, NB);
-    static constexpr int SMALL_COLS = NSMALL > 0 ? 2 * BN : 0;   // double-buffered chain
+    // chain buffers: two at BN = 64; one at BN = 128, which leaves three ring slots (the chain is
+    // drained once per PREC_CHUNK k-blocks, the ring once per MMA)
+    static constexpr int NCHAIN = NSMALL > 0 ? (BN >= 128 ? 1 : 2) : 0;
+    static constexpr int SMALL_COLS = NCHAIN * BN;
     static constexpr int NSLOT = (512 - SMALL_COLS) / BN < 8 ? (512 - SMALL_COLS) / BN : 8;
     static constexpr int TMEM_COLS = 512;
 };
@@ -683,7 +686,7 @@ k_tc_prec(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
                 if (C::NSMALL > 0) {
                     tc_commit(sfull + sbuf);
                     sph ^= 1u << sbuf;
-                    sbuf ^= 1;
+                    if (++sbuf == C::NCHAIN) sbuf = 0;
                 }
             }
         }
@@ -748,7 +751,7 @@ k_tc_prec(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
                     tc_fence_before();
                     mbar_arrive(sempty + sbuf);
                     sph ^= 1u << sbuf;
-                    sbuf ^= 1;
+                    if (++sbuf == C::NCHAIN) sbuf = 0;
                 }
             }
             if (!ok) break;
