@@ -479,6 +479,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
 // A_lo V_mid: 2^-18) accumulate in tensor memory over PREC_CHUNK k-blocks, where their bias is
 // scaled down by those factors.  A_lo V_lo (2^-27) is dropped.
 constexpr int PREC_CHUNK = 16;
+constexpr int PREC_LEAD = 2;   // leading-product MMAs (K = 16 each) per tensor-memory slot
 constexpr int PREC_EPI = 8;                          // epilogue warps
 constexpr int PREC_THREADS = 64 + 32 * PREC_EPI;     // TMA warp, MMA warp, epilogue warps
 
@@ -658,14 +659,19 @@ k_tc_prec(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
 #pragma unroll
                         for (int j = 0; j < NB; ++j)
                             db[j] = sdesc(sbb + j * C::B_TILE + kk * (UMMA_K * 2), 16, 1024);
-                        // leading product into a fresh slot
-                        ok = mbar_wait(bempty + slot, ((slot_ph >> slot) & 1u) ^ 1u, p.err);
-                        if (!ok) break;
-                        tc_fence_after();
-                        tc_mma(tm_big + uint32_t(slot * BN), da[0], db[0], idesc, 0u);
-                        tc_commit(bfull + slot);
-                        slot_ph ^= 1u << slot;
-                        if (++slot == C::NSLOT) slot = 0;
+                        // leading product: PREC_LEAD MMAs into a fresh slot
+                        if (kk % PREC_LEAD == 0) {
+                            ok = mbar_wait(bempty + slot, ((slot_ph >> slot) & 1u) ^ 1u, p.err);
+                            if (!ok) break;
+                            tc_fence_after();
+                        }
+                        tc_mma(tm_big + uint32_t(slot * BN), da[0], db[0], idesc,
+                               kk % PREC_LEAD == 0 ? 0u : 1u);
+                        if (kk % PREC_LEAD == PREC_LEAD - 1) {
+                            tc_commit(bfull + slot);
+                            slot_ph ^= 1u << slot;
+                            if (++slot == C::NSLOT) slot = 0;
+                        }
                         // lower-order products, smallest weight first
                         uint32_t acc = (kb > c0 || kk > 0) ? 1u : 0u;
 #pragma unroll
@@ -719,16 +725,24 @@ k_tc_prec(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
             for (int k0 = sg.k0; k0 < sg.k1 && ok; k0 += PREC_CHUNK) {
                 const int k1 = min(sg.k1, k0 + PREC_CHUNK);
                 for (int kb = k0; kb < k1 && ok; ++kb) {
-                    for (int kk = 0; kk < BK / UMMA_K && ok; ++kk) {
+                    for (int kk = 0; kk < BK / UMMA_K / PREC_LEAD && ok; ++kk) {
                         ok = mbar_wait(bfull + slot, (slot_ph >> slot) & 1u, p.err);
                         if (!ok) break;
                         tc_fence_after();
+                        if constexpr (HC == 64) {
+                            float v[64];
+                            tmem_ld64(tm_big + lane_off + uint32_t(slot * BN) + col_off, v);
 #pragma unroll
-                        for (int cc = 0; cc < HC; cc += 32) {
-                            float v[32];
-                            tmem_ld32(tm_big + lane_off + uint32_t(slot * BN) + col_off + uint32_t(cc), v);
+                            for (int j = 0; j < 64; ++j) accr[j] += v[j];
+                        } else {
 #pragma unroll
-                            for (int j = 0; j < 32; ++j) accr[cc + j] += v[j];
+                            for (int cc = 0; cc < HC; cc += 32) {
+                                float v[32];
+                                tmem_ld32(tm_big + lane_off + uint32_t(slot * BN) + col_off +
+                                              uint32_t(cc), v);
+#pragma unroll
+                                for (int j = 0; j < 32; ++j) accr[cc + j] += v[j];
+                            }
                         }
                         tc_fence_before();
                         mbar_arrive(bempty + slot);
