@@ -34,6 +34,12 @@ RANK_SPECTRUM = 4096
 TOL, B, P, SEED_A, SEED_OMEGA = 1e-3, 64, 1, 1606, 9402
 L_TILDE = 50 * B
 RANK_CAP = 4096
+# DRAM bytes of one k_tc_prec<128, true, 2, 2> launch (w = 512): ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum) on the 16384 x 8192 case, 604.1 MB + 13.2 MB, scaled by the size of A
+# (x 5.96) to 40000 x 20000; the algorithmic bytes there are 3.28 GB (A hi + lo and G's two terms).
+PREC_TRAFFIC_BYTES = 3.68e9
+PREC_TRAFFIC_NOTE = ("ncu dram bytes of k_tc_prec<128,1,2,2> on 16384x8192 (617.3 MB), scaled by "
+                     "the size of A to 40000x20000; algorithmic 3.28 GB")
 
 
 def parse():
@@ -46,6 +52,9 @@ def parse():
     ap.add_argument("--quick", action="store_true", help="smaller workload (smoke only)")
     ap.add_argument("--steps-only", action="store_true",
                     help="time the mixed randQB_FP steps only (no side measurements); for profiling")
+    ap.add_argument("--profile-small", action="store_true",
+                    help="two mixed randQB_FP factorisations of a 16384 x 8192 matrix (the small "
+                         "case for ncu section captures); prints the rank")
     return ap.parse_args()
 
 
@@ -370,9 +379,10 @@ def run_ours(args, ws, rank, local):
     t_sk_wide = event_time(torch, lambda: qb.qb_apass_sketch(hi, Om), reps, stream)
     t_tr_wide = event_time(torch, lambda: qb.qb_apass_trans(hi, G, precise=1, a_lo=lo), reps,
                            stream)
-    # the precise transposed pass of the step: one H_CHUNK = 512-column chunk of H = A^T G
+    # the precise transposed pass of the step: one 512-column chunk of H = A^T G, G held as
+    # two-term bf16 values (precise=3, four tensor-core products per output)
     Gc = torch.randn(m, 512, device=dev, dtype=torch.float32)
-    t_tr_chunk = event_time(torch, lambda: qb.qb_apass_trans(hi, Gc, precise=1, a_lo=lo), reps,
+    t_tr_chunk = event_time(torch, lambda: qb.qb_apass_trans(hi, Gc, precise=3, a_lo=lo), reps,
                             stream)
     t_wrap_c = event_time(torch, lambda: (Gc.T.contiguous(), torch.empty(512, n, device=dev)),
                           reps, stream)
@@ -465,11 +475,12 @@ def run_ours(args, ws, rank, local):
                    "svd_rank": 1382 if not args.quick else None},
         "roofline": {"bound": "tensor",
                      "kernel": "k_tc_prec: precise H = (A_hi + A_lo)^T G chunk (w = 512), "
-                               "5 bf16 tensor-core products per output",
+                               "4 bf16 tensor-core products per output",
                      "achieved": tf_prec, "peak": sustained, "unit": "TFLOP/s",
-                     "frac": tf_prec / sustained, "traffic": None,
-                     "algorithmic": "2 m n w flops per launch (the product, not the 5 issued)",
-                     "issued_frac": 5 * tf_prec / sustained, "ms_per_launch": t_prec * 1e3,
+                     "frac": tf_prec / sustained, "traffic": PREC_TRAFFIC_BYTES if not args.quick else None,
+                     "traffic_note": PREC_TRAFFIC_NOTE,
+                     "algorithmic": "2 m n w flops per launch (the product, not the 4 issued)",
+                     "issued_frac": 4 * tf_prec / sustained, "ms_per_launch": t_prec * 1e3,
                      "peak_source": f"{pk_src} bf16_tflops_sustained"},
         "roofline_sketch": {"bound": "tensor", "kernel": "k_tc_gemm: sketch G = A_hi Omega "
                                                          "(w = l~ = 3200)",
@@ -495,8 +506,29 @@ def run_ours(args, ws, rank, local):
     _ = np
 
 
+def run_profile_small():
+    """The small case of the mixed randQB_FP step for ncu captures: A 16384 x 8192 (sigma_j =
+    exp(-j/100) + 1e-6, j <= 2048), b = 64, P = 1, tol 1e-3; A hi+lo = 537 MB, larger than L2."""
+    import torch
+
+    import paper_1606_09402_gb300 as qb
+    import synth
+    A = synth.dense_from_spectrum_torch(16384, 8192, synth.sigma_exp(2048, 100.0, 1e-6), 3, "cuda")
+    hi, lo, norms = qb.quantize_bf16x2(A)
+    del A
+    torch.cuda.synchronize()
+    for _ in range(2):
+        _, _, info = qb.qb_fp_dense(hi, TOL, B, P=P, seed=1, prec="mixed", a_lo=lo,
+                                    src_norm2=norms[0], rank_cap=1600)
+        torch.cuda.synchronize()
+        print("rank", info.rank, "status", info.status, flush=True)
+
+
 def main():
     args = parse()
+    if args.profile_small:
+        run_profile_small()
+        return
     ws, rank, local = dist_env()
     if ws > 1:
         import torch
