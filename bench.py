@@ -240,6 +240,36 @@ def run_batched(torch, qb, dev, stream):
             "note": "one graph launch per call; includes graph build/instantiate"}
 
 
+def run_sparse(torch, qb, dev, stream):
+    """The sparse workload: CSR 200000 x 100000, Poisson(100) row lengths, Zipf(1.1) columns,
+    log-normal float32 values (seed 909), b = 32, P = 1, relative tol 0.5, rank cap 1024;
+    randQB_EI and randQB_FP time-to-tolerance, and the A-pass bandwidth of EI from its phase
+    times (the CSR passes run in the sketch and transposed phases)."""
+    import numpy as np
+
+    import synth
+    csr = synth.csr_zipf(200000, 100000, 100.0, 1.1, seed=909, val_dtype=np.float32)
+    rp = torch.tensor(csr.rowptr, device=dev)
+    ci = torch.tensor(csr.colind, device=dev)
+    v = torch.tensor(csr.val, device=dev)
+    shape = (csr.m, csr.n)
+    kw = dict(P=1, seed=9402, rank_cap=1024)
+    out = {"m": csr.m, "n": csr.n, "nnz": int(ci.numel()), "b": 32, "P": 1, "tol": 0.5}
+    for name, f in (("ei", qb.qb_ei_csr), ("fp", qb.qb_fp_csr)):
+        f(rp, ci, v, shape, 0.5, 32, **kw)                   # warm-up
+        torch.cuda.synchronize()
+        t = event_time(torch, lambda: f(rp, ci, v, shape, 0.5, 32, **kw), 3, stream)
+        _, _, info = f(rp, ci, v, shape, 0.5, 32, flags=2, **kw)
+        ph = qb.profile_last()
+        out[name] = {"time_to_tol_s": t, "rank": info.rank, "passes": info.passes,
+                     "status": info.status, "pass_ms": ph["sketch"] + ph["trans"]}
+    a_bytes = 8.0 * out["nnz"] + 4.0 * (csr.m + 1)
+    ei = out["ei"]
+    out["a_bytes_per_pass"] = a_bytes
+    out["ei_pass_gbs"] = ei["passes"] * a_bytes / (ei["pass_ms"] * 1e-3) / 1e9
+    return out
+
+
 def run_adjoint(torch, qb, dev, stream):
     """Fixed-rank k = 256 QB of an 8192 x 8192 bf16 A (sigma_j = 1/j): forward and backward."""
     import numpy as np
@@ -432,6 +462,8 @@ def run_ours(args, ws, rank, local):
     batched = None if args.quick else run_batched(torch, qb, dev, stream)
     # ---- fixed-rank adjoint: 8192 x 8192 bf16, k = 256, sigma_j = 1/j
     adjoint = None if args.quick else run_adjoint(torch, qb, dev, stream)
+    # ---- sparse: CSR 200000 x 100000, nnz ~ 2e7
+    sparse = None if args.quick else run_sparse(torch, qb, dev, stream)
 
     # ---- end to end through the public API with host buffers (pinned)
     hi_h = hi.cpu().pin_memory()
@@ -496,6 +528,7 @@ def run_ours(args, ws, rank, local):
         "mixed_randqb_ei": ei,
         "batched_ei_256": batched,
         "fixed_rank_adjoint_8192": adjoint,
+        "sparse_csr_200000x100000": sparse,
         "e2e": {"value": t_e2e, "unit": "s", "h2d_bytes_per_step": int(2 * hi.numel() * 2),
                 "d2h_bytes_per_step": int(d2h["b"])},
         "gpu_launches": gpu_launches,

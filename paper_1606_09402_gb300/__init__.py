@@ -173,7 +173,7 @@ def qb_fp_dense(A, tol, b, P=0, seed=0, relative=True, rank_cap=None, l_tilde=No
 
 
 def _csr_call(fn, name, rowptr, colind, val, shape, tol, b, P, seed, relative, rank_cap, l_tilde,
-              row_by_row, stream, workspace):
+              row_by_row, stream, workspace, flags=0):
     torch = _torch()
     lib = _lib.load()
     _check_dev(rowptr, colind, val)
@@ -183,7 +183,7 @@ def _csr_call(fn, name, rowptr, colind, val, shape, tol, b, P, seed, relative, r
     s = _lib.qb_csr(m=m, n=n, nnz=colind.numel(), rowptr=rowptr.data_ptr(),
                     colind=colind.data_ptr(), dtype=_dtype_code(val), reserved=0,
                     val=val.data_ptr())
-    o = _opts(tol, b, P, seed, relative, rank_cap, l_tilde, row_by_row, prec)
+    o = _opts(tol, b, P, seed, relative, rank_cap, l_tilde, row_by_row, prec, flags)
     algo = 1 if name.startswith("qb_fp") else 0
     wsb = lib.qb_csr_workspace(C.byref(s), C.byref(o), algo)
     if wsb == 0:
@@ -205,17 +205,17 @@ def _csr_call(fn, name, rowptr, colind, val, shape, tol, b, P, seed, relative, r
 
 
 def qb_ei_csr(rowptr, colind, val, shape, tol, b, P=0, seed=0, relative=True, rank_cap=None,
-              row_by_row=True, stream=None, workspace=None):
+              row_by_row=True, stream=None, workspace=None, flags=0):
     """randQB_EI on a CSR matrix (int32 indices; float64 values -> fp64 path, float32 -> mixed)."""
     return _csr_call(_lib.load().qb_ei_csr, "qb_ei_csr", rowptr, colind, val, shape, tol, b, P,
-                     seed, relative, rank_cap, None, row_by_row, stream, workspace)
+                     seed, relative, rank_cap, None, row_by_row, stream, workspace, flags)
 
 
 def qb_fp_csr(rowptr, colind, val, shape, tol, b, P=0, seed=0, relative=True, rank_cap=None,
-              l_tilde=None, row_by_row=True, stream=None, workspace=None):
+              l_tilde=None, row_by_row=True, stream=None, workspace=None, flags=0):
     """randQB_FP on a CSR matrix."""
     return _csr_call(_lib.load().qb_fp_csr, "qb_fp_csr", rowptr, colind, val, shape, tol, b, P,
-                     seed, relative, rank_cap, l_tilde, row_by_row, stream, workspace)
+                     seed, relative, rank_cap, l_tilde, row_by_row, stream, workspace, flags)
 
 
 def qb_omega(n, col0, w, seed, dtype=None, device="cuda", stream=None):
