@@ -144,25 +144,32 @@ def csr_zipf(m: int, n: int, mean_len: float, zipf_s: float, seed: int,
     cdf = np.cumsum(ranks ** (-zipf_s))
     cdf /= cdf[-1]
     perm = rng.permutation(n).astype(np.int64)
-    rows = np.repeat(np.arange(m, dtype=np.int64), lens)
-    need = lens.copy()
-    keys = np.empty(0, dtype=np.int64)
-    # draw, dedupe per row, redraw what is missing
-    pending_rows = rows
+    keys = np.empty(0, dtype=np.int64)        # sorted, unique keys row * n + rank
+    have = np.zeros(m, dtype=np.int64)
+    # draw, dedupe per row, redraw what is missing; only the new draws are sorted and merged into
+    # the kept keys, which gives the same key set as re-sorting everything each round
+    pending_rows = np.repeat(np.arange(m, dtype=np.int64), lens)
     for _ in range(64):
         if pending_rows.size == 0:
             break
         u = rng.random(pending_rows.size)
         c = np.minimum(np.searchsorted(cdf, u, side="right"), n - 1)
-        keys = np.unique(np.concatenate([keys, pending_rows * n + c]))
-        have = np.bincount(keys // n, minlength=m)
+        new = np.sort(pending_rows * n + c)
+        if new.size:
+            new = new[np.concatenate(([True], new[1:] != new[:-1]))]
+        pos = np.searchsorted(keys, new)
+        if keys.size:
+            present = keys[np.minimum(pos, keys.size - 1)] == new
+            new = new[~present]
+            pos = pos[~present]
+        keys = np.insert(keys, pos, new)
+        have += np.bincount(new // n, minlength=m)
         missing = lens - have
         pending_rows = np.repeat(np.arange(m, dtype=np.int64), np.maximum(missing, 0))
-    r_of = keys // n
-    cols = perm[keys % n]
-    order = np.lexsort((cols, r_of))
-    r_of = r_of[order]
-    cols = cols[order]
+    # sort by (row, column id): the pairs are distinct, so one sort of row * n + column does it
+    rc = np.sort((keys // n) * n + perm[keys % n])
+    r_of = rc // n
+    cols = rc % n
     counts = np.bincount(r_of, minlength=m)
     rowptr = np.zeros(m + 1, dtype=np.int64)
     np.cumsum(counts, out=rowptr[1:])
