@@ -52,9 +52,9 @@ def parse():
     ap.add_argument("--quick", action="store_true", help="smaller workload (smoke only)")
     ap.add_argument("--steps-only", action="store_true",
                     help="time the mixed randQB_FP steps only (no side measurements); for profiling")
-    ap.add_argument("--profile-small", action="store_true",
-                    help="two mixed randQB_FP factorisations of a 16384 x 8192 matrix (the small "
-                         "case for ncu section captures); prints the rank")
+    ap.add_argument("--profile-small", nargs="?", const="fp", default=None, choices=["fp", "ei"],
+                    help="two mixed randQB_FP (or randQB_EI) factorisations of a 16384 x 8192 "
+                         "matrix (the small case for ncu section captures); prints the rank")
     return ap.parse_args()
 
 
@@ -539,9 +539,10 @@ def run_ours(args, ws, rank, local):
     _ = np
 
 
-def run_profile_small():
-    """The small case of the mixed randQB_FP step for ncu captures: A 16384 x 8192 (sigma_j =
-    exp(-j/100) + 1e-6, j <= 2048), b = 64, P = 1, tol 1e-3; A hi+lo = 537 MB, larger than L2."""
+def run_profile_small(alg):
+    """The small case of the mixed randQB_FP (alg "fp") or randQB_EI (alg "ei": its passes are the
+    narrow w = b ones) step for ncu captures: A 16384 x 8192 (sigma_j = exp(-j/100) + 1e-6,
+    j <= 2048), b = 64, P = 1, tol 1e-3; A hi+lo = 537 MB, larger than L2."""
     import torch
 
     import paper_1606_09402_gb300 as qb
@@ -550,9 +551,10 @@ def run_profile_small():
     hi, lo, norms = qb.quantize_bf16x2(A)
     del A
     torch.cuda.synchronize()
+    f = qb.qb_fp_dense if alg == "fp" else qb.qb_ei_dense
     for _ in range(2):
-        _, _, info = qb.qb_fp_dense(hi, TOL, B, P=P, seed=1, prec="mixed", a_lo=lo,
-                                    src_norm2=norms[0], rank_cap=1600)
+        _, _, info = f(hi, TOL, B, P=P, seed=1, prec="mixed", a_lo=lo, src_norm2=norms[0],
+                       rank_cap=1600)
         torch.cuda.synchronize()
         print("rank", info.rank, "status", info.status, flush=True)
 
@@ -560,7 +562,7 @@ def run_profile_small():
 def main():
     args = parse()
     if args.profile_small:
-        run_profile_small()
+        run_profile_small(args.profile_small)
         return
     ws, rank, local = dist_env()
     if ws > 1:

@@ -3,8 +3,13 @@
 // The dense operands are column-major in the QB loop; a warp-per-row gather wants the w values of
 // one row of X contiguous, so X is transposed into a row-major staging buffer, 128 columns at a
 // time (the 128-column slice of X for n = 1e5 is 51 MB and stays in L2), and the row-major result
-// is transposed back.  A^T X runs the same kernel on a CSC copy of A built once per call, so no
-// atomics touch the Zipf-hot columns.
+// is transposed back.  A^T X runs the same kernels on a CSC copy of A built once per call.
+//
+// Rows longer than CSR_SEG nonzeros (the Zipf-hot columns of A, in the CSC copy: the hottest of
+// 1e5 columns holds about an eighth of all nonzeros) would serialise a whole pass behind one warp,
+// so a per-call table cuts them into CSR_SEG-nonzero segments, one warp each, whose partial rows
+// are added with atomics into the row that the warp-per-row kernel zeroed.  Rows up to CSR_SEG
+// nonzeros keep a fixed summation order.
 #include "qb_internal.cuh"
 
 namespace qb {
@@ -57,46 +62,156 @@ __global__ void k_scatter(const int32_t* __restrict__ rowptr, const int32_t* __r
     }
 }
 
-// Y_rm (rows x wc, ld ldy) = A * X_rm (cols x wc, ld ldx), one warp per row, up to 128 columns.
-template <class T>
-__global__ void __launch_bounds__(256)
-k_spmm_rm(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx, const T* __restrict__ val,
-          int64_t rows, const T* __restrict__ X, int64_t ldx, int wc, T* __restrict__ Y, int64_t ldy) {
-    const int64_t r = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (r >= rows) return;
-    T acc[WCH / 32];
-#pragma unroll
-    for (int q = 0; q < WCH / 32; ++q) acc[q] = T(0);
-    const int32_t b = ptr[r], e = ptr[r + 1];
+template <class T, int NQ> struct Vec;
+template <> struct Vec<float, 1> {
+    static __device__ __forceinline__ void ld(const float* p, float* o) { o[0] = __ldg(p); }
+    static __device__ __forceinline__ void st(float* p, const float* v) { p[0] = v[0]; }
+};
+template <> struct Vec<float, 2> {
+    static __device__ __forceinline__ void ld(const float* p, float* o) {
+        const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+        o[0] = v.x; o[1] = v.y;
+    }
+    static __device__ __forceinline__ void st(float* p, const float* v) {
+        *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+    }
+};
+template <> struct Vec<float, 4> {
+    static __device__ __forceinline__ void ld(const float* p, float* o) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+        o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    }
+    static __device__ __forceinline__ void st(float* p, const float* v) {
+        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+};
+template <> struct Vec<double, 1> {
+    static __device__ __forceinline__ void ld(const double* p, double* o) { o[0] = __ldg(p); }
+    static __device__ __forceinline__ void st(double* p, const double* v) { p[0] = v[0]; }
+};
+template <> struct Vec<double, 2> {
+    static __device__ __forceinline__ void ld(const double* p, double* o) {
+        const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+        o[0] = v.x; o[1] = v.y;
+    }
+    static __device__ __forceinline__ void st(double* p, const double* v) {
+        *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+    }
+};
+template <> struct Vec<double, 4> {
+    static __device__ __forceinline__ void ld(const double* p, double* o) {
+        Vec<double, 2>::ld(p, o);
+        Vec<double, 2>::ld(p + 2, o + 2);
+    }
+    static __device__ __forceinline__ void st(double* p, const double* v) {
+        Vec<double, 2>::st(p, v);
+        Vec<double, 2>::st(p + 2, v + 2);
+    }
+};
+
+// acc += sum over p in [b, e) of val[p] * X[idx[p], lane*NQ .. lane*NQ+NQ).  The 32 (index, value)
+// pairs of a chunk are loaded once by the warp and broadcast; full chunks are unrolled so that
+// eight row gathers are in flight per warp.
+template <class T, int NQ>
+__device__ __forceinline__ void row_acc(const int32_t* __restrict__ idx, const T* __restrict__ val,
+                                        int32_t b, int32_t e, const T* __restrict__ X, int64_t ldx,
+                                        int lane, T (&acc)[NQ]) {
+    const T* xl = X + lane * NQ;
     for (int32_t p0 = b; p0 < e; p0 += 32) {
         const int32_t p = p0 + lane;
         int32_t c = 0;
         T v = T(0);
         if (p < e) { c = idx[p]; v = val[p]; }
         const int cnt = min(32, e - p0);
-        for (int t = 0; t < cnt; ++t) {
+        auto step = [&](int t) {
             const int32_t cc = __shfl_sync(0xffffffffu, c, t);
             const T vv = __shfl_sync(0xffffffffu, v, t);
-            const T* xr = X + int64_t(cc) * ldx;
+            T x[NQ];
+            Vec<T, NQ>::ld(xl + int64_t(cc) * ldx, x);
 #pragma unroll
-            for (int q = 0; q < WCH / 32; ++q) {
-                const int j = lane + 32 * q;
-                if (j < wc) acc[q] = fma(vv, xr[j], acc[q]);
-            }
+            for (int q = 0; q < NQ; ++q) acc[q] = fma(vv, x[q], acc[q]);
+        };
+        if (cnt == 32) {
+#pragma unroll 8
+            for (int t = 0; t < 32; ++t) step(t);
+        } else {
+            for (int t = 0; t < cnt; ++t) step(t);
         }
-    }
-#pragma unroll
-    for (int q = 0; q < WCH / 32; ++q) {
-        const int j = lane + 32 * q;
-        if (j < wc) Y[r * ldy + j] = acc[q];
     }
 }
 
-// col-major (rows x cols, ld) slice [c0, c0+wc) -> row-major (rows x wc)
+// Y_rm (rows x 32 NQ, ld ldy) = A * X_rm (cols x 32 NQ, ld ldx), one warp per row; lane l owns
+// columns [l NQ, l NQ + NQ).  Rows longer than long_len are written as zeros here: their segments
+// are added by k_spmm_seg, which runs after this kernel on the same stream.
+template <class T, int NQ>
+__global__ void __launch_bounds__(256)
+k_spmm_rm(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx, const T* __restrict__ val,
+          int64_t rows, const T* __restrict__ X, int64_t ldx, T* __restrict__ Y, int64_t ldy,
+          int32_t long_len) {
+    const int64_t r = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (r >= rows) return;
+    T acc[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc[q] = T(0);
+    const int32_t b = ptr[r], e = ptr[r + 1];
+    if (e - b <= long_len) row_acc<T, NQ>(idx, val, b, e, X, ldx, lane, acc);
+    Vec<T, NQ>::st(Y + r * ldy + lane * NQ, acc);
+}
+
+// One warp per segment of a long row: the CSR_SEG-nonzero piece [beg, beg + CSR_SEG) of row
+// seg_row[s], added into Y with atomics (grid-stride over the *count segments).
+template <class T, int NQ>
+__global__ void __launch_bounds__(256)
+k_spmm_seg(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx, const T* __restrict__ val,
+           const int32_t* __restrict__ seg_row, const int32_t* __restrict__ seg_beg,
+           const int32_t* __restrict__ count, const T* __restrict__ X, int64_t ldx, int wc,
+           T* __restrict__ Y, int64_t ldy) {
+    const int lane = threadIdx.x & 31;
+    const int64_t S = *count;
+    const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t s = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; s < S; s += nw) {
+        const int32_t r = seg_row[s];
+        const int32_t b = seg_beg[s];
+        const int32_t e = min(b + CSR_SEG, ptr[r + 1]);
+        T acc[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) acc[q] = T(0);
+        row_acc<T, NQ>(idx, val, b, e, X, ldx, lane, acc);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int j = lane * NQ + q;
+            if (j < wc) atomicAdd(Y + int64_t(r) * ldy + j, acc[q]);
+        }
+    }
+}
+
+__global__ void k_seg_count(const int32_t* __restrict__ ptr, int64_t rows, int32_t* __restrict__ cnt) {
+    for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < rows;
+         r += int64_t(gridDim.x) * blockDim.x) {
+        const int32_t len = ptr[r + 1] - ptr[r];
+        cnt[r] = len > CSR_SEG ? (len + CSR_SEG - 1) / CSR_SEG : 0;
+    }
+}
+
+__global__ void k_seg_fill(const int32_t* __restrict__ ptr, int64_t rows, const int32_t* __restrict__ off,
+                           int32_t* __restrict__ seg_row, int32_t* __restrict__ seg_beg) {
+    for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < rows;
+         r += int64_t(gridDim.x) * blockDim.x) {
+        const int32_t b = ptr[r], len = ptr[r + 1] - b;
+        if (len <= CSR_SEG) continue;
+        const int32_t o = off[r];
+        for (int32_t k = 0; k * CSR_SEG < len; ++k) {
+            seg_row[o + k] = int32_t(r);
+            seg_beg[o + k] = b + k * CSR_SEG;
+        }
+    }
+}
+
+// col-major (rows x cols, ld) slice [c0, c0+wc) -> row-major (rows x wc, ld wp)
 template <class T>
 __global__ void k_cm_to_rm(const T* __restrict__ X, int64_t ldx, int64_t rows, int64_t c0, int wc,
-                           T* __restrict__ Xr) {
+                           T* __restrict__ Xr, int wp) {
     __shared__ T tile[32][33];
     const int64_t r0 = int64_t(blockIdx.x) * 32;
     const int j0 = blockIdx.y * 32;
@@ -109,12 +224,12 @@ __global__ void k_cm_to_rm(const T* __restrict__ X, int64_t ldx, int64_t rows, i
     for (int k = threadIdx.y; k < 32; k += blockDim.y) {
         const int64_t r = r0 + k;
         const int j = j0 + threadIdx.x;
-        if (r < rows && j < wc) Xr[r * wc + j] = tile[threadIdx.x][k];
+        if (r < rows && j < wc) Xr[r * wp + j] = tile[threadIdx.x][k];
     }
 }
 
 template <class T>
-__global__ void k_rm_to_cm(const T* __restrict__ Yr, int64_t rows, int wc, T* __restrict__ Y,
+__global__ void k_rm_to_cm(const T* __restrict__ Yr, int wp, int64_t rows, int wc, T* __restrict__ Y,
                            int64_t ldy, int64_t c0) {
     __shared__ T tile[32][33];
     const int64_t r0 = int64_t(blockIdx.x) * 32;
@@ -122,7 +237,7 @@ __global__ void k_rm_to_cm(const T* __restrict__ Yr, int64_t rows, int wc, T* __
     for (int k = threadIdx.y; k < 32; k += blockDim.y) {
         const int64_t r = r0 + k;
         const int j = j0 + threadIdx.x;
-        if (r < rows && j < wc) tile[k][threadIdx.x] = Yr[r * wc + j];
+        if (r < rows && j < wc) tile[k][threadIdx.x] = Yr[r * wp + j];
     }
     __syncthreads();
     for (int k = threadIdx.y; k < 32; k += blockDim.y) {
@@ -132,22 +247,43 @@ __global__ void k_rm_to_cm(const T* __restrict__ Yr, int64_t rows, int wc, T* __
     }
 }
 
+template <class T, int NQ>
+void spmm_slice(cudaStream_t st, const int32_t* ptr, const int32_t* idx, const T* val, int64_t rows,
+                const CsrSegs* segs, const T* Xr, int wc, T* Yr) {
+    constexpr int wp = 32 * NQ;
+    k_spmm_rm<T, NQ><<<unsigned(cdiv(rows * 32, 256)), 256, 0, st>>>(
+        ptr, idx, val, rows, Xr, wp, Yr, wp, segs ? int32_t(CSR_SEG) : INT32_MAX);
+    QB_LAUNCHED();
+    if (segs && segs->cap > 0) {
+        const unsigned g = unsigned(std::min<int64_t>(cdiv(segs->cap, 8), 152 * 16));
+        k_spmm_seg<T, NQ><<<g, 256, 0, st>>>(ptr, idx, val, segs->row, segs->beg, segs->count, Xr,
+                                             wp, wc, Yr, wp);
+        QB_LAUNCHED();
+    }
+}
+
 template <class T>
 void spmm_t(cudaStream_t st, const int32_t* ptr, const int32_t* idx, const T* val, int64_t rows,
-            int64_t cols, const T* X, int64_t ldx, int64_t w, T* Y, int64_t ldy, T* stage) {
+            int64_t cols, const CsrSegs* segs, const T* X, int64_t ldx, int64_t w, T* Y,
+            int64_t ldy, T* stage) {
     T* Xr = stage;
     T* Yr = stage + cols * WCH;
     for (int64_t c0 = 0; c0 < w; c0 += WCH) {
         const int wc = int(std::min<int64_t>(WCH, w - c0));
+        const int nq = wc <= 32 ? 1 : wc <= 64 ? 2 : 4;
+        const int wp = 32 * nq;
         dim3 blk(32, 8);
         k_cm_to_rm<T><<<dim3(unsigned(cdiv(cols, 32)), unsigned(cdiv(wc, 32))), blk, 0, st>>>(
-            X, ldx, cols, c0, wc, Xr);
+            X, ldx, cols, c0, wc, Xr, wp);
         QB_LAUNCHED();
-        k_spmm_rm<T><<<unsigned(cdiv(rows * 32, 256)), 256, 0, st>>>(ptr, idx, val, rows, Xr, wc,
-                                                                     wc, Yr, wc);
-        QB_LAUNCHED();
+        if (nq == 1)
+            spmm_slice<T, 1>(st, ptr, idx, val, rows, segs, Xr, wc, Yr);
+        else if (nq == 2)
+            spmm_slice<T, 2>(st, ptr, idx, val, rows, segs, Xr, wc, Yr);
+        else
+            spmm_slice<T, 4>(st, ptr, idx, val, rows, segs, Xr, wc, Yr);
         k_rm_to_cm<T><<<dim3(unsigned(cdiv(rows, 32)), unsigned(cdiv(wc, 32))), blk, 0, st>>>(
-            Yr, rows, wc, Y, ldy, c0);
+            Yr, wp, rows, wc, Y, ldy, c0);
         QB_LAUNCHED();
     }
 }
@@ -183,16 +319,34 @@ void csr_to_csc(cudaStream_t st, const CsrDev& A, int32_t* colptr, int32_t* rowi
     }
 }
 
+int64_t csr_seg_cap(int64_t nnz) { return 2 * nnz / CSR_SEG + 1; }
+
+void csr_segments(cudaStream_t st, const int32_t* ptr, int64_t rows, int32_t* off, int32_t* tmp,
+                  CsrSegs& segs) {
+    segs.count = off + rows;
+    if (rows <= 0) {
+        QB_CUDA(cudaMemsetAsync(segs.count, 0, sizeof(int32_t), st));
+        return;
+    }
+    const unsigned g = unsigned(std::min<int64_t>(cdiv(rows, 256), 4096));
+    k_seg_count<<<g, 256, 0, st>>>(ptr, rows, tmp);
+    QB_LAUNCHED();
+    k_scan<<<1, 1024, 0, st>>>(tmp, rows, off, tmp + rows);
+    QB_LAUNCHED();
+    k_seg_fill<<<g, 256, 0, st>>>(ptr, rows, off, segs.row, segs.beg);
+    QB_LAUNCHED();
+}
+
 void csr_spmm(cudaStream_t st, bool f64, const int32_t* ptr, const int32_t* idx, const void* val,
-              int64_t rows, int64_t cols, const void* X, int64_t ldx, int64_t w, void* Y,
-              int64_t ldy, void* stage) {
+              int64_t rows, int64_t cols, const CsrSegs* segs, const void* X, int64_t ldx,
+              int64_t w, void* Y, int64_t ldy, void* stage) {
     if (rows <= 0 || w <= 0) return;
     if (f64)
-        spmm_t<double>(st, ptr, idx, reinterpret_cast<const double*>(val), rows, cols,
+        spmm_t<double>(st, ptr, idx, reinterpret_cast<const double*>(val), rows, cols, segs,
                        reinterpret_cast<const double*>(X), ldx, w, reinterpret_cast<double*>(Y),
                        ldy, reinterpret_cast<double*>(stage));
     else
-        spmm_t<float>(st, ptr, idx, reinterpret_cast<const float*>(val), rows, cols,
+        spmm_t<float>(st, ptr, idx, reinterpret_cast<const float*>(val), rows, cols, segs,
                       reinterpret_cast<const float*>(X), ldx, w, reinterpret_cast<float*>(Y), ldy,
                       reinterpret_cast<float*>(stage));
 }

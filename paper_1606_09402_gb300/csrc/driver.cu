@@ -507,26 +507,38 @@ struct CsrOp : AOp {
     void* cval = nullptr;
     int32_t* cnt = nullptr;
     void* stage = nullptr;
+    CsrSegs seg_r, seg_c;            // long rows of A, long columns of A (rows of the CSC copy)
+    int32_t* off_r = nullptr;
+    int32_t* off_c = nullptr;
     explicit CsrOp(const qb_csr& ss) : s(ss) { m = ss.m; n = ss.n; }
     bool f64v() const { return s.dtype == QB_F64; }
     void reserve(Arena& ar, const Ctx&, int64_t) override {
         colptr = ar.get<int32_t>(n + 1);
         rowind = ar.get<int32_t>(s.nnz);
         cval = ar.get<char>(s.nnz * (f64v() ? 8 : 4));
-        cnt = ar.get<int32_t>(2 * n);
+        cnt = ar.get<int32_t>(2 * std::max(m, n));
         stage = ar.get<char>(int64_t(csr_stage_bytes(m, n, f64v())));
+        for (CsrSegs* g : {&seg_r, &seg_c}) {
+            g->cap = csr_seg_cap(s.nnz);
+            g->row = ar.get<int32_t>(g->cap);
+            g->beg = ar.get<int32_t>(g->cap);
+        }
+        off_r = ar.get<int32_t>(m + 1);
+        off_c = ar.get<int32_t>(n + 1);
     }
     void prepare(Ctx& c) override {
         CsrDev A{m, n, s.nnz, s.rowptr, s.colind, s.val, f64v()};
         csr_to_csc(c.st, A, colptr, rowind, cval, cnt);
+        csr_segments(c.st, s.rowptr, m, off_r, cnt, seg_r);
+        csr_segments(c.st, colptr, n, off_c, cnt, seg_c);
     }
     void apply(Ctx& c, const void* X, int64_t ldx, int64_t w, void* Y, int64_t ldy, int) override {
         Ctx::Scope sc(c, PH_SKETCH);
-        csr_spmm(c.st, f64v(), s.rowptr, s.colind, s.val, m, n, X, ldx, w, Y, ldy, stage);
+        csr_spmm(c.st, f64v(), s.rowptr, s.colind, s.val, m, n, &seg_r, X, ldx, w, Y, ldy, stage);
     }
     void apply_t(Ctx& c, const void* X, int64_t ldx, int64_t w, void* Y, int64_t ldy, int) override {
         Ctx::Scope sc(c, PH_TRANS);
-        csr_spmm(c.st, f64v(), colptr, rowind, cval, n, m, X, ldx, w, Y, ldy, stage);
+        csr_spmm(c.st, f64v(), colptr, rowind, cval, n, m, &seg_c, X, ldx, w, Y, ldy, stage);
     }
     double norm2(Ctx& c) override {
         vec_norm2(c.st, s.val, f64v(), s.nnz, c.part, c.state + 4, c.flags);

@@ -232,10 +232,26 @@ size_t csr_stage_bytes(int64_t m, int64_t n, bool f64);
 // column come in no particular order (atomic scatter).
 void csr_to_csc(cudaStream_t st, const CsrDev& A, int32_t* colptr, int32_t* rowind, void* cval,
                 int32_t* cnt);
+// Rows of a compressed matrix longer than CSR_SEG nonzeros are cut into CSR_SEG-nonzero segments:
+// segment s covers [beg[s], min(beg[s] + CSR_SEG, ptr[row[s] + 1])) of row row[s]; *count
+// segments (device int), at most cap.
+constexpr int CSR_SEG = 256;
+struct CsrSegs {
+    int32_t* row = nullptr;
+    int32_t* beg = nullptr;
+    int32_t* count = nullptr;
+    int64_t cap = 0;
+};
+// upper bound on the segments of any matrix with nnz nonzeros
+int64_t csr_seg_cap(int64_t nnz);
+// fills segs.row / segs.beg (caller-owned, segs.cap entries each); off: rows + 1 int32 (count is
+// off[rows]); tmp: 2 rows int32 scratch
+void csr_segments(cudaStream_t st, const int32_t* ptr, int64_t rows, int32_t* off, int32_t* tmp,
+                  CsrSegs& segs);
 // Y (rows x w, col-major) = S X, S given by (ptr, idx, val) compressed along its rows,
-// X (cols x w, col-major)
+// X (cols x w, col-major); segs: the long-row table of S (nullptr: one warp per row throughout)
 void csr_spmm(cudaStream_t st, bool f64, const int32_t* ptr, const int32_t* idx, const void* val,
-              int64_t rows, int64_t cols, const void* X, int64_t ldx, int64_t w, void* Y,
-              int64_t ldy, void* stage);
+              int64_t rows, int64_t cols, const CsrSegs* segs, const void* X, int64_t ldx,
+              int64_t w, void* Y, int64_t ldy, void* stage);
 
 }  // namespace qb

@@ -71,3 +71,32 @@ def test_csr_mixed_float32(alg):
     ref = (oracle.randqb_ei if alg == "ei" else oracle.randqb_fp)(S, 0.5, 32, seed=3, P=1,
                                                                    rank_cap=512)
     assert abs(info.rank - ref.rank) <= 2
+
+
+@pytest.mark.parametrize("alg", ["ei", "fp"])
+def test_csr_long_rows_and_wide_slices(alg):
+    """Rows and columns many times longer than one long-row segment (a full row of 4000 nonzeros,
+    a half row, two full columns), and pass widths that fill 128-column staging slices and leave
+    ragged ones (EI: w = b = 48; FP: l~ = 300), in float64 against the oracle."""
+    import scipy.sparse as sp
+    rng = np.random.default_rng(21)
+    m, n = 700, 4000
+    dense = rng.standard_normal((m, n)) * (rng.random((m, n)) < 0.01)
+    dense[3, :] = rng.standard_normal(n)
+    dense[100, ::2] = 1.0 + rng.random(n // 2)
+    dense[:, 7] = rng.standard_normal(m)
+    dense[:, 11] = 2.0
+    S = sp.csr_matrix(dense)
+    rp = torch.tensor(S.indptr.astype(np.int32)).cuda()
+    ci = torch.tensor(S.indices.astype(np.int32)).cuda()
+    v = torch.tensor(S.data).cuda()
+    if alg == "ei":
+        Q, B, info = qb.qb_ei_csr(rp, ci, v, (m, n), 0.2, 48, P=1, seed=8, rank_cap=480)
+        ref = oracle.randqb_ei(S, 0.2, 48, seed=8, P=1, rank_cap=480)
+    else:
+        Q, B, info = qb.qb_fp_csr(rp, ci, v, (m, n), 0.2, 48, P=1, seed=8, rank_cap=480,
+                                  l_tilde=300)
+        ref = oracle.randqb_fp(S, 0.2, 48, seed=8, P=1, rank_cap=480, l_tilde=300)
+    assert info.rank == ref.rank and info.status == ref.status
+    diff = np.linalg.norm((Q @ B).cpu().numpy() - ref.Q @ ref.B) / np.linalg.norm(dense)
+    assert diff <= 1e-10
