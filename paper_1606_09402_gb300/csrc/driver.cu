@@ -510,9 +510,20 @@ struct CsrOp : AOp {
     CsrSegs seg_r, seg_c;            // long rows of A, long columns of A (rows of the CSC copy)
     int32_t* off_r = nullptr;
     int32_t* off_c = nullptr;
+    // The passes over A are SIMT gathers; on the float32 path the projections against Q and B
+    // still run on tensor cores (three-term bf16 shadows), which needs the tensor-core scratch.
+    bool use_tc = false;
+    void* tc_scr = nullptr;
+    size_t tc_bytes = 0;
     explicit CsrOp(const qb_csr& ss) : s(ss) { m = ss.m; n = ss.n; }
     bool f64v() const { return s.dtype == QB_F64; }
-    void reserve(Arena& ar, const Ctx&, int64_t) override {
+    void reserve(Arena& ar, const Ctx& c, int64_t w) override {
+        use_tc = !c.f64 && !c.simt_apass && m >= 128 && n >= 128 &&
+                 (ar.base == nullptr || tc_available());
+        if (use_tc) {
+            tc_bytes = tc_scratch_bytes(m, n, w);
+            tc_scr = ar.get<char>(int64_t(tc_bytes));
+        }
         colptr = ar.get<int32_t>(n + 1);
         rowind = ar.get<int32_t>(s.nnz);
         cval = ar.get<char>(s.nnz * (f64v() ? 8 : 4));
@@ -526,7 +537,21 @@ struct CsrOp : AOp {
         off_r = ar.get<int32_t>(m + 1);
         off_c = ar.get<int32_t>(n + 1);
     }
+    bool tc_scratch(void** p, size_t* b) override {
+        if (!use_tc) return false;
+        *p = tc_scr;
+        *b = tc_bytes;
+        return true;
+    }
+    bool timed_out(Ctx& c) override {
+        if (!use_tc) return false;
+        int h = 0;
+        QB_CUDA(cudaMemcpyAsync(&h, tc_error_flag(tc_scr), sizeof h, cudaMemcpyDeviceToHost, c.st));
+        QB_CUDA(cudaStreamSynchronize(c.st));
+        return h != 0;
+    }
     void prepare(Ctx& c) override {
+        if (use_tc) QB_CUDA(cudaMemsetAsync(tc_error_flag(tc_scr), 0, 256, c.st));
         CsrDev A{m, n, s.nnz, s.rowptr, s.colind, s.val, f64v()};
         csr_to_csc(c.st, A, colptr, rowind, cval, cnt);
         csr_segments(c.st, s.rowptr, m, off_r, cnt, seg_r);
