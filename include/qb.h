@@ -138,7 +138,8 @@ const char* qb_last_cuda_error(void);
 /* Total kernels launched by the library in this process (all calls). */
 int64_t qb_launch_count(void);
 
-/* Device milliseconds per phase of the last call made with QB_FLAG_PROFILE, in this order:
+/* Device milliseconds per phase of the last call made with QB_FLAG_PROFILE (or of the last
+ * qb_apass_sketch / qb_apass_trans call, which always records its pass), in this order:
  * 0 Omega generation, 1 sketch passes over A (A X), 2 transposed passes over A (A^T X),
  * 3 power-scheme orthonormalisation, 4 projections against Q and B, 5 CholeskyQR2 of the new
  * block (with its re-orthogonalisation), 6 randQB_FP's B_i formula, 7 indicator and host

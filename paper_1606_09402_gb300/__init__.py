@@ -59,7 +59,8 @@ def launch_count() -> int:
 
 
 def profile_last() -> dict:
-    """Per-phase device milliseconds of the last call made with flags=QB_FLAG_PROFILE (2)."""
+    """Per-phase device milliseconds of the last call made with flags=QB_FLAG_PROFILE (2), or of
+    the last qb_apass_sketch / qb_apass_trans call (phase "sketch" / "trans")."""
     buf = (C.c_double * len(_lib.PHASES))()
     _lib.load().qb_profile_last(buf, len(_lib.PHASES))
     return dict(zip(_lib.PHASES, (float(x) for x in buf)))

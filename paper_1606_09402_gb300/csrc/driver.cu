@@ -1187,12 +1187,14 @@ static int32_t apass(const qb_dense* A, bool trans, const void* V, int64_t ldv, 
         DenseOp op(*A);
         op.reserve(ar, c, std::max<int64_t>(w, 1));
         op.prepare(c);
+        c.prof = true;   // the pass's device time, read back with qb_profile_last
         if (trans)
             op.apply_t(c, V, ldv, w, Y, ldy,
                        precise == 0 ? 1 : (precise == 2 ? 2 : (precise == 3 ? 4 : 3)));
         else op.apply(c, V, ldv, w, Y, ldy, 1);
-        if (op.timed_out(c)) return int32_t(QB_ERR_TIMEOUT);
-        return int32_t(QB_OK);
+        const bool to = op.timed_out(c);
+        c.flush_profile();
+        return int32_t(to ? QB_ERR_TIMEOUT : QB_OK);
     });
 }
 

@@ -431,10 +431,36 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) k_cholqr_coop(CoopArgs p) {
     const int64_t r0 = int64_t(cta) * p.rows_per;
     const int64_t r_end = p.rows < r0 + p.rows_per ? p.rows : r0 + p.rows_per;
     const int nr = r_end > r0 ? int(r_end - r0) : 0;
-    for (int e = tid; e < nr * MAXB; e += COOP_THREADS) {
-        const int r = e % nr, col = e / nr;
-        Ps[r][col] = col < bi ? p.P[r0 + r + int64_t(col) * p.ldp] : 0.f;
-    }
+    // A slice taller than COOP_ROWS is streamed through shared memory in tiles of COOP_ROWS rows
+    // (each phase re-reads it from global memory); a slice of one tile stays resident throughout.
+    const int ntile = nr > 0 ? (nr + COOP_ROWS - 1) / COOP_ROWS : 1;
+    auto tile_rows = [&](int t) { return min(COOP_ROWS, nr - t * COOP_ROWS); };
+    auto load_tile = [&](int t) {
+        const int tn = tile_rows(t);
+        const int64_t rb = r0 + int64_t(t) * COOP_ROWS;
+        for (int e = tid; e < tn * MAXB; e += COOP_THREADS) {
+            const int r = e % tn, col = e / tn;
+            Ps[r][col] = col < bi ? p.P[rb + r + int64_t(col) * p.ldp] : 0.f;
+        }
+    };
+    // write the tile back; the final write also emits the optional bf16 shadow
+    auto store_tile = [&](int t, bool final) {
+        const int tn = tile_rows(t);
+        const int64_t rb = r0 + int64_t(t) * COOP_ROWS;
+        for (int e = tid; e < tn * MAXB; e += COOP_THREADS) {
+            const int r = e % tn, col = e / tn;
+            if (col >= bi) continue;
+            const float v = Ps[r][col];
+            p.P[rb + r + int64_t(col) * p.ldp] = v;
+            if (final && p.out_hi) {
+                const bf16 h = __float2bfloat16_rn(v);
+                p.out_hi[rb + r + int64_t(col) * p.ldo] = h;
+                if (p.out_lo)
+                    p.out_lo[rb + r + int64_t(col) * p.ldo] = __float2bfloat16_rn(v - __bfloat162float(h));
+            }
+        }
+    };
+    if (ntile == 1) load_tile(0);
     // Gram block of thread t < 3 * 136: the (t % 136)-th 4 x 4 block of the upper triangle over
     // rows t / 136, t / 136 + 3, ...
     const int blk = tid % 136, grp = tid / 136;
@@ -447,14 +473,21 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) k_cholqr_coop(CoopArgs p) {
     // partial Gram of the slice into p.part[cta]; mode 0 float32, 1 two-level, 2 exact products
     auto gram = [&](int mode) {
         __syncthreads();
-        if (grp < 3) {
-            float hi[4][4], lo[4][4], ch[4][4];
+        float hi[4][4], lo[4][4], ch[4][4];
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int b = 0; b < 4; ++b) hi[a][b] = lo[a][b] = ch[a][b] = 0.f;
-            int cnt = 0;
-            for (int r = grp; r < nr; r += 3) {
+            for (int b = 0; b < 4; ++b) hi[a][b] = lo[a][b] = ch[a][b] = 0.f;
+        int cnt = 0;
+        for (int t = 0; t < ntile; ++t) {
+            if (ntile > 1) {
+                __syncthreads();
+                load_tile(t);
+                __syncthreads();
+            }
+            const int tn = ntile > 1 ? tile_rows(t) : nr;
+            if (grp >= 3) continue;
+            for (int r = grp; r < tn; r += 3) {
                 float x[4], y[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
@@ -483,6 +516,10 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) k_cholqr_coop(CoopArgs p) {
                     }
                 }
             }
+        }
+        // the Gram scratch aliases S / Sf, free here: the factor of the previous pass is done
+        __syncthreads();
+        if (grp < 3) {
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -585,14 +622,21 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) k_cholqr_coop(CoopArgs p) {
             for (int q = 0; q < 8; ++q) Pc[i][c0 + q] = acc[q];
         }
         // ---- rows <- rows * R^-1, 128 rows at a time (thread: one row, 16 columns)
-        {
+        const bool last = pass + 1 == p.passes;
+        for (int t = 0; t < ntile; ++t) {
+            if (ntile > 1) {
+                __syncthreads();
+                load_tile(t);
+                __syncthreads();
+            }
+            const int tn = ntile > 1 ? tile_rows(t) : nr;
             const int i = tid & 127, c0 = (tid >> 7) * 16;
-            for (int rb = 0; rb < nr; rb += 128) {
+            for (int rb = 0; rb < tn; rb += 128) {
                 const int r = rb + i;
                 float acc[16];
 #pragma unroll
                 for (int q = 0; q < 16; ++q) acc[q] = 0.f;
-                if (r < nr) {
+                if (r < tn) {
                     for (int q2 = 0; q2 < bi; ++q2) {
                         const float v = Ps[r][q2];
 #pragma unroll
@@ -600,12 +644,13 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) k_cholqr_coop(CoopArgs p) {
                     }
                 }
                 __syncthreads();
-                if (r < nr) {
+                if (r < tn) {
 #pragma unroll
                     for (int q = 0; q < 16; ++q) Ps[r][c0 + q] = acc[q];
                 }
                 __syncthreads();
             }
+            if (ntile > 1) store_tile(t, last);
         }
     }
     __syncthreads();
@@ -613,17 +658,7 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) k_cholqr_coop(CoopArgs p) {
         for (int e = tid; e < MAXB * MAXB; e += COOP_THREADS)
             p.rinv_out[e] = double(Pc[e % MAXB][e / MAXB]);
     }
-    for (int e = tid; e < nr * MAXB; e += COOP_THREADS) {
-        const int r = e % nr, col = e / nr;
-        if (col >= bi) continue;
-        const float v = Ps[r][col];
-        p.P[r0 + r + int64_t(col) * p.ldp] = v;
-        if (p.out_hi) {
-            const bf16 h = __float2bfloat16_rn(v);
-            p.out_hi[r0 + r + int64_t(col) * p.ldo] = h;
-            if (p.out_lo) p.out_lo[r0 + r + int64_t(col) * p.ldo] = __float2bfloat16_rn(v - __bfloat162float(h));
-        }
-    }
+    if (ntile == 1) store_tile(0, true);
 }
 
 __global__ void k_identity(double* R, int bi) {
@@ -823,7 +858,8 @@ bool cholqr_coop(cudaStream_t st, float* P, int64_t ldp, int64_t rows, int bi, i
     if (max_ctas[v] <= 0 || bi < 1 || bi > MAXB || rows <= 0 || passes < 1) return false;
     int G = int(std::min<int64_t>(max_ctas[v], cdiv(rows, 64)));
     const int64_t rows_per = cdiv(rows, G);
-    if (rows_per > COOP_ROWS) return false;
+    // slices taller than COOP_ROWS are streamed in tiles (int row indices inside a slice)
+    if (rows_per > (int64_t(1) << 28)) return false;
     G = int(cdiv(rows, rows_per));
     if (scratch_bytes < cholqr_coop_scratch_bytes()) return false;
     CoopArgs a;

@@ -222,3 +222,37 @@ def test_quantize_bf16x2_split():
     assert rel.max() <= 2.0 ** -16
     assert abs(norms[0] - np.sum(A * A)) <= 1e-12 * norms[0]
     assert abs(norms[2] - np.sum((A - hi.double().cpu().numpy()) ** 2)) <= 1e-9 * norms[2]
+
+
+@pytest.fixture(scope="module")
+def A_tall():
+    return synth.dense_from_spectrum(70000, 1024, synth.sigma_exp(1024, 20.0, 1e-6), seed=19)
+
+
+@pytest.mark.parametrize("alg", ["ei", "fp"])
+def test_mixed_tall_panels(A_tall, alg):
+    """m = 70000 rows: the fused CholeskyQR slices (461 rows per CTA) exceed the rows a CTA holds
+    in shared memory, so each phase streams them in tiles.  Same bar as the resident case:
+    converged, true error below tol, rank close to the float64 oracle's (140), Q orthonormal to
+    float32 accuracy, and the indicator within Theorem 3's float32 bound of the true error.
+
+    n = 1024 keeps the rank small against n: the sketches read bf16 A_hi, and every captured
+    direction is rotated by the quantisation error D = A - A_hi, leaving about ||D||_2^2 of energy
+    behind, k ||D||_2^2 ~ (u_bf16^2 / 3)(k / n)(1 + sqrt(n / m))^2 ||A||^2 in all; at n = 256 and
+    k ~ 140 that floor (1.7e-6 ||A||^2) is above tol^2 and the mixed path cannot converge."""
+    A = A_tall
+    tol = 1e-3
+    Ad = torch.tensor(A, device="cuda")
+    hi, lo, norms = qb.quantize_bf16x2(Ad)
+    del Ad
+    f = qb.qb_ei_dense if alg == "ei" else qb.qb_fp_dense
+    Q, B, info = f(hi, tol, 32, P=1, seed=4, a_lo=lo, src_norm2=norms[0], prec="mixed")
+    assert info.converged
+    err = np.linalg.norm(A - _qb(Q, B)) / np.linalg.norm(A)
+    assert err < tol
+    ref = (oracle.randqb_ei if alg == "ei" else oracle.randqb_fp)(A, tol, 32, seed=4, P=1)
+    assert ref.rank - 2 <= info.rank <= 1.15 * ref.rank
+    Qd = Q.double()
+    orth = (Qd.T @ Qd - torch.eye(info.rank, dtype=torch.float64, device="cuda")).abs().max().item()
+    assert orth <= 1e-4
+    assert abs(info.err2_est - (err ** 2) * info.normA2) <= 4 * 2.0 ** -24 * info.normA2
