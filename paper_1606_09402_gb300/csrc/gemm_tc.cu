@@ -498,8 +498,13 @@ struct PCfg {
     static constexpr int A_TILE = BM * BK * 2;
     static constexpr int B_TILE = BN * BK * 2;
     static constexpr int STAGE = NA * A_TILE + NB * B_TILE;
-    static constexpr int STAGES = (200 * 1024) / STAGE < 8 ? (200 * 1024) / STAGE : 8;
+    // up to 224 KB of stages (the kernel has no static shared memory; 227 KB per block): the
+    // three-term operands make a stage 56-72 KB at BN = 64, where every extra stage in flight
+    // counts for the HBM-bound narrow passes
+    static constexpr int STAGE_BUDGET = 224 * 1024;
+    static constexpr int STAGES = STAGE_BUDGET / STAGE < 8 ? STAGE_BUDGET / STAGE : 8;
     static constexpr int SMEM = STAGES * STAGE + 1024 + 512;
+    static_assert(SMEM <= 227 * 1024, "dynamic shared memory above the per-block limit");
     static constexpr int NSMALL = prec_nsmall(NA, NB);
     // chain buffers: two at BN = 64; one at BN = 128, which leaves three ring slots (the chain is
     // drained once per PREC_CHUNK k-blocks, the ring once per MMA)
