@@ -112,17 +112,18 @@ template <> struct Vec<double, 4> {
 // acc += sum over p in [b, e) of val[p] * X[idx[p], lane*NQ .. lane*NQ+NQ).  The 32 (index, value)
 // pairs of a chunk are loaded once by the warp and broadcast; full chunks are unrolled so that
 // eight row gathers are in flight per warp.
+// Positions are int64 so that p0 + 32 cannot wrap for nnz near INT32_MAX.
 template <class T, int NQ>
 __device__ __forceinline__ void row_acc(const int32_t* __restrict__ idx, const T* __restrict__ val,
-                                        int32_t b, int32_t e, const T* __restrict__ X, int64_t ldx,
+                                        int64_t b, int64_t e, const T* __restrict__ X, int64_t ldx,
                                         int lane, T (&acc)[NQ]) {
     const T* xl = X + lane * NQ;
-    for (int32_t p0 = b; p0 < e; p0 += 32) {
-        const int32_t p = p0 + lane;
+    for (int64_t p0 = b; p0 < e; p0 += 32) {
+        const int64_t p = p0 + lane;
         int32_t c = 0;
         T v = T(0);
         if (p < e) { c = idx[p]; v = val[p]; }
-        const int cnt = min(32, e - p0);
+        const int cnt = int(e - p0 < 32 ? e - p0 : 32);
         auto step = [&](int t) {
             const int32_t cc = __shfl_sync(0xffffffffu, c, t);
             const T vv = __shfl_sync(0xffffffffu, v, t);
@@ -172,8 +173,8 @@ k_spmm_seg(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx, con
     const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
     for (int64_t s = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; s < S; s += nw) {
         const int32_t r = seg_row[s];
-        const int32_t b = seg_beg[s];
-        const int32_t e = min(b + CSR_SEG, ptr[r + 1]);
+        const int64_t b = seg_beg[s];
+        const int64_t e = b + CSR_SEG < int64_t(ptr[r + 1]) ? b + CSR_SEG : int64_t(ptr[r + 1]);
         T acc[NQ];
 #pragma unroll
         for (int q = 0; q < NQ; ++q) acc[q] = T(0);
@@ -190,7 +191,7 @@ __global__ void k_seg_count(const int32_t* __restrict__ ptr, int64_t rows, int32
     for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < rows;
          r += int64_t(gridDim.x) * blockDim.x) {
         const int32_t len = ptr[r + 1] - ptr[r];
-        cnt[r] = len > CSR_SEG ? (len + CSR_SEG - 1) / CSR_SEG : 0;
+        cnt[r] = len > CSR_SEG ? len / CSR_SEG + (len % CSR_SEG != 0) : 0;
     }
 }
 
@@ -201,7 +202,8 @@ __global__ void k_seg_fill(const int32_t* __restrict__ ptr, int64_t rows, const 
         const int32_t b = ptr[r], len = ptr[r + 1] - b;
         if (len <= CSR_SEG) continue;
         const int32_t o = off[r];
-        for (int32_t k = 0; k * CSR_SEG < len; ++k) {
+        const int32_t nk = len / CSR_SEG + (len % CSR_SEG != 0);   // b + k CSR_SEG < b + len
+        for (int32_t k = 0; k < nk; ++k) {
             seg_row[o + k] = int32_t(r);
             seg_beg[o + k] = b + k * CSR_SEG;
         }
