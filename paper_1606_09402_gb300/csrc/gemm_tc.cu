@@ -23,6 +23,7 @@
 // loop of the next).  Every mbarrier wait is bounded: on timeout the kernel records an error flag
 // and leaves the loop instead of spinning.
 #include "qb_internal.cuh"
+#include "sched.cuh"
 
 #include <cuda.h>
 
@@ -31,12 +32,12 @@
 namespace qb {
 namespace {
 
-constexpr int BM = 128;      // rows of the accumulator tile (MMA M)
-constexpr int BK = 64;       // k per stage: one 128-byte swizzle row of bf16
+constexpr int BM = TC_BM;    // rows of the accumulator tile (MMA M)
+constexpr int BK = TC_BK;    // k per stage: one 128-byte swizzle row of bf16
 constexpr int UMMA_K = 16;   // k per tcgen05.mma (kind::f16)
 constexpr int NUM_THREADS = 192;
 constexpr uint64_t WAIT_NS = 2000000000ull;   // bounded waits: 2 s
-constexpr int MAX_SK_CTAS = 160;              // stream-K launches use at most this many CTAs
+constexpr int MAX_SK_CTAS = TC_MAX_SK_CTAS;
 
 // ---------------------------------------------------------------- PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -199,18 +200,6 @@ __device__ __forceinline__ void store_row(float* D, int64_t ldd, int64_t gr, int
 }
 
 // ---------------------------------------------------------------- schedule
-struct Sched {
-    int tiles_m, tiles_n, kb;   // units = tiles_m * tiles_n, k-blocks per unit
-    int streamk;                // 1: split flattened k-blocks evenly across CTAs
-};
-// Segment of CTA c: unit u, k-blocks [k0, k1), slot = partial slot (-1 = whole unit)
-struct Seg {
-    int u, k0, k1, slot;
-};
-__host__ __device__ __forceinline__ int64_t sk_begin(int64_t total, int64_t c, int64_t G) {
-    return (total * c) / G;
-}
-
 // ---------------------------------------------------------------- kernel
 struct Params {
     int M, N, K;                 // D is M x N, reduction length K
@@ -275,33 +264,6 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
 
     // this CTA's segments
     const Sched& sc = p.s;
-    const int64_t units = int64_t(sc.tiles_m) * sc.tiles_n;
-    int64_t beg, end;   // in k-blocks (stream-K) or units (raster)
-    if (sc.streamk) {
-        beg = sk_begin(units * sc.kb, cta, G);
-        end = sk_begin(units * sc.kb, cta + 1, G);
-    } else {
-        beg = cta;
-        end = units;
-    }
-    auto next_seg = [&](int64_t& pos, Seg& sg, bool& first) -> bool {
-        if (sc.streamk) {
-            if (pos >= end) return false;
-            const int64_t u = pos / sc.kb;
-            const int k0 = int(pos - u * sc.kb);
-            const int64_t rem = end - u * sc.kb;
-            const int k1 = int(rem < sc.kb ? rem : int64_t(sc.kb));
-            const bool whole = (k0 == 0 && k1 == sc.kb);
-            sg = Seg{int(u), k0, k1, whole ? -1 : (first ? 0 : 1)};
-            pos = u * sc.kb + k1;
-        } else {
-            if (pos >= end) return false;
-            sg = Seg{int(pos), 0, sc.kb, -1};
-            pos += G;
-        }
-        first = false;
-        return true;
-    };
     auto unit_rc = [&](int u, int& r0, int& c0) {
         r0 = (u / sc.tiles_n) * BM;
         c0 = (u % sc.tiles_n) * BN;
@@ -312,11 +274,10 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
         // ---------------------------------------------------------- TMA producer
         int stage = 0;
         uint32_t phase = 0;
-        int64_t pos = beg;
-        bool first = true;
+        SegWalk wk(sc, cta, G);
         Seg sg;
         constexpr uint32_t bytes = uint32_t(C::STAGE);
-        while (ok && next_seg(pos, sg, first)) {
+        while (ok && wk.next(sg)) {
             int r0, c0;
             unit_rc(sg.u, r0, c0);
             for (int kb = sg.k0; kb < sg.k1 && ok; ++kb) {
@@ -347,12 +308,11 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
         constexpr uint32_t idesc = idesc_bf16(BN, TRANS);
         int stage = 0;
         uint32_t phase = 0;
-        int64_t pos = beg;
-        bool first = true;
+        SegWalk wk(sc, cta, G);
         Seg sg;
         int buf = 0;
         uint32_t tphase[2] = {0, 0};
-        while (ok && next_seg(pos, sg, first)) {
+        while (ok && wk.next(sg)) {
             for (int c0 = sg.k0; c0 < sg.k1 && ok; c0 += p.chunk) {
                 const int c1 = min(sg.k1, c0 + p.chunk);
                 ok = mbar_wait(tempty + buf, tphase[buf] ^ 1, p.err);
@@ -394,12 +354,11 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
         // ---------------------------------------------------------- epilogue
         const int q = warp & 3;                 // tensor-memory lane quarter of this warp
         const int row = q * 32 + lane;
-        int64_t pos = beg;
-        bool first = true;
+        SegWalk wk(sc, cta, G);
         Seg sg;
         int buf = 0;
         uint32_t tphase[2] = {0, 0};
-        while (ok && next_seg(pos, sg, first)) {
+        while (ok && wk.next(sg)) {
             int r0, c0;
             unit_rc(sg.u, r0, c0);
             const int64_t gr = int64_t(r0) + row;
@@ -564,42 +523,15 @@ k_tc_prec(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
     const uint32_t tm_big = tmem + uint32_t(C::SMALL_COLS);  // NSLOT x BN columns
 
     const Sched& sc = p.s;
-    const int64_t units = int64_t(sc.tiles_m) * sc.tiles_n;
-    int64_t beg, end;
-    if (sc.streamk) {
-        beg = sk_begin(units * sc.kb, cta, G);
-        end = sk_begin(units * sc.kb, cta + 1, G);
-    } else {
-        beg = cta;
-        end = units;
-    }
-    auto next_seg = [&](int64_t& pos, Seg& sg, bool& first) -> bool {
-        if (pos >= end) return false;
-        if (sc.streamk) {
-            const int64_t u = pos / sc.kb;
-            const int k0 = int(pos - u * sc.kb);
-            const int64_t rem = end - u * sc.kb;
-            const int k1 = int(rem < sc.kb ? rem : int64_t(sc.kb));
-            const bool whole = (k0 == 0 && k1 == sc.kb);
-            sg = Seg{int(u), k0, k1, whole ? -1 : (first ? 0 : 1)};
-            pos = u * sc.kb + k1;
-        } else {
-            sg = Seg{int(pos), 0, sc.kb, -1};
-            pos += G;
-        }
-        first = false;
-        return true;
-    };
 
     bool ok = true;
     if (warp == 0 && lane == 0) {
         // ---------------------------------------------------------- TMA producer
         int stage = 0;
         uint32_t phase = 0;
-        int64_t pos = beg;
-        bool first = true;
+        SegWalk wk(sc, cta, G);
         Seg sg;
-        while (ok && next_seg(pos, sg, first)) {
+        while (ok && wk.next(sg)) {
             const int r0 = (sg.u / sc.tiles_n) * BM, c0 = (sg.u % sc.tiles_n) * BN;
             for (int kb = sg.k0; kb < sg.k1 && ok; ++kb) {
                 ok = mbar_wait(empty + stage, phase ^ 1, p.err);
@@ -635,10 +567,9 @@ k_tc_prec(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
         uint32_t slot_ph = 0;   // bit s: phase of slot s
         int sbuf = 0;
         uint32_t sph = 0;   // bit b: phase of chain buffer b
-        int64_t pos = beg;
-        bool first = true;
+        SegWalk wk(sc, cta, G);
         Seg sg;
-        while (ok && next_seg(pos, sg, first)) {
+        while (ok && wk.next(sg)) {
             for (int c0 = sg.k0; c0 < sg.k1 && ok; c0 += PREC_CHUNK) {
                 const int c1 = min(sg.k1, c0 + PREC_CHUNK);
                 const uint32_t acc_s = tm_small + uint32_t(sbuf * BN);
@@ -715,10 +646,9 @@ k_tc_prec(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
         uint32_t slot_ph = 0;
         int sbuf = 0;
         uint32_t sph = 0;   // bit b: phase of chain buffer b
-        int64_t pos = beg;
-        bool first = true;
+        SegWalk wk(sc, cta, G);
         Seg sg;
-        while (ok && next_seg(pos, sg, first)) {
+        while (ok && wk.next(sg)) {
             const int r0 = (sg.u / sc.tiles_n) * BM, c0 = (sg.u % sc.tiles_n) * BN + h * HC;
             const int64_t gr = int64_t(r0) + row;
             float* pslot = sg.slot >= 0
@@ -803,27 +733,22 @@ __global__ void __launch_bounds__(256) k_tc_fixup(Params p, int G) {
     __shared__ int64_t first_s;
     __shared__ int count_s;
     const Sched& sc = p.s;
-    const int u = blockIdx.x;
-    const int64_t total = int64_t(sc.tiles_m) * sc.tiles_n * sc.kb;
+    // unit ur of the split space: all units (stream-K) or those after the raster ones (hybrid)
+    const int64_t ur = blockIdx.x;
+    const int u = int(split_first_unit(sc) + ur);
     if (threadIdx.x == 0) {
-        auto owner = [&](int64_t x) {
-            int64_t c = (x * G) / total;
-            while (c + 1 < G && sk_begin(total, c + 1, G) <= x) ++c;
-            while (c > 0 && sk_begin(total, c, G) > x) --c;
-            return c;
-        };
-        const int64_t f = int64_t(u) * sc.kb;
-        const int64_t c_first = owner(f), c_last = owner(f + sc.kb - 1);
+        int64_t c_first;
+        int count;
+        split_owners(sc, ur, G, c_first, count);
         first_s = c_first;
-        count_s = c_first == c_last ? 0 : int(c_last - c_first + 1);
+        count_s = count;
     }
     __syncthreads();
     const int count = count_s;
     if (count == 0) return;
     for (int t = threadIdx.x; t < count; t += blockDim.x) {
         const int64_t c = first_s + t;
-        const int slot = (sk_begin(total, c, G) / sc.kb == u) ? 0 : 1;
-        base[t] = (c * 2 + slot) * BN * BM;
+        base[t] = (c * 2 + split_slot(sc, ur, c, G)) * BN * BM;
     }
     __syncthreads();
     const int e = blockIdx.y * blockDim.x + threadIdx.x;
@@ -946,7 +871,7 @@ void run(cudaStream_t st, const CUtensorMap& a0, const CUtensorMap& a1, const CU
     kern<<<G, NUM_THREADS, C::SMEM, st>>>(a0, a1, b0, b1, p);
     QB_LAUNCHED();
     if (p.s.streamk) {
-        const dim3 grid(unsigned(p.s.tiles_m * p.s.tiles_n), unsigned(BM * BN / 256));
+        const dim3 grid(unsigned(split_units(p.s)), unsigned(BM * BN / 256));
         k_tc_fixup<BN><<<grid, 256, 0, st>>>(p, G);
         QB_LAUNCHED();
     }
@@ -969,7 +894,7 @@ void run_prec(cudaStream_t st, const CUtensorMap& a0, const CUtensorMap& a1, con
     kern<<<G, PREC_THREADS, C::SMEM, st>>>(a0, a1, a2, b0, b1, b2, p);
     QB_LAUNCHED();
     if (p.s.streamk) {
-        const dim3 grid(unsigned(p.s.tiles_m * p.s.tiles_n), unsigned(BM * BN / 256));
+        const dim3 grid(unsigned(split_units(p.s)), unsigned(BM * BN / 256));
         k_tc_fixup<BN><<<grid, 256, 0, st>>>(p, G);
         QB_LAUNCHED();
     }
@@ -1008,31 +933,17 @@ Scratch carve(void* scratch, size_t bytes, int64_t rows, int64_t w) {
     return s;
 }
 
-Sched make_sched(int64_t M, int64_t N, int64_t K, int bn, int G) {
-    Sched s;
-    s.tiles_m = int(cdiv(M, BM));
-    s.tiles_n = int(cdiv(N, bn));
-    s.kb = int(cdiv(K, BK));
-    const int64_t units = int64_t(s.tiles_m) * s.tiles_n;
-    // Stream-K balances the k-blocks exactly but costs a fix-up launch and partial-tile traffic
-    // (worth about 8 k-blocks); raster runs whole units in ceil(units / G) waves.  Take stream-K
-    // below ~8 waves when it is the shorter of the two.  With several column tiles, raster CTAs
-    // of one row tile walk k together and share each A tile through L2, while stream-K CTAs sit
-    // at unrelated k positions and read A once per column tile: raster then, unless there is
-    // less than one wave of units.
-    const int64_t waves = (units + G - 1) / G;
-    s.streamk = (units < 8LL * G && (units * s.kb) / G + 8 < waves * s.kb &&
-                 (s.tiles_n == 1 || units < G)) ? 1 : 0;
-    return s;
-}
-
-// CTAs to launch: never more than there are k-blocks (stream-K) or units (raster), so that every
-// CTA of a stream-K launch owns a non-empty range.
-int grid_size(const Sched& s, int sms) {
-    const int64_t units = int64_t(s.tiles_m) * s.tiles_n;
-    const int64_t work = s.streamk ? units * s.kb : units;
-    const int64_t cap = s.streamk ? std::min(sms, MAX_SK_CTAS) : sms;
-    return int(std::max<int64_t>(1, std::min<int64_t>(cap, work)));
+// The partial slots of a split launch must fit the scratch; a hybrid schedule that does not fit
+// falls back to raster, a stream-K one is an error.
+void fit_partials(Sched& s, int& G, int sms, int bn, size_t part_bytes) {
+    if (!s.streamk || size_t(G) * 2 * bn * BM * sizeof(float) <= part_bytes) return;
+    if (s.streamk == 2) {
+        s.streamk = 0;
+        s.dp_units = 0;
+        G = grid_size(s, sms);
+        return;
+    }
+    throw Error{QB_ERR_WORKSPACE, "tensor-core partials"};
 }
 
 }  // namespace
@@ -1079,8 +990,7 @@ void tc_sketch(cudaStream_t st, const bf16* A, int64_t lda, int64_t m, int64_t n
     p.ldd = ldy;
     p.part = s.part;
     p.err = s.err;
-    if (p.s.streamk && size_t(G) * 2 * bn * BM * sizeof(float) > s.part_bytes)
-        throw Error{QB_ERR_WORKSPACE, "tensor-core partials"};
+    fit_partials(p.s, G, num_sms(), bn, s.part_bytes);
     const CUtensorMap a = make_map(A, n, m, lda, BK, BM);
     const CUtensorMap b = make_map(Vt, n, w, ldv, BK, bn);
     if (Vt_lo) {
@@ -1122,8 +1032,7 @@ void tc_trans(cudaStream_t st, const bf16* A_hi, const bf16* A_lo, int64_t lda, 
     p.ldd = ldz;
     p.part = s.part;
     p.err = s.err;
-    if (p.s.streamk && size_t(G) * 2 * bn * BM * sizeof(float) > s.part_bytes)
-        throw Error{QB_ERR_WORKSPACE, "tensor-core partials"};
+    fit_partials(p.s, G, num_sms(), bn, s.part_bytes);
     // A as an (n inner, m outer) tensor; boxes of 64 columns x 64 rows
     const CUtensorMap a0 = make_map(A_hi, n, m, lda, 64, BK);
     const CUtensorMap b0 = make_map(s.vhi, m, w, ldo, BK, bn);
@@ -1185,8 +1094,7 @@ void tc_prec_gemm(cudaStream_t st, bool trans, const bf16* const* A, int na, int
     p.ldd = ldd;
     p.part = s.part;
     p.err = s.err;
-    if (p.s.streamk && size_t(G) * 2 * bn * BM * sizeof(float) > s.part_bytes)
-        throw Error{QB_ERR_WORKSPACE, "tensor-core partials"};
+    fit_partials(p.s, G, num_sms(), bn, s.part_bytes);
     const int64_t Kd = std::max<int64_t>(K, 1);
     CUtensorMap am[3];
     for (int i = 0; i < 3; ++i) {
@@ -1245,8 +1153,7 @@ void tc_xtp(cudaStream_t st, const bf16* Xhi, const bf16* Xlo, int64_t ldx, int6
     p.ldd = ldt;
     p.part = s.part;
     p.err = s.err;
-    if (p.s.streamk && size_t(G) * 2 * bn * BM * sizeof(float) > s.part_bytes)
-        throw Error{QB_ERR_WORKSPACE, "tensor-core partials"};
+    fit_partials(p.s, G, num_sms(), bn, s.part_bytes);
     // "A" operand: X^T as a row-major j0 x rows matrix = X column-major
     const CUtensorMap a0 = make_map(Xhi, rows, j0, ldx, BK, BM);
     const CUtensorMap b0 = make_map(s.vhi, rows, bw, ldb, BK, bn);
@@ -1286,8 +1193,7 @@ void tc_p_minus_xt(cudaStream_t st, const bf16* Xhi, const bf16* Xlo, int64_t ld
     p.ldd = ldp;
     p.part = s.part;
     p.err = s.err;
-    if (p.s.streamk && size_t(G) * 2 * bn * BM * sizeof(float) > s.part_bytes)
-        throw Error{QB_ERR_WORKSPACE, "tensor-core partials"};
+    fit_partials(p.s, G, num_sms(), bn, s.part_bytes);
     // "A" operand of the transposed form: X^T as a row-major j0 x rows tensor (K = j0, M = rows)
     const CUtensorMap a0 = make_map(Xhi, rows, j0, ldx, 64, BK);
     const CUtensorMap b0 = make_map(s.vhi, j0, bw, ldo, BK, bn);

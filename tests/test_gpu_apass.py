@@ -1,6 +1,7 @@
 """The tensor-core passes over dense A (tcgen05 + TMA), through the C ABI, against float64
 products computed on the CPU.  Covers the stream-K schedule (one column tile), the raster
-schedule (many units), ragged tails in every dimension, and the three-product hi/lo pass."""
+schedule (many units), the hybrid schedule (whole raster waves, then the k-blocks of the
+remaining units split across all CTAs), ragged tails in every dimension, and the hi/lo passes."""
 import numpy as np
 import pytest
 
@@ -73,6 +74,39 @@ def test_trans_bf16(m, n, w, precise):
         Ah = hi.double().cpu().numpy()
         ref = Ah.T @ _bf16(V).double().numpy()
         scale = np.abs(Ah.T) @ np.abs(_bf16(V).double().numpy()) + 1e-30
+        assert _rel_err(Z, ref, scale) < 1e-5
+
+
+@pytest.mark.parametrize("kind", ["sketch", "trans_two_term"])
+def test_hybrid_schedule(kind):
+    """Shapes whose last raster wave is partial, which the hybrid schedule splits: a sketch of
+    20000 rows at w = 512 (157 x 2 units of 128 x 256 on 152 CTAs) and the transposed pass of
+    randQB_FP's H chunk at 20000 output rows, w = 512, G held as two-term bf16 values (157 x 4
+    units of 128 x 128: the pattern of the 40000 x 20000 step)."""
+    rng = np.random.default_rng(17 if kind == "sketch" else 18)
+    if kind == "sketch":
+        m, n, w = 20000, 4096, 512
+        A = rng.standard_normal((m, n)).astype(np.float32)
+        V = rng.standard_normal((n, w)).astype(np.float32)
+        Ad = _bf16(A).cuda()
+        Y = qb.qb_apass_sketch(Ad, torch.tensor(V).cuda()).cpu().numpy().astype(np.float64)
+        Ah = Ad.double().cpu().numpy()
+        Vh = _bf16(V).double().numpy()
+        ref = Ah @ Vh
+        scale = np.abs(Ah) @ np.abs(Vh) + 1e-30
+        assert _rel_err(Y, ref, scale) < 1e-5
+    else:
+        m, n, w = 4096, 20000, 512
+        A = rng.standard_normal((m, n))
+        Vt = torch.tensor(rng.standard_normal((m, w)).astype(np.float32))
+        v_hi = Vt.to(torch.bfloat16).float()
+        V2 = v_hi + (Vt - v_hi).to(torch.bfloat16).float()     # 16 significant bits
+        hi, lo, _ = qb.quantize_bf16x2(torch.tensor(A).cuda())
+        Z = qb.qb_apass_trans(hi, V2.cuda(), precise=3, a_lo=lo).cpu().numpy().astype(np.float64)
+        Ahl = hi.double().cpu().numpy() + lo.double().cpu().numpy()
+        Vd = V2.double().numpy()
+        ref = Ahl.T @ Vd
+        scale = np.abs(Ahl.T) @ np.abs(Vd) + 1e-30
         assert _rel_err(Z, ref, scale) < 1e-5
 
 
