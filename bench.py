@@ -34,12 +34,14 @@ RANK_SPECTRUM = 4096
 TOL, B, P, SEED_A, SEED_OMEGA = 1e-3, 64, 1, 1606, 9402
 L_TILDE = 50 * B
 RANK_CAP = 4096
-# DRAM bytes of one k_tc_prec<128, true, 2, 2> launch (w = 512): ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum) on the 16384 x 8192 case, 604.1 MB + 13.2 MB, scaled by the size of A
-# (x 5.96) to 40000 x 20000; the algorithmic bytes there are 3.28 GB (A hi + lo and G's two terms).
-PREC_TRAFFIC_BYTES = 3.68e9
-PREC_TRAFFIC_NOTE = ("ncu dram bytes of k_tc_prec<128,1,2,2> on 16384x8192 (617.3 MB), scaled by "
-                     "the size of A to 40000x20000; algorithmic 3.28 GB")
+# DRAM bytes of one k_tc_prec<128, true, 2, 2> launch (w = 512) at 40000 x 20000: not measured
+# for the current schedule.  The small case's counters (ncu on 16384 x 8192: 1468.6 MB read,
+# 18.6 MB written, for 570 MB algorithmic) do not scale to it: that launch splits 104 of its 256
+# units across CTAs, the full-size one 20 of 628, and split units read A without the L2 sharing
+# of raster order.  Under raster the small case read 617.3 MB, 1.08x algorithmic.
+PREC_TRAFFIC_BYTES = None
+PREC_TRAFFIC_NOTE = ("not measured at 40000x20000 for the hybrid schedule; ncu at 16384x8192 "
+                     "(104 of 256 units split): 1487.2 MB read + written for 570 MB algorithmic")
 
 
 def parse():
