@@ -34,14 +34,13 @@ RANK_SPECTRUM = 4096
 TOL, B, P, SEED_A, SEED_OMEGA = 1e-3, 64, 1, 1606, 9402
 L_TILDE = 50 * B
 RANK_CAP = 4096
-# DRAM bytes of one k_tc_prec<128, true, 2, 2> launch (w = 512) at 40000 x 20000: not measured
-# for the current schedule.  The small case's counters (ncu on 16384 x 8192: 1468.6 MB read,
-# 18.6 MB written, for 570 MB algorithmic) do not scale to it: that launch splits 104 of its 256
-# units across CTAs, the full-size one 20 of 628, and split units read A without the L2 sharing
-# of raster order.  Under raster the small case read 617.3 MB, 1.08x algorithmic.
-PREC_TRAFFIC_BYTES = None
-PREC_TRAFFIC_NOTE = ("not measured at 40000x20000 for the hybrid schedule; ncu at 16384x8192 "
-                     "(104 of 256 units split): 1487.2 MB read + written for 570 MB algorithmic")
+# DRAM bytes of one k_tc_prec<128, true, 2, 2> launch (w = 512) at 40000 x 20000: ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum, one pass) on the first H chunk of one mixed
+# randQB_FP step, 4.23 GB + 44.4 MB, against 3.32 GB algorithmic (A hi + lo 3.2 GB, G's two bf16
+# terms 82 MB, H 41 MB): the 20 units the hybrid schedule splits read A without L2 sharing.
+PREC_TRAFFIC_BYTES = 4.274e9
+PREC_TRAFFIC_NOTE = ("ncu dram bytes (one pass) of the first k_tc_prec<128,1,2,2> launch of a "
+                     "40000x20000 step: 4.23 GB read + 44.4 MB written; algorithmic 3.32 GB")
 
 
 def parse():
