@@ -311,8 +311,10 @@ k_chol(const double* __restrict__ W, int bi, double tau_rel, double* __restrict_
 // keeps its slice of rows in shared memory for the whole call, forms the partial Gram of the slice,
 // the CTAs sum the partials (each CTA an equal share of the entries, in CTA order), every CTA
 // factors the 64 x 64 Gram itself (the same arithmetic in every CTA, so the same R), and applies
-// R^-1 to its rows.  The panel is read and written once.  Grid-wide barriers use a global arrive
-// counter and generation word; every wait is bounded and a timeout sets err.
+// R^-1 to its rows.  The panel is read and written once when every slice fits in shared memory
+// (COOP_ROWS rows per CTA); a taller slice is streamed through it in tiles of COOP_ROWS rows,
+// re-read in each phase.  Grid-wide barriers use a global arrive counter and generation word;
+// every wait is bounded and a timeout sets err.
 //
 // PRECISE = false (power scheme, only the span matters): float32 Gram and factor.
 // PRECISE = true (Q_i of the randQB loops): the Gram is summed in two levels (float32 over 8 rows,

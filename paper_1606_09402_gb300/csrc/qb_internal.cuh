@@ -197,7 +197,8 @@ enum CholPrec { CHOL_F64 = 0, CHOL_F64_INV_F32 = 1, CHOL_F32 = 2, CHOL_ADAPTIVE 
 // two may be the same buffer).
 // bar: two zero-initialised words kept across calls; err is set if a grid barrier timed out.
 // out_hi (nullable): also write bf16(P) there (ld ldo), and bf16(P - bf16(P)) to out_lo when given.
-// Returns false (nothing launched) when the panel does not fit the launch.
+// Slices taller than the rows a CTA holds in shared memory are streamed through it in tiles.
+// Returns false (nothing launched) when no cooperative launch is possible or the scratch is short.
 size_t cholqr_coop_scratch_bytes();
 bool cholqr_coop(cudaStream_t st, float* P, int64_t ldp, int64_t rows, int bi, int passes,
                  bool precise, double tau, const double* rinv_prev, double* rinv_out,
