@@ -50,7 +50,8 @@ typedef enum {
     QB_ERR_CUDA = -3,        /* a CUDA call failed; qb_last_cuda_error() names it */
     QB_ERR_BREAKDOWN = -4,   /* reserved: panel factorisation produced non-finite values */
     QB_ERR_WORKSPACE = -5,   /* ws_bytes below the matching *_workspace() query */
-    QB_ERR_TIMEOUT = -6,     /* a bounded device-side wait ran out (batched path) */
+    QB_ERR_TIMEOUT = -6,     /* a bounded device-side wait ran out (tensor-core pipelines, grid
+                                barriers of the fused CholeskyQR, the batched graph) */
     QB_ERR_UNSUPPORTED = -7  /* dtype / precision combination not provided */
 } qb_status;
 
