@@ -189,6 +189,26 @@ def pass_time(torch, qb, fn, reps, phase):
     return total / 1e3 / reps
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), or "" if neither says."""
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return ""
+
+
 def cpu_baseline(A_rows, m_full):
     """The float64 oracle's randQB_FP on a row sample of the same A, scaled to the full workload
     by m_full / rows (every dominant cost of randQB_FP is linear in m)."""
@@ -207,7 +227,7 @@ def cpu_baseline(A_rows, m_full):
         cores = max((i.get("num_threads") or 0) for i in threadpool_info()) or cores
     except Exception:
         pass
-    return {"value": t * scale, "unit": "s", "cores": cores, "kind": "oracle",
+    return {"value": t * scale, "unit": "s", "cores": cores, "kind": "oracle", "cpu": cpu_model(),
             "sample": f"oracle randQB_FP (float64 numpy/LAPACK) on rows 0..{m_s - 1} of the same A "
                       f"(rank {r.rank}), {t:.1f} s measured, scaled by m/{m_s} = {scale:g}"}
 
@@ -342,6 +362,7 @@ def run_reference(args, ws, rank):
             "data": "synthetic",
             "config": config_dict(m, n),
             "cpu_baseline": {"value": v, "unit": "s", "cores": cores, "kind": "oracle",
+                             "cpu": cpu_model(),
                              "sample": f"oracle randQB_FP on rows 0..{m_s - 1} (rank {rank_out}), "
                                        f"scaled by m/{m_s}"},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
