@@ -532,7 +532,10 @@ def run_ours(args, ws, rank, local):
     if rank != 0:
         return
 
-    sustained = pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
+    # the passes are timed alone (pass_time: CUDA events around one single-pass call), so the
+    # burst figure is their peak; the sustained one is kept beside it for reference
+    burst = pk["bf16_tflops"]
+    sustained = pk.get("bf16_tflops_sustained", burst)
     cpu = cpu_baseline(A64[: (1000 if args.quick else 4000)].cpu().numpy(), m)
     line = {
         "metric": METRIC, "value": t_step, "unit": "s", "n_gpus": ws, "steps": args.steps,
@@ -545,16 +548,18 @@ def run_ours(args, ws, rank, local):
         "roofline": {"bound": "tensor",
                      "kernel": "k_tc_prec: precise H = (A_hi + A_lo)^T G chunk (w = 512), "
                                "4 bf16 tensor-core products per output",
-                     "achieved": tf_prec, "peak": sustained, "unit": "TFLOP/s",
-                     "frac": tf_prec / sustained, "traffic": PREC_TRAFFIC_BYTES if not args.quick else None,
+                     "achieved": tf_prec, "peak": burst, "unit": "TFLOP/s",
+                     "frac": tf_prec / burst, "traffic": PREC_TRAFFIC_BYTES if not args.quick else None,
                      "traffic_note": PREC_TRAFFIC_NOTE,
                      "algorithmic": "2 m n w flops per launch (the product, not the 4 issued)",
-                     "issued_frac": 4 * tf_prec / sustained, "ms_per_launch": t_prec * 1e3,
-                     "peak_source": f"{pk_src} bf16_tflops_sustained"},
+                     "issued_frac": 4 * tf_prec / burst, "ms_per_launch": t_prec * 1e3,
+                     "frac_of_sustained": tf_prec / sustained,
+                     "peak_source": f"{pk_src} bf16_tflops (burst: the pass is timed alone)"},
         "roofline_sketch": {"bound": "tensor", "kernel": "k_tc_gemm: sketch G = A_hi Omega "
                                                          "(w = l~ = 3200)",
-                            "achieved": tf_sk, "peak": sustained, "unit": "TFLOP/s",
-                            "frac": tf_sk / sustained, "ms_per_launch": t_sk_wide * 1e3},
+                            "achieved": tf_sk, "peak": burst, "unit": "TFLOP/s",
+                            "frac": tf_sk / burst, "ms_per_launch": t_sk_wide * 1e3,
+                            "peak_source": f"{pk_src} bf16_tflops (burst)"},
         "apass": {"sketch_narrow_gbs": gbs_nar_sk, "trans_narrow_precise_gbs": gbs_nar_tr,
                   "hbm_peak_gbs": hbm, "sketch_narrow_frac": gbs_nar_sk / hbm,
                   "trans_narrow_frac": gbs_nar_tr / hbm, "w": B,

@@ -7,9 +7,12 @@
  * Two generators of the blocks Q_i, B_i are offered (Yu, Gu, Li, arXiv:1606.09402):
  *   randQB_EI  (Algorithm 2): per block, sketch A Omega_i, project against Q, orthonormalise,
  *              re-orthogonalise, B_i = Q_i^T A.  2 + 2P passes over A per block.
- *   randQB_FP  (Algorithm 4): G = A Omega and H = A^T G for l~ columns at once (one pass over a
- *              row-major A, Remark 4.2), then the blocked loop builds Q, B from G, H, Omega only
- *              (the re-orthogonalised B_i formula of Sect. 4.2).  1 + 2P passes per Omega batch.
+ *   randQB_FP  (Algorithm 4): G = A Omega and H = A^T G for l~ columns, then the blocked loop
+ *              builds Q, B from G, H, Omega only (the re-orthogonalised B_i formula of
+ *              Sect. 4.2).  Remark 4.2 forms G and H in one read of a row-major A; this library
+ *              forms them in two kernels, each reading A once, so a batch (or chunk, see
+ *              QB_FLAG_WHOLE_BATCH) costs 2 + 2P reads of A where Table 1 counts 1 + 2P.
+ *              qb_info.passes counts every read.
  *
  * Conventions shared by every entry point
  *   - All matrix pointers are DEVICE pointers unless stated otherwise; the caller owns every
@@ -111,10 +114,11 @@ typedef struct {
 /* qb_opts.flags: record CUDA events around the phases of the call (adds a synchronisation at the
  * end); read the device milliseconds with qb_profile_last(). */
 #define QB_FLAG_PROFILE 2
-/* qb_opts.flags (randQB_FP): form each Omega batch of l~ columns in one go, 2 + 2P passes over A
- * per batch as Algorithm 4 is written.  By default the batch is formed in chunks of 512 columns
- * as the blocked loop reaches them (P <= 1): the same Q and B up to rounding (orth is
- * column-causal), the columns after the stopping block are never formed, at 2 + 2P passes per
+/* qb_opts.flags (randQB_FP): form each Omega batch of l~ columns in one go as Algorithm 4 is
+ * written: 1 + 2P reads of A for the power scheme and G, plus one read per 512-column piece of
+ * H (formed as the blocked loop reaches it).  By default the batch is formed in chunks of 512
+ * columns as the blocked loop reaches them (P <= 1): the same Q and B up to rounding (orth is
+ * column-causal), the columns after the stopping block are never formed, at 2 + 2P reads of A per
  * chunk.  With P > 1 the batch is always formed in one go. */
 #define QB_FLAG_WHOLE_BATCH 4
 
@@ -123,7 +127,7 @@ typedef struct {
     double err2_est;     /* E at exit (may be slightly negative through rounding) */
     double err_est;      /* sqrt(max(E, 0)) */
     double normA2;       /* ||A||_F^2 used by the indicator */
-    int64_t passes;      /* passes over A (Table 1 accounting) */
+    int64_t passes;      /* reads of A by the kernels (Table 1's unit; G and H count two) */
     int64_t omega_cols;  /* global Omega columns drawn */
     int32_t status_bits; /* QB_BIT_* */
     int32_t blocks;      /* blocks of the loop that ran */
@@ -159,8 +163,8 @@ size_t qb_dense_workspace(const qb_dense* A, const qb_opts* opts, int32_t algo);
 int32_t qb_ei_dense(const qb_dense* A, const qb_opts* opts, void* Q, int64_t ldq, void* B,
                     int64_t ldb, void* ws, size_t ws_bytes, qb_info* info, void* stream);
 
-/* randQB_FP, Algorithm 4 (power scheme on the whole Omega batch, one pass for G = A Omega and
- * H = A^T G, blocked loop with the re-orthogonalised B_i of Sect. 4.2).  When l~ columns do not
+/* randQB_FP, Algorithm 4 (power scheme on the whole Omega batch, G = A Omega and H = A^T G,
+ * blocked loop with the re-orthogonalised B_i of Sect. 4.2).  When l~ columns do not
  * reach the tolerance the next batch of l~ global Omega columns is drawn (Sect. 4.3), its power
  * iterations act on the implicit residual, and the loop continues with the same Q, B. */
 int32_t qb_fp_dense(const qb_dense* A, const qb_opts* opts, void* Q, int64_t ldq, void* B,
@@ -252,12 +256,14 @@ int32_t qb_fixed_rank_bwd(const qb_dense* A, int64_t k, uint64_t seed, int32_t p
  * tensor-core kernel as qb_apass_sketch, for callers that can neither allocate device memory nor
  * pass a workspace (a process whose device memory is entirely carved up by its own pool, a plug-in
  * that must not call the device allocator).  Its scratch is one 16 MiB file-scope device array
- * that every GPU loading the library reserves until exit; limits: w <= 64 and
- * align8(n) * w * 2 bytes + 10.5 MiB <= 16 MiB (n up to about 43000 at w = 64).  Larger calls
- * return QB_ERR_WORKSPACE.  The first call on a device looks the array's address up
+ * that every GPU loading the library reserves until exit.  Limits: w <= 64, and the bf16 copy of
+ * V (align8(n) * w * 2 bytes, rounded up to 256) plus 10 MiB + 256 bytes of partial tiles and
+ * flag must fit in the 16 MiB, so n <= 49144 at w = 64.  Larger calls return QB_ERR_WORKSPACE
+ * before anything is launched.  The first call on a device looks the array's address up
  * (cudaGetSymbolAddress) and should come before any stream capture.  All calls share the array:
- * calls that overlap on the GPU (other streams, other host threads) race.  The call synchronises
- * the stream to read the kernel's timeout flag.
+ * calls that overlap on the GPU (other streams, other host threads) race.  Every call ends by
+ * copying the kernel's timeout flag to the host and synchronising the stream, so it returns
+ * only after its work has completed.
  * ------------------------------------------------------------------------------------------- */
 int32_t qb_apass_sketch_noalloc(const qb_dense* A, const float* V, int64_t ldv, int64_t w,
                                 float* Y, int64_t ldy, void* stream);

@@ -167,13 +167,18 @@ def randqb_b(A, tol: float, b: int, seed: int, P: int = 0, relative: bool = True
 # ----------------------------------------------------------------------------- randQB_EI (Alg. 2)
 def randqb_ei(A, tol: float, b: int, seed: int, P: int = 0, relative: bool = True,
               rank_cap=None, row_by_row: bool = True, reorth: bool = True,
-              fixed_rank=None, omega_fn=None) -> QBResult:
+              fixed_rank=None, omega_fn=None, A_sketch=None) -> QBResult:
     """Algorithm 2 with the row-by-row stop and the power-scheme reading in the module header.
 
     ``fixed_rank=k`` runs exactly k columns with no tolerance test (the fixed-rank version used by
     Proposition 2).  ``omega_fn(col0, w)`` replaces the Philox Omega (equivalence tests only).
+    ``A_sketch`` (default A) is the matrix the sketch and power steps multiply by; B_i = Q_i^T A
+    and the indicator always use A.  A sketch only has to capture a span, so a perturbed copy
+    (A rounded to bf16) still gives a valid QB of A; this models a representation that streams a
+    reduced copy of A for the sketches.
     """
     m, n = A.shape
+    As = A if A_sketch is None else A_sketch
     normA2 = frob2(A)
     eps = _eps_abs(tol, relative, normA2)
     eps2 = eps * eps
@@ -192,12 +197,12 @@ def randqb_ei(A, tol: float, b: int, seed: int, P: int = 0, relative: bool = Tru
         bi = min(b, cap - k)
         drawn = k + bi
         Om = _omega(n, k, bi, seed) if omega_fn is None else omega_fn(k, bi)
-        Y = A @ Om - Q @ (B @ Om)
+        Y = As @ Om - Q @ (B @ Om)
         passes += 1
         for _ in range(P):
             Y = orth(Y)
-            Z = orth(np.asarray(A.T @ Y) - B.T @ (Q.T @ Y))
-            Y = A @ Z - Q @ (B @ Z)
+            Z = orth(np.asarray(As.T @ Y) - B.T @ (Q.T @ Y))
+            Y = As @ Z - Q @ (B @ Z)
             passes += 2
         Qi = orth(Y)
         if reorth:
@@ -222,12 +227,16 @@ def randqb_ei(A, tol: float, b: int, seed: int, P: int = 0, relative: bool = Tru
 # ----------------------------------------------------------------------------- randQB_FP (Alg. 3/4)
 def randqb_fp(A, tol: float, b: int, seed: int, P: int = 0, l_tilde=None,
               relative: bool = True, rank_cap=None, row_by_row: bool = True,
-              reorth: bool = True, fixed_rank=None, omega_fn=None) -> QBResult:
+              reorth: bool = True, fixed_rank=None, omega_fn=None, A_sketch=None) -> QBResult:
     """Algorithm 4 (Algorithm 3 when ``reorth=False``) with the row-by-row stop.
 
-    ``l_tilde`` defaults to 50 b (Sect. 5.4), clamped to the rank cap.
+    ``l_tilde`` defaults to 50 b (Sect. 5.4), clamped to the rank cap.  ``A_sketch`` (default A)
+    is the matrix the power steps and G = A_sketch Omega multiply by; H = A^T G uses A.  The B_i
+    formula of Sect. 4.2 needs only H = A^T G for the G it is given and B = Q^T A, so B_i is still
+    Q_i^T A with Q_i = orth(G_i - Q B Omega_i).
     """
     m, n = A.shape
+    As = A if A_sketch is None else A_sketch
     normA2 = frob2(A)
     eps = _eps_abs(tol, relative, normA2)
     eps2 = eps * eps
@@ -253,12 +262,12 @@ def randqb_fp(A, tol: float, b: int, seed: int, P: int = 0, l_tilde=None,
         Om = _omega(n, col0, w, seed) if omega_fn is None else omega_fn(col0, w)
         drawn = col0 + w
         for _ in range(P):
-            G = orth(A @ Om - Q @ (B @ Om))
-            Om = orth(np.asarray(A.T @ G) - B.T @ (Q.T @ G))
+            G = orth(As @ Om - Q @ (B @ Om))
+            Om = orth(np.asarray(As.T @ G) - B.T @ (Q.T @ G))
             passes += 2
         if q == 0:
             omega_used = Om.copy()
-        G = A @ Om
+        G = As @ Om
         H = np.asarray(A.T @ G)
         passes += 1
         for c0 in range(0, w, b):

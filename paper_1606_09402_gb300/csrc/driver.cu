@@ -742,7 +742,8 @@ void run_fp(Ctx& c, AOp& A, const Plan& p, const qb_opts& o, Bufs& bf, void* Q, 
         // through the power scheme, G = A Omega and H = A^T G before the blocked loop reaches
         // it.  orth is column-causal (panel Gram-Schmidt / CholeskyQR), so every column comes out
         // as in Algorithm 4 on the whole batch; the chunks after the stopping block are never
-        // formed.  QB_FLAG_WHOLE_BATCH forms the whole batch at once (2 + 2P passes over A).
+        // formed.  QB_FLAG_WHOLE_BATCH forms the whole batch at once: 1 + 2P passes over A for
+        // the power scheme and G, plus one per H_CHUNK-column piece of H.
         const int64_t chunk = whole ? w : std::min<int64_t>(FP_CHUNK, w);
         for (int64_t cc = 0; cc < w && !stop; cc += chunk) {
             const int64_t cw = std::min<int64_t>(chunk, w - cc);
@@ -789,7 +790,9 @@ void run_fp(Ctx& c, AOp& A, const Plan& p, const qb_opts& o, Bufs& bf, void* Q, 
                     const int64_t hw =
                         std::min<int64_t>(std::max<int64_t>(H_CHUNK, bi), cc + cw - h_done);
                     A.apply_t(c, c.col(bf.G, m, h_done), m, hw, c.col(bf.H, n, h_done), n, 4);
-                    if (h_done > cc) out.passes += 1;   // the first H rides on G's pass (Remark 4.2)
+                    // every piece of H is a read of A of its own: G and H are two launches here
+                    // (Remark 4.2's single read would need all n x w of H held on chip)
+                    out.passes += 1;
                     h_done += hw;
                 }
                 const char* Om_i = c.col(bf.Om, n, c0);

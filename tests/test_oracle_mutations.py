@@ -111,3 +111,19 @@ def test_planted_box_muller_mistake_breaks_pairing():
                   "rho * np.cos(theta), rho * np.cos(theta))\n\n\ndef omega_f32")
     z = mod.omega(50000, 0, 2, seed=9402)
     assert abs(np.corrcoef(z[:, 0], z[:, 1])[0, 1]) > 0.5
+
+
+def test_planted_h_from_sketch_copy_breaks_b_equals_qta():
+    """randQB_FP must form H = A^T G from A itself; H taken from the sketch copy makes B differ
+    from Q^T A by about the copy's rounding."""
+    A = synth.dense_from_spectrum(300, 200, synth.sigma_exp(200, 20.0, 1e-6), seed=31)
+    As = A + 1e-3 * np.linalg.norm(A) / np.sqrt(A.size) * \
+        np.random.default_rng(0).standard_normal(A.shape)
+
+    def gap(mod):
+        r = mod.randqb_fp(A, 1e-3, 10, seed=3, P=1, A_sketch=As)
+        return np.linalg.norm(r.B - r.Q.T @ A) / np.linalg.norm(A)
+
+    import oracle.qb as good
+    assert gap(good) <= 1e-10
+    assert gap(mutated("qb.py", "H = np.asarray(A.T @ G)", "H = np.asarray(As.T @ G)")) > 1e-6

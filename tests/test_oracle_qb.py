@@ -286,3 +286,32 @@ def test_adjoint_matches_torch_autograd():
     ref = At.grad.numpy()
     ours = oracle.qb_fixed_rank_adjoint(A, k, 3, GQ, GB)
     assert np.linalg.norm(ours - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+# ----------------------------------------------------------------------------- reduced sketch copy
+def _bf16(X):
+    """Round float64 entries to bfloat16 (round to nearest even) and back (test-side model of a
+    reduced copy of A; the product path has its own kernel for this)."""
+    u = np.ascontiguousarray(X, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("alg", ["ei", "fp"])
+def test_sketch_copy_still_gives_qb_of_a(alg):
+    """With the sketches taken on bf16(A) (a span only), Theorem 1 and B = Q^T A still hold for A
+    itself: for randQB_FP because the B_i formula of Sect. 4.2 needs only H = A^T G for the G it
+    uses.  A mistake that formed H or B_i from the sketch copy breaks both checks."""
+    A = synth.dense_from_spectrum(300, 200, synth.sigma_exp(200, 20.0, 1e-6), seed=31)
+    As = _bf16(A)
+    assert np.linalg.norm(A - As) > 1e-4 * np.linalg.norm(A)
+    f = oracle.randqb_ei if alg == "ei" else oracle.randqb_fp
+    r = f(A, 1e-3, 10, seed=3, P=1, A_sketch=As)
+    assert r.status in (0, 2)
+    nA2 = r.normA2
+    assert np.linalg.norm(r.B - r.Q.T @ A) <= 1e-10 * np.sqrt(nA2)
+    assert abs(r.E - np.linalg.norm(A - r.Q @ r.B) ** 2) <= 1e-12 * nA2
+    assert oracle.orth_loss(r.Q) <= 1e-12
+    # the sketch copy changes Q (a different span), not its validity
+    r0 = f(A, 1e-3, 10, seed=3, P=1)
+    assert np.linalg.norm(r0.Q @ r0.B - r.Q @ r.B) > 1e-8 * np.sqrt(nA2)

@@ -58,3 +58,28 @@ def test_noalloc_rejects_sizes_beyond_its_array():
     V = torch.zeros(256, 65, dtype=torch.float32, device="cuda")
     rc, _ = _call_noalloc(lib, qb, A, V)
     assert rc == -5   # QB_ERR_WORKSPACE: w above the fixed array's limit
+
+
+def test_noalloc_size_limit_boundary():
+    """Both sides of the array's size limit at w = 64: n = 49144 is the largest width whose bf16
+    copy of V (align8(n) * 64 * 2 bytes) fits beside the 10 MiB + 256 bytes of partial tiles and
+    flag in the 16 MiB array, and it runs and matches the workspace entry point; n = 49152 (the
+    next multiple of 8) is refused before any launch."""
+    from paper_1606_09402_gb300 import _lib
+    lib = _lib.load()
+    import paper_1606_09402_gb300 as qb
+
+    rng = np.random.default_rng(11)
+    m, w = 128, 64
+    for n, ok in [(49144, True), (49152, False)]:
+        A = torch.tensor(rng.standard_normal((m, n)), dtype=torch.float32).to(torch.bfloat16).cuda()
+        V = torch.tensor(rng.standard_normal((n, w)), dtype=torch.float32).cuda()
+        rc, Y = _call_noalloc(lib, qb, A, V)
+        if not ok:
+            assert rc == -5, (n, rc)   # QB_ERR_WORKSPACE
+            continue
+        assert rc == 0, (n, lib.qb_status_str(rc))
+        ref = qb.qb_apass_sketch(A, V).double().cpu().numpy()
+        scale = (np.abs(A.double().cpu().numpy()) @
+                 np.abs(V.to(torch.bfloat16).double().cpu().numpy())) + 1e-30
+        assert np.max(np.abs(Y.double().cpu().numpy() - ref) / scale) < 1e-5
