@@ -250,6 +250,28 @@ int32_t qb_fixed_rank_bwd(const qb_dense* A, int64_t k, uint64_t seed, int32_t p
                           void* ws, size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------------------------
+ * SVD from a QB factorisation (Sect. 2, the approximate SVD A ~ Q B = (Q U~) S~ V~^T): the SVD of
+ * the small k x n B, B = U~ S~ V~^T, then U = Q U~.  The first columns of U, V and the leading
+ * entries of S approximate A's singular triplets; with randQB_FP at P = 0 (Algorithm 3, one
+ * sweep over A for G and H) this is the single-pass SVD of Sect. 5.3.
+ *   Q: m x k column-major (ldq >= m), B: k x n row-major (ldb >= n), both float64 (prec
+ *   QB_PREC_FP64) or float32 (QB_PREC_MIXED): the outputs of qb_*_dense / qb_*_csr.
+ *   S: k doubles (device), descending, S[j] = sqrt(lambda_j) of W = B B^T (float64).
+ *   U: m x k column-major (ldu), V: n x k column-major (ldv), in Q's type; either may be NULL.
+ * Method: W = B B^T (float64 sums; float32 B with exact products in float32-pair sums), cyclic
+ * Jacobi eigendecomposition of W in float64 (one cooperative launch, bounded barrier waits), V =
+ * B^T U~ S~^-1 (zero columns where S~ = 0).  Singular values are accurate to about
+ * u (s_1 / s_j)^2 relative (W squares the condition number).  1 <= k <= min(m, n, 4096).
+ * Workspace: qb_svd_workspace(m, n, k, prec) bytes.  Returns QB_OK, QB_NOT_CONVERGED (40 Jacobi
+ * sweeps did not settle; S, U, V hold the last iterate), QB_ERR_TIMEOUT or another error; *sweeps
+ * (nullable, host) receives the sweeps run.  Synchronises the stream.
+ * ------------------------------------------------------------------------------------------- */
+size_t qb_svd_workspace(int64_t m, int64_t n, int64_t k, int32_t prec);
+int32_t qb_svd_from_qb(int64_t m, int64_t n, int64_t k, int32_t prec, const void* Q, int64_t ldq,
+                       const void* B, int64_t ldb, double* S, void* U, int64_t ldu, void* V,
+                       int64_t ldv, void* ws, size_t ws_bytes, int32_t* sweeps, void* stream);
+
+/* ---------------------------------------------------------------------------------------------
  * Allocation-free sketch pass (no counterpart in the paper; a deployment convenience).
  * Y (m x w, column-major, float32, ldy) = A_hi V, V float32 column-major n x w (ldv), A a
  * bf16 or bf16x2 dense A with ld % 8 == 0 and a 16-byte aligned base, m, n >= 128: the same

@@ -18,7 +18,8 @@ from . import _lib
 
 __all__ = ["qb_ei_dense", "qb_fp_dense", "qb_ei_csr", "qb_fp_csr", "qb_omega",
            "quantize_bf16x2", "qb_apass_sketch", "qb_apass_trans", "qb_fixed_rank_fwd",
-           "qb_fixed_rank_bwd", "QBFixedRank", "qb_ei_batched", "QBError", "QBInfo",
+           "qb_fixed_rank_bwd", "QBFixedRank", "qb_ei_batched", "qb_svd_from_qb", "QBError",
+           "QBInfo",
            "launch_count", "status_str"]
 
 
@@ -416,6 +417,40 @@ def qb_ei_batched(As, tols, seed=0, rank_cap=None, relative=True, row_by_row=Tru
         q, b = outs[t]
         res.append((q[:k].T, b[:k], info))
     return res
+
+
+def qb_svd_from_qb(Q, B, want_u=True, want_v=True, stream=None):
+    """SVD from a QB factorisation: (U, S, V, sweeps) with A ~ Q B = U diag(S) V^T, U = Q U~
+    (m x k), V (n x k), S descending (float64).  Q, B as returned by the qb_* calls (float64 or
+    float32, Q an m x k view of column-major storage, B k x n row-major)."""
+    torch = _torch()
+    lib = _lib.load()
+    _check_dev(Q, B)
+    m, k = Q.shape
+    k2, n = B.shape
+    assert k == k2 and Q.dtype == B.dtype
+    f64 = Q.dtype == torch.float64
+    prec = _lib.QB_PREC_FP64 if f64 else _lib.QB_PREC_MIXED
+    Qc = Q if (Q.stride(0) == 1 and Q.stride(1) >= m) else Q.T.contiguous().T   # column-major
+    Bc = B if B.stride(1) == 1 else B.contiguous()
+    S = torch.empty(k, dtype=torch.float64, device=Q.device)
+    Ut = torch.empty(k, m, dtype=Q.dtype, device=Q.device) if want_u else None
+    Vt = torch.empty(k, n, dtype=Q.dtype, device=Q.device) if want_v else None
+    wsb = lib.qb_svd_workspace(m, n, k, prec)
+    if wsb == 0:
+        raise QBError(_lib.QB_ERR_INVALID_ARG, "qb_svd_workspace")
+    ws = torch.empty(wsb, dtype=torch.uint8, device=Q.device)
+    sweeps = C.c_int32(0)
+    with torch.cuda.device(Q.device):
+        rc = lib.qb_svd_from_qb(m, n, k, prec, C.c_void_p(Qc.data_ptr()), Qc.stride(1),
+                                C.c_void_p(Bc.data_ptr()), Bc.stride(0), C.c_void_p(S.data_ptr()),
+                                C.c_void_p(Ut.data_ptr()) if want_u else None, m,
+                                C.c_void_p(Vt.data_ptr()) if want_v else None, n,
+                                C.c_void_p(ws.data_ptr()), wsb, C.byref(sweeps),
+                                _stream_ptr(stream))
+    if rc < 0:
+        raise QBError(rc, "qb_svd_from_qb")
+    return (Ut.T if want_u else None), S, (Vt.T if want_v else None), int(sweeps.value)
 
 
 def _autograd_function():

@@ -80,27 +80,30 @@ def dense_low_rank(m: int, n: int, r: int, seed: int) -> np.ndarray:
     return dense_from_spectrum(m, n, sigma, seed)
 
 
-def dense_from_spectrum_torch(m: int, n: int, sigma, seed: int, device, dtype=None):
+def dense_from_spectrum_torch(m: int, n: int, sigma, seed: int, device, dtype=None,
+                              work_dtype=None):
     """Large-scale variant of ``dense_from_spectrum`` drawn on a torch device.
 
-    U and V come from the QR of seeded N(0,1) matrices computed in float32 on ``device`` (their
-    orthonormality is ~1e-6, which perturbs the singular values relatively by the same amount);
-    the product is formed in float32 and returned as ``dtype`` (default float64), row-major.
+    U and V come from the QR of seeded N(0,1) matrices computed in ``work_dtype`` (default
+    float32: orthonormality ~1e-6, which perturbs the singular values relatively by the same
+    amount; float64 keeps them to ~1e-15) on ``device``; the product is formed in the same type
+    and returned as ``dtype`` (default float64), row-major.
     """
     import torch
 
     dtype = dtype or torch.float64
+    wd = work_dtype or torch.float32
     r = len(sigma)
     gen = torch.Generator(device=device)
     gen.manual_seed(int(seed))
     prev = torch.backends.cuda.matmul.allow_tf32
     torch.backends.cuda.matmul.allow_tf32 = False
     try:
-        s = torch.as_tensor(np.asarray(sigma, dtype=np.float32), device=device)
-        gu = torch.randn(m, r, generator=gen, device=device, dtype=torch.float32)
+        s = torch.as_tensor(np.asarray(sigma, dtype=np.float64), device=device).to(wd)
+        gu = torch.randn(m, r, generator=gen, device=device, dtype=torch.float32).to(wd)
         u, _ = torch.linalg.qr(gu)
         del gu
-        gv = torch.randn(n, r, generator=gen, device=device, dtype=torch.float32)
+        gv = torch.randn(n, r, generator=gen, device=device, dtype=torch.float32).to(wd)
         v, _ = torch.linalg.qr(gv)
         del gv
         a = torch.empty(m, n, device=device, dtype=dtype)
