@@ -310,6 +310,35 @@ def run_sparse(torch, qb, dev, stream):
     ei = out["ei"]
     out["a_bytes_per_pass"] = a_bytes
     out["ei_pass_gbs"] = ei["passes"] * a_bytes / (ei["pass_ms"] * 1e-3) / 1e9
+    # the same matrix as COO triplets sorted by row (Sect. 5.1's coordinate format)
+    lens = np.diff(csr.rowptr.astype(np.int64))
+    row = torch.tensor(np.repeat(np.arange(csr.m, dtype=np.int32), lens), device=dev)
+    for name, f in (("coo_ei", qb.qb_ei_coo), ("coo_fp", qb.qb_fp_coo)):
+        f(row, ci, v, shape, 0.5, 32, **kw)                   # warm-up
+        torch.cuda.synchronize()
+        t = event_time(torch, lambda: f(row, ci, v, shape, 0.5, 32, **kw), 3, stream)
+        _, _, info = f(row, ci, v, shape, 0.5, 32, flags=2, **kw)
+        ph = qb.profile_last()
+        out[name] = {"time_to_tol_s": t, "rank": info.rank, "passes": info.passes,
+                     "status": info.status, "pass_ms": ph["sketch"] + ph["trans"]}
+    out["coo_ei"]["pass_gbs"] = (out["coo_ei"]["passes"] * (12.0 * out["nnz"]) /
+                                 (out["coo_ei"]["pass_ms"] * 1e-3) / 1e9)
+    del row
+    # the merged-duplicates reading of the generator: converges at tol 0.5 well under the cap
+    mc = synth.csr_zipf(200000, 100000, 100.0, 1.1, seed=909, val_dtype=np.float32,
+                        merge_duplicates=True)
+    rpm = torch.tensor(mc.rowptr, device=dev)
+    cim = torch.tensor(mc.colind, device=dev)
+    vm = torch.tensor(mc.val, device=dev)
+    merged = {"nnz": int(cim.numel()), "note": "duplicate Zipf draws merged (summed values)"}
+    for name, f in (("ei", qb.qb_ei_csr), ("fp", qb.qb_fp_csr)):
+        f(rpm, cim, vm, shape, 0.5, 32, **kw)
+        torch.cuda.synchronize()
+        t = event_time(torch, lambda: f(rpm, cim, vm, shape, 0.5, 32, **kw), 3, stream)
+        _, _, info = f(rpm, cim, vm, shape, 0.5, 32, **kw)
+        merged[name] = {"time_to_tol_s": t, "rank": info.rank, "passes": info.passes,
+                        "status": info.status, "err_rel_est": info.err_est / info.normA2 ** 0.5}
+    out["merged_duplicates"] = merged
     return out
 
 

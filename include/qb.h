@@ -181,6 +181,29 @@ int32_t qb_fp_csr(const qb_csr* A, const qb_opts* opts, void* Q, int64_t ldq, vo
                   int64_t ldb, void* ws, size_t ws_bytes, qb_info* info, void* stream);
 
 /* ---------------------------------------------------------------------------------------------
+ * Sparse COO A (Sect. 5.1: a coordinate-format copy of the sparse matrix lets randQB_FP spread
+ * its work more evenly than CSR).  Triplets (row[e], col[e], val[e]), e < nnz, int32 zero-based
+ * indices, val of dtype QB_F64 or QB_F32; duplicates add up; any order is accepted and entries
+ * sorted by row are fastest.  The passes give every warp the same number of nonzeros whatever
+ * the row and column lengths; A^T products run on a column-sorted copy the call builds in its
+ * workspace.  Same semantics, outputs and statuses as the dense and CSR calls.
+ * ------------------------------------------------------------------------------------------- */
+typedef struct {
+    int64_t m, n, nnz;
+    const int32_t* row;
+    const int32_t* col;
+    int32_t dtype;
+    int32_t reserved;
+    const void* val;
+} qb_coo;
+
+size_t qb_coo_workspace(const qb_coo* A, const qb_opts* opts, int32_t algo);
+int32_t qb_ei_coo(const qb_coo* A, const qb_opts* opts, void* Q, int64_t ldq, void* B,
+                  int64_t ldb, void* ws, size_t ws_bytes, qb_info* info, void* stream);
+int32_t qb_fp_coo(const qb_coo* A, const qb_opts* opts, void* Q, int64_t ldq, void* B,
+                  int64_t ldb, void* ws, size_t ws_bytes, qb_info* info, void* stream);
+
+/* ---------------------------------------------------------------------------------------------
  * Single passes over dense A (the hot step of both algorithms, exposed for measurement and
  * verification).  Same kernels the drivers use; float64 A runs the float64 kernels, bf16 / bf16x2
  * A the tensor-core kernels (float32 V and outputs).

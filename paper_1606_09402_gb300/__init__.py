@@ -16,7 +16,8 @@ from dataclasses import dataclass
 
 from . import _lib
 
-__all__ = ["qb_ei_dense", "qb_fp_dense", "qb_ei_csr", "qb_fp_csr", "qb_omega",
+__all__ = ["qb_ei_dense", "qb_fp_dense", "qb_ei_csr", "qb_fp_csr", "qb_ei_coo", "qb_fp_coo",
+           "qb_omega",
            "quantize_bf16x2", "qb_apass_sketch", "qb_apass_trans", "qb_fixed_rank_fwd",
            "qb_fixed_rank_bwd", "QBFixedRank", "qb_ei_batched", "qb_svd_from_qb", "QBError",
            "QBInfo",
@@ -218,6 +219,53 @@ def qb_fp_csr(rowptr, colind, val, shape, tol, b, P=0, seed=0, relative=True, ra
     """randQB_FP on a CSR matrix."""
     return _csr_call(_lib.load().qb_fp_csr, "qb_fp_csr", rowptr, colind, val, shape, tol, b, P,
                      seed, relative, rank_cap, l_tilde, row_by_row, stream, workspace, flags)
+
+
+def _coo_call(fn, name, row, col, val, shape, tol, b, P, seed, relative, rank_cap, l_tilde,
+              row_by_row, stream, workspace, flags=0):
+    torch = _torch()
+    lib = _lib.load()
+    _check_dev(row, col, val)
+    assert row.dtype == torch.int32 and col.dtype == torch.int32
+    assert row.numel() == col.numel() == val.numel()
+    m, n = shape
+    prec = "fp64" if val.dtype == torch.float64 else "mixed"
+    s = _lib.qb_coo(m=m, n=n, nnz=val.numel(), row=row.data_ptr(), col=col.data_ptr(),
+                    dtype=_dtype_code(val), reserved=0, val=val.data_ptr())
+    o = _opts(tol, b, P, seed, relative, rank_cap, l_tilde, row_by_row, prec, flags)
+    algo = 1 if name.startswith("qb_fp") else 0
+    wsb = lib.qb_coo_workspace(C.byref(s), C.byref(o), algo)
+    if wsb == 0:
+        raise QBError(_lib.QB_ERR_INVALID_ARG, name + " workspace query")
+    cap = min(m, n) if not rank_cap or rank_cap <= 0 else min(m, n, int(rank_cap))
+    Qt, B = _alloc_out(m, n, cap, prec, val.device, None)
+    ws = workspace if workspace is not None and workspace.numel() >= wsb else \
+        torch.empty(wsb, dtype=torch.uint8, device=val.device)
+    inf = _lib.qb_info()
+    with torch.cuda.device(val.device):
+        rc = fn(C.byref(s), C.byref(o), C.c_void_p(Qt.data_ptr()), Qt.stride(0),
+                C.c_void_p(B.data_ptr()), B.stride(0), C.c_void_p(ws.data_ptr()), ws.numel(),
+                C.byref(inf), _stream_ptr(stream))
+    if rc < 0:
+        raise QBError(rc, name)
+    info = _info(rc, inf)
+    k = info.rank
+    return Qt[:k].T, B[:k], info
+
+
+def qb_ei_coo(row, col, val, shape, tol, b, P=0, seed=0, relative=True, rank_cap=None,
+              row_by_row=True, stream=None, workspace=None, flags=0):
+    """randQB_EI on a COO matrix (int32 row / col indices, any order, sorted by row fastest;
+    float64 values -> fp64 path, float32 -> mixed)."""
+    return _coo_call(_lib.load().qb_ei_coo, "qb_ei_coo", row, col, val, shape, tol, b, P, seed,
+                     relative, rank_cap, None, row_by_row, stream, workspace, flags)
+
+
+def qb_fp_coo(row, col, val, shape, tol, b, P=0, seed=0, relative=True, rank_cap=None,
+              l_tilde=None, row_by_row=True, stream=None, workspace=None, flags=0):
+    """randQB_FP on a COO matrix."""
+    return _coo_call(_lib.load().qb_fp_coo, "qb_fp_coo", row, col, val, shape, tol, b, P, seed,
+                     relative, rank_cap, l_tilde, row_by_row, stream, workspace, flags)
 
 
 def qb_omega(n, col0, w, seed, dtype=None, device="cuda", stream=None):

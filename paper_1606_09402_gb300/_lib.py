@@ -44,6 +44,12 @@ class qb_csr(C.Structure):
                 ("val", C.c_void_p)]
 
 
+class qb_coo(C.Structure):
+    _fields_ = [("m", C.c_int64), ("n", C.c_int64), ("nnz", C.c_int64), ("row", C.c_void_p),
+                ("col", C.c_void_p), ("dtype", C.c_int32), ("reserved", C.c_int32),
+                ("val", C.c_void_p)]
+
+
 class qb_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("relative", C.c_int32), ("b", C.c_int32), ("P", C.c_int32),
                 ("row_by_row", C.c_int32), ("seed", C.c_uint64), ("rank_cap", C.c_int64),
@@ -76,6 +82,11 @@ _SIG = {
     "qb_ei_csr": (C.c_int32, [C.POINTER(qb_csr), C.POINTER(qb_opts), _P, _I64, _P, _I64, _P,
                               C.c_size_t, C.POINTER(qb_info), _P]),
     "qb_fp_csr": (C.c_int32, [C.POINTER(qb_csr), C.POINTER(qb_opts), _P, _I64, _P, _I64, _P,
+                              C.c_size_t, C.POINTER(qb_info), _P]),
+    "qb_coo_workspace": (C.c_size_t, [C.POINTER(qb_coo), C.POINTER(qb_opts), C.c_int32]),
+    "qb_ei_coo": (C.c_int32, [C.POINTER(qb_coo), C.POINTER(qb_opts), _P, _I64, _P, _I64, _P,
+                              C.c_size_t, C.POINTER(qb_info), _P]),
+    "qb_fp_coo": (C.c_int32, [C.POINTER(qb_coo), C.POINTER(qb_opts), _P, _I64, _P, _I64, _P,
                               C.c_size_t, C.POINTER(qb_info), _P]),
     "qb_omega": (C.c_int32, [_I64, _I64, _I64, C.c_uint64, C.c_int32, _P, _I64, _P]),
     "qb_apass_workspace": (C.c_size_t, [C.POINTER(qb_dense), _I64]),

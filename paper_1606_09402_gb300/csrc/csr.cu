@@ -290,6 +290,114 @@ void spmm_t(cudaStream_t st, const int32_t* ptr, const int32_t* idx, const T* va
     }
 }
 
+// ---------------------------------------------------------------- COO (coordinate) passes
+// Y_rm (rows x 32 NQ) += A X_rm for A given as nnz (key, idx, val) triplets: Y(key) += val X(idx).
+// Nonzero-balanced: warp w takes the COO_SEG triplets [w COO_SEG, (w + 1) COO_SEG) in storage
+// order whatever rows they belong to, sums val X(idx, :) in registers while the key stays the
+// same and adds the sum into row `key` of the zeroed Y with atomics when the key changes and at the
+// chunk's end.  Correct for any order; with triplets sorted by key most rows lie inside one chunk
+// (a single addition into zero, so their sums have a fixed order), and a row spread over two
+// chunks gets two additions (commutative, also exact in order); only rows over three or more
+// chunks sum in a run-dependent order.
+constexpr int COO_SEG = 256;
+
+template <class T, int NQ>
+__global__ void __launch_bounds__(256)
+k_coo_spmm(const int32_t* __restrict__ key, const int32_t* __restrict__ idx,
+           const T* __restrict__ val, int64_t nnz, const T* __restrict__ X, int64_t ldx, int wc,
+           T* __restrict__ Y, int64_t ldy) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    const T* xl = X + lane * NQ;
+    for (int64_t w = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; w * COO_SEG < nnz;
+         w += nw) {
+        const int64_t b = w * COO_SEG;
+        const int64_t e = b + COO_SEG < nnz ? b + COO_SEG : nnz;
+        T acc[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) acc[q] = T(0);
+        int32_t cur = -1;
+        auto flush = [&]() {
+            if (cur < 0) return;
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const int j = lane * NQ + q;
+                if (j < wc) atomicAdd(Y + int64_t(cur) * ldy + j, acc[q]);
+                acc[q] = T(0);
+            }
+        };
+        for (int64_t p0 = b; p0 < e; p0 += 32) {
+            const int64_t p = p0 + lane;
+            int32_t kk = 0, c = 0;
+            T v = T(0);
+            if (p < e) { kk = key[p]; c = idx[p]; v = val[p]; }
+            const int cnt = int(e - p0 < 32 ? e - p0 : 32);
+            for (int t = 0; t < cnt; ++t) {
+                const int32_t kt = __shfl_sync(0xffffffffu, kk, t);
+                const int32_t ct = __shfl_sync(0xffffffffu, c, t);
+                const T vt = __shfl_sync(0xffffffffu, v, t);
+                if (kt != cur) {
+                    flush();
+                    cur = kt;
+                }
+                T x[NQ];
+                Vec<T, NQ>::ld(xl + int64_t(ct) * ldx, x);
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) acc[q] = fma(vt, x[q], acc[q]);
+            }
+        }
+        flush();
+    }
+}
+
+// Column-sorted copy of COO triplets: position = cursor[col]++ (counting sort by column).
+template <class T>
+__global__ void k_coo_scatter(const int32_t* __restrict__ row, const int32_t* __restrict__ col,
+                              const T* __restrict__ val, int64_t nnz, int32_t* __restrict__ cursor,
+                              int32_t* __restrict__ ocol, int32_t* __restrict__ orow,
+                              T* __restrict__ oval) {
+    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < nnz;
+         e += int64_t(gridDim.x) * blockDim.x) {
+        const int32_t c = col[e];
+        const int32_t pos = atomicAdd(cursor + c, 1);
+        ocol[pos] = c;
+        orow[pos] = row[e];
+        oval[pos] = val[e];
+    }
+}
+
+template <class T>
+void coo_spmm_t(cudaStream_t st, const int32_t* key, const int32_t* idx, const T* val, int64_t nnz,
+                int64_t rows, int64_t cols, const T* X, int64_t ldx, int64_t w, T* Y, int64_t ldy,
+                T* stage) {
+    T* Xr = stage;
+    T* Yr = stage + cols * WCH;
+    const int64_t chunks = cdiv(std::max<int64_t>(nnz, 1), COO_SEG);
+    const unsigned g = unsigned(std::max<int64_t>(1, std::min<int64_t>(cdiv(chunks, 8), 1 << 20)));
+    for (int64_t c0 = 0; c0 < w; c0 += WCH) {
+        const int wc = int(std::min<int64_t>(WCH, w - c0));
+        const int nq = wc <= 32 ? 1 : wc <= 64 ? 2 : 4;
+        const int wp = 32 * nq;
+        dim3 blk(32, 8);
+        k_cm_to_rm<T><<<dim3(unsigned(cdiv(cols, 32)), unsigned(cdiv(wc, 32))), blk, 0, st>>>(
+            X, ldx, cols, c0, wc, Xr, wp);
+        QB_LAUNCHED();
+        QB_CUDA(cudaMemsetAsync(Yr, 0, sizeof(T) * size_t(rows) * size_t(wp), st));
+        if (nnz > 0) {
+            if (nq == 1)
+                k_coo_spmm<T, 1><<<g, 256, 0, st>>>(key, idx, val, nnz, Xr, wp, wc, Yr, wp);
+            else if (nq == 2)
+                k_coo_spmm<T, 2><<<g, 256, 0, st>>>(key, idx, val, nnz, Xr, wp, wc, Yr, wp);
+            else
+                k_coo_spmm<T, 4><<<g, 256, 0, st>>>(key, idx, val, nnz, Xr, wp, wc, Yr, wp);
+            QB_LAUNCHED();
+        }
+        k_rm_to_cm<T><<<dim3(unsigned(cdiv(rows, 32)), unsigned(cdiv(wc, 32))), blk, 0, st>>>(
+            Yr, wp, rows, wc, Y, ldy, c0);
+        QB_LAUNCHED();
+    }
+}
+
 }  // namespace
 
 size_t csr_stage_bytes(int64_t m, int64_t n, bool f64) {
@@ -351,6 +459,50 @@ void csr_spmm(cudaStream_t st, bool f64, const int32_t* ptr, const int32_t* idx,
         spmm_t<float>(st, ptr, idx, reinterpret_cast<const float*>(val), rows, cols, segs,
                       reinterpret_cast<const float*>(X), ldx, w, reinterpret_cast<float*>(Y), ldy,
                       reinterpret_cast<float*>(stage));
+}
+
+}  // namespace qb
+
+namespace qb {
+
+void coo_by_column(cudaStream_t st, const CooDev& A, int32_t* ocol, int32_t* orow, void* oval,
+                   int32_t* colptr, int32_t* cnt) {
+    QB_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * size_t(A.n), st));
+    const unsigned g = unsigned(std::max<int64_t>(1, std::min<int64_t>(cdiv(A.nnz, 256), 4096)));
+    if (A.nnz > 0) {
+        k_hist<<<g, 256, 0, st>>>(A.col, A.nnz, cnt);
+        QB_LAUNCHED();
+    }
+    int32_t* cursor = cnt + A.n;
+    k_scan<<<1, 1024, 0, st>>>(cnt, A.n, colptr, cursor);
+    QB_LAUNCHED();
+    if (A.nnz > 0) {
+        if (A.f64)
+            k_coo_scatter<double><<<g, 256, 0, st>>>(A.row, A.col,
+                                                    reinterpret_cast<const double*>(A.val), A.nnz,
+                                                    cursor, ocol, orow,
+                                                    reinterpret_cast<double*>(oval));
+        else
+            k_coo_scatter<float><<<g, 256, 0, st>>>(A.row, A.col,
+                                                   reinterpret_cast<const float*>(A.val), A.nnz,
+                                                   cursor, ocol, orow,
+                                                   reinterpret_cast<float*>(oval));
+        QB_LAUNCHED();
+    }
+}
+
+void coo_spmm(cudaStream_t st, bool f64, const int32_t* key, const int32_t* idx, const void* val,
+              int64_t nnz, int64_t rows, int64_t cols, const void* X, int64_t ldx, int64_t w,
+              void* Y, int64_t ldy, void* stage) {
+    if (rows <= 0 || w <= 0) return;
+    if (f64)
+        coo_spmm_t<double>(st, key, idx, reinterpret_cast<const double*>(val), nnz, rows, cols,
+                           reinterpret_cast<const double*>(X), ldx, w,
+                           reinterpret_cast<double*>(Y), ldy, reinterpret_cast<double*>(stage));
+    else
+        coo_spmm_t<float>(st, key, idx, reinterpret_cast<const float*>(val), nnz, rows, cols,
+                          reinterpret_cast<const float*>(X), ldx, w, reinterpret_cast<float*>(Y),
+                          ldy, reinterpret_cast<float*>(stage));
 }
 
 }  // namespace qb

@@ -574,6 +574,72 @@ struct CsrOp : AOp {
     }
 };
 
+// Sparse A as COO triplets (Sect. 5.1: COO instead of CSR).  A X runs the nonzero-balanced
+// segmented kernel on the caller's triplets (fastest sorted by row); A^T X on a column-sorted copy
+// built once per call.  No row pointer is needed and no row or column length sets the load of a
+// warp: every warp takes 256 nonzeros.
+struct CooOp : AOp {
+    qb_coo s;
+    int32_t* ocol = nullptr;
+    int32_t* orow = nullptr;
+    void* oval = nullptr;
+    int32_t* colptr = nullptr;
+    int32_t* cnt = nullptr;
+    void* stage = nullptr;
+    bool use_tc = false;
+    void* tc_scr = nullptr;
+    size_t tc_bytes = 0;
+    explicit CooOp(const qb_coo& ss) : s(ss) { m = ss.m; n = ss.n; }
+    bool f64v() const { return s.dtype == QB_F64; }
+    void reserve(Arena& ar, const Ctx& c, int64_t w) override {
+        use_tc = !c.f64 && !c.simt_apass && m >= 128 && n >= 128 &&
+                 (ar.base == nullptr || tc_available());
+        if (use_tc) {
+            tc_bytes = tc_scratch_bytes(m, n, w);
+            tc_scr = ar.get<char>(int64_t(tc_bytes));
+        }
+        ocol = ar.get<int32_t>(s.nnz);
+        orow = ar.get<int32_t>(s.nnz);
+        oval = ar.get<char>(s.nnz * (f64v() ? 8 : 4));
+        colptr = ar.get<int32_t>(n + 1);
+        cnt = ar.get<int32_t>(2 * std::max<int64_t>(n, 1));
+        stage = ar.get<char>(int64_t(csr_stage_bytes(m, n, f64v())));
+    }
+    bool tc_scratch(void** p, size_t* b) override {
+        if (!use_tc) return false;
+        *p = tc_scr;
+        *b = tc_bytes;
+        return true;
+    }
+    bool timed_out(Ctx& c) override {
+        if (!use_tc) return false;
+        int h = 0;
+        QB_CUDA(cudaMemcpyAsync(&h, tc_error_flag(tc_scr), sizeof h, cudaMemcpyDeviceToHost, c.st));
+        QB_CUDA(cudaStreamSynchronize(c.st));
+        return h != 0;
+    }
+    void prepare(Ctx& c) override {
+        if (use_tc) QB_CUDA(cudaMemsetAsync(tc_error_flag(tc_scr), 0, 256, c.st));
+        CooDev A{m, n, s.nnz, s.row, s.col, s.val, f64v()};
+        coo_by_column(c.st, A, ocol, orow, oval, colptr, cnt);
+    }
+    void apply(Ctx& c, const void* X, int64_t ldx, int64_t w, void* Y, int64_t ldy, int) override {
+        Ctx::Scope sc(c, PH_SKETCH);
+        coo_spmm(c.st, f64v(), s.row, s.col, s.val, s.nnz, m, n, X, ldx, w, Y, ldy, stage);
+    }
+    void apply_t(Ctx& c, const void* X, int64_t ldx, int64_t w, void* Y, int64_t ldy, int) override {
+        Ctx::Scope sc(c, PH_TRANS);
+        coo_spmm(c.st, f64v(), ocol, orow, oval, s.nnz, n, m, X, ldx, w, Y, ldy, stage);
+    }
+    double norm2(Ctx& c) override {
+        vec_norm2(c.st, s.val, f64v(), s.nnz, c.part, c.state + 4, c.flags);
+        double h = 0;
+        QB_CUDA(cudaMemcpyAsync(&h, c.state + 4, sizeof h, cudaMemcpyDeviceToHost, c.st));
+        QB_CUDA(cudaStreamSynchronize(c.st));
+        return h;
+    }
+};
+
 // ------------------------------------------------------------------------------------ shared setup
 struct Plan {
     int64_t m, n, cap, lt;
@@ -1047,6 +1113,15 @@ bool valid_csr(const qb_csr* A, const qb_opts* o) {
     return true;
 }
 
+bool valid_coo(const qb_coo* A, const qb_opts* o) {
+    if (!A || !o || A->m < 0 || A->n < 0 || A->nnz < 0 || A->nnz > INT32_MAX) return false;
+    if (A->nnz > 0 && (!A->row || !A->col || !A->val)) return false;
+    if (A->dtype != QB_F64 && A->dtype != QB_F32) return false;
+    if (o->prec == QB_PREC_FP64 && A->dtype != QB_F64) return false;
+    if (o->prec == QB_PREC_MIXED && A->dtype != QB_F32) return false;
+    return true;
+}
+
 }  // namespace
 
 }  // namespace qb
@@ -1136,6 +1211,35 @@ int32_t qb_fp_csr(const qb_csr* A, const qb_opts* opts, void* Q, int64_t ldq, vo
                   int64_t ldb, void* ws, size_t ws_bytes, qb_info* info, void* stream) {
     if (!valid_csr(A, opts)) return QB_ERR_INVALID_ARG;
     CsrOp op(*A);
+    return guarded([&] {
+        return run_common(op, opts, true, Q, ldq, B, ldb, ws, ws_bytes, info, stream, nullptr);
+    });
+}
+
+size_t qb_coo_workspace(const qb_coo* A, const qb_opts* opts, int32_t algo) {
+    if (!valid_coo(A, opts) || !valid_opts(opts) || (algo != 0 && algo != 1)) return 0;
+    size_t bytes = 0;
+    CooOp op(*A);
+    int32_t rc = guarded([&] {
+        return run_common(op, opts, algo == 1, nullptr, 0, nullptr, 0, nullptr, 0, nullptr,
+                          nullptr, &bytes);
+    });
+    return rc == QB_OK ? bytes : 0;
+}
+
+int32_t qb_ei_coo(const qb_coo* A, const qb_opts* opts, void* Q, int64_t ldq, void* B,
+                  int64_t ldb, void* ws, size_t ws_bytes, qb_info* info, void* stream) {
+    if (!valid_coo(A, opts)) return QB_ERR_INVALID_ARG;
+    CooOp op(*A);
+    return guarded([&] {
+        return run_common(op, opts, false, Q, ldq, B, ldb, ws, ws_bytes, info, stream, nullptr);
+    });
+}
+
+int32_t qb_fp_coo(const qb_coo* A, const qb_opts* opts, void* Q, int64_t ldq, void* B,
+                  int64_t ldb, void* ws, size_t ws_bytes, qb_info* info, void* stream) {
+    if (!valid_coo(A, opts)) return QB_ERR_INVALID_ARG;
+    CooOp op(*A);
     return guarded([&] {
         return run_common(op, opts, true, Q, ldq, B, ldb, ws, ws_bytes, info, stream, nullptr);
     });

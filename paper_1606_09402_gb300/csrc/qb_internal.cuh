@@ -255,4 +255,22 @@ void csr_spmm(cudaStream_t st, bool f64, const int32_t* ptr, const int32_t* idx,
               int64_t rows, int64_t cols, const CsrSegs* segs, const void* X, int64_t ldx,
               int64_t w, void* Y, int64_t ldy, void* stage);
 
+// ------------------------------------------------------------------------------------ COO
+struct CooDev {
+    int64_t m, n, nnz;
+    const int32_t* row;
+    const int32_t* col;
+    const void* val;
+    bool f64;
+};
+// Column-sorted copy of COO triplets (counting sort by column; order inside a column is not
+// fixed): ocol, orow, oval (nnz each); colptr n + 1 int32; cnt: 2 n int32 scratch.
+void coo_by_column(cudaStream_t st, const CooDev& A, int32_t* ocol, int32_t* orow, void* oval,
+                   int32_t* colptr, int32_t* cnt);
+// Y (rows x w, col-major) = S X for S given by nnz triplets (key = row of S, idx = column of S,
+// val), any order (sorted by key is fastest); X (cols x w, col-major); stage as for csr_spmm.
+void coo_spmm(cudaStream_t st, bool f64, const int32_t* key, const int32_t* idx, const void* val,
+              int64_t nnz, int64_t rows, int64_t cols, const void* X, int64_t ldx, int64_t w,
+              void* Y, int64_t ldy, void* stage);
+
 }  // namespace qb

@@ -40,7 +40,7 @@ def _check_svd(Q, B, U, S, V, tol_rec=1e-10):
     lead = int(np.sum(s >= 1e-3 * s[0]))
     assert np.max(np.abs(Vh[:, :lead].T @ Vh[:, :lead] - np.eye(lead))) <= 1e-9
     # the leading singular vectors match the oracle's up to sign where the gaps are wide
-    gap = np.abs(np.diff(sr[: lead + 1])) / sr[0]
+    gap = np.append(np.abs(np.diff(sr[: lead + 1])) / sr[0], np.inf)   # gap below s_j
     for j in range(min(lead, 10)):
         if gap[j] > 1e-3 and (j == 0 or gap[j - 1] > 1e-3):
             c = abs(float(Uh[:, j] @ Ur[:, j]))
