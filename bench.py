@@ -53,9 +53,13 @@ def parse():
     ap.add_argument("--quick", action="store_true", help="smaller workload (smoke only)")
     ap.add_argument("--steps-only", action="store_true",
                     help="time the mixed randQB_FP steps only (no side measurements); for profiling")
-    ap.add_argument("--profile-small", nargs="?", const="fp", default=None, choices=["fp", "ei"],
-                    help="two mixed randQB_FP (or randQB_EI) factorisations of a 16384 x 8192 "
-                         "matrix (the small case for ncu section captures); prints the rank")
+    ap.add_argument("--profile-small", nargs="?", const="fp", default=None,
+                    choices=["fp", "ei", "csr", "coo", "batched", "adjoint", "svd"],
+                    help="small cases for ncu section captures: two mixed randQB_FP (fp) or "
+                         "randQB_EI (ei) factorisations of a 16384 x 8192 matrix; the sparse "
+                         "passes on a 50000 x 25000 Zipf CSR / COO matrix (csr, coo); a batch of "
+                         "32 matrices (batched); the 4096 x 4096 fixed-rank map and adjoint "
+                         "(adjoint); the SVD from a rank-1024 QB (svd)")
     return ap.parse_args()
 
 
@@ -641,10 +645,67 @@ def run_profile_small(alg):
         print("rank", info.rank, "status", info.status, flush=True)
 
 
+def run_profile_other(kind):
+    """Small cases of the other kernel families for ncu captures (each exits 0 on success)."""
+    import numpy as np
+    import torch
+
+    import paper_1606_09402_gb300 as qb
+    import synth
+    dev = "cuda"
+    if kind in ("csr", "coo"):
+        # 50000 x 25000, Poisson(100) rows, Zipf(1.1) columns: CSR 40 MB (> L2 with X staging)
+        c = synth.csr_zipf(50000, 25000, 100.0, 1.1, seed=909, val_dtype=np.float32)
+        rp, ci, v = (torch.tensor(c.rowptr, device=dev), torch.tensor(c.colind, device=dev),
+                     torch.tensor(c.val, device=dev))
+        for _ in range(2):
+            if kind == "csr":
+                _, _, info = qb.qb_ei_csr(rp, ci, v, (c.m, c.n), 0.5, 32, P=1, seed=1, rank_cap=128)
+            else:
+                row = torch.tensor(np.repeat(np.arange(c.m, dtype=np.int32),
+                                             np.diff(c.rowptr.astype(np.int64))), device=dev)
+                _, _, info = qb.qb_ei_coo(row, ci, v, (c.m, c.n), 0.5, 32, P=1, seed=1,
+                                          rank_cap=128)
+            torch.cuda.synchronize()
+            print("rank", info.rank, "status", info.status, flush=True)
+    elif kind == "batched":
+        specs = synth.batched_specs(32, 1606)
+        mats = [synth.dense_from_spectrum_torch(s.m, s.n, synth.sigma_pow(min(s.m, s.n, 512), 2.0,
+                                                                          s.scale),
+                                                s.seed, dev, dtype=torch.float32) for s in specs]
+        for _ in range(2):
+            res = qb.qb_ei_batched(mats, [s.tol for s in specs], seed=9402)
+            torch.cuda.synchronize()
+            print("ranks", [r[2].rank for r in res[:8]], flush=True)
+    elif kind == "adjoint":
+        m = n = 4096
+        k = 256
+        A = synth.dense_from_spectrum_torch(m, n, 1.0 / np.arange(1, n + 1), 1606, dev,
+                                            dtype=torch.float32).to(torch.bfloat16)
+        GQ, GB = synth.cotangents(m, n, k, seed=5)
+        GQ = torch.tensor(GQ, dtype=torch.float32, device=dev)
+        GB = torch.tensor(GB, dtype=torch.float32, device=dev)
+        for _ in range(2):
+            Q, B, R = qb.qb_fixed_rank_fwd(A, k, 9)
+            GA = qb.qb_fixed_rank_bwd(A, k, 9, Q, R, GQ, GB)
+            torch.cuda.synchronize()
+            print("grad norm", float(GA.double().norm()), flush=True)
+    elif kind == "svd":
+        A = synth.dense_from_spectrum_torch(8192, 4096, synth.sigma_exp(4096, 300.0), 7, dev)
+        Q, B, info = qb.qb_fp_dense(A, 0.0, 64, P=1, seed=2, rank_cap=1024)
+        for _ in range(2):
+            _, S, _, sweeps = qb.qb_svd_from_qb(Q, B)
+            torch.cuda.synchronize()
+            print("sweeps", sweeps, "s1", float(S[0]), flush=True)
+
+
 def main():
     args = parse()
-    if args.profile_small:
+    if args.profile_small in ("fp", "ei"):
         run_profile_small(args.profile_small)
+        return
+    if args.profile_small:
+        run_profile_other(args.profile_small)
         return
     ws, rank, local = dist_env()
     if ws > 1:

@@ -183,8 +183,8 @@ int32_t qb_fp_csr(const qb_csr* A, const qb_opts* opts, void* Q, int64_t ldq, vo
 /* ---------------------------------------------------------------------------------------------
  * Sparse COO A (Sect. 5.1: a coordinate-format copy of the sparse matrix lets randQB_FP spread
  * its work more evenly than CSR).  Triplets (row[e], col[e], val[e]), e < nnz, int32 zero-based
- * indices, val of dtype QB_F64 or QB_F32; duplicates add up; any order is accepted and entries
- * sorted by row are fastest.  The passes give every warp the same number of nonzeros whatever
+ * indices, val of dtype QB_F64 or QB_F32; each (row, col) at most once (||A||_F^2 is the sum of
+ * val^2); any order is accepted and entries sorted by row are fastest.  The passes give every warp the same number of nonzeros whatever
  * the row and column lengths; A^T products run on a column-sorted copy the call builds in its
  * workspace.  Same semantics, outputs and statuses as the dense and CSR calls.
  * ------------------------------------------------------------------------------------------- */

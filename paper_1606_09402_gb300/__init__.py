@@ -255,8 +255,8 @@ def _coo_call(fn, name, row, col, val, shape, tol, b, P, seed, relative, rank_ca
 
 def qb_ei_coo(row, col, val, shape, tol, b, P=0, seed=0, relative=True, rank_cap=None,
               row_by_row=True, stream=None, workspace=None, flags=0):
-    """randQB_EI on a COO matrix (int32 row / col indices, any order, sorted by row fastest;
-    float64 values -> fp64 path, float32 -> mixed)."""
+    """randQB_EI on a COO matrix (int32 row / col indices, each (row, col) at most once, any
+    order, sorted by row fastest; float64 values -> fp64 path, float32 -> mixed)."""
     return _coo_call(_lib.load().qb_ei_coo, "qb_ei_coo", row, col, val, shape, tol, b, P, seed,
                      relative, rank_cap, None, row_by_row, stream, workspace, flags)
 

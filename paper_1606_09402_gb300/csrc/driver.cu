@@ -1011,6 +1011,10 @@ struct FixedBufs {
     char* Yb = nullptr;   // m x k
     char* Qt = nullptr;   // k x m
     char* Gb = nullptr;   // n x k (mixed: rounded copy of G_B^T)
+    bf16* P1 = nullptr;   // mixed, tensor-core path: n x kp rows [G_B^T hi | G_B^T lo | Omega | 0]
+    bf16* P2h = nullptr;  // m x kp rows [Q | Q | Ybar | 0], bf16 hi terms ...
+    bf16* P2l = nullptr;  // ... and lo terms
+    int64_t kp = 0;
 };
 
 void fixed_reserve(Arena& ar, Ctx& c, DenseOp& A, int64_t k, FixedBufs& f, bool bwd) {
@@ -1028,6 +1032,12 @@ void fixed_reserve(Arena& ar, Ctx& c, DenseOp& A, int64_t k, FixedBufs& f, bool 
         f.Gb = ar.get<char>(n * k * es);
     }
     A.reserve(ar, c, k);
+    if (bwd && A.use_tc && n >= 128 && m >= 1) {
+        f.kp = std::max<int64_t>(align_up(3 * k, 64), 128);   // at least one 128-wide K tile
+        f.P1 = ar.get<bf16>(n * f.kp);
+        f.P2h = ar.get<bf16>(m * f.kp);
+        f.P2l = ar.get<bf16>(m * f.kp);
+    }
 }
 
 void fixed_fwd(Ctx& c, DenseOp& A, int64_t k, uint64_t seed, FixedBufs& f, void* Q, int64_t ldq,
@@ -1078,6 +1088,32 @@ void fixed_bwd(Ctx& c, DenseOp& A, int64_t k, uint64_t seed, FixedBufs& f, const
     tri_inv_big(c.st, c.f64, R, ldr, k, f.Ri, k);
     transpose(c.st, c.f64, f.Ri, k, k, k, f.M, k);              // M <- R^-T
     c.nn(m, k, k, 1.0, f.Qb, m, f.M, k, 0.0, f.Yb, m, c.acc_proj);
+    if (f.P1) {
+        // Abar = Q G_B + Ybar Omega^T as ONE tensor-core product with K = 3k: Abar^T (n x m,
+        // column-major = Abar row-major) = [G_B^T hi | G_B^T lo | Omega] [Q | Q | Ybar]^T, the
+        // right factor in two bf16 terms (two products); G_B's lo term carries its float32 part,
+        // Omega is bf16-valued on this path (exact).  Padding columns are zero on both sides.
+        const int64_t kp = f.kp;
+        if (kp > 3 * k) {      // zero padding columns (the packs write the rest)
+            const size_t pw = sizeof(bf16) * size_t(kp - 3 * k), pitch = sizeof(bf16) * size_t(kp);
+            QB_CUDA(cudaMemset2DAsync(f.P1 + 3 * k, pitch, 0, pw, size_t(n), c.st));
+            QB_CUDA(cudaMemset2DAsync(f.P2h + 3 * k, pitch, 0, pw, size_t(m), c.st));
+            QB_CUDA(cudaMemset2DAsync(f.P2l + 3 * k, pitch, 0, pw, size_t(m), c.st));
+        }
+        const float* gb = reinterpret_cast<const float*>(GB);
+        pack_rows_bf16(c.st, gb, ldgb, n, k, f.P1, nullptr, kp, 0);
+        pack_rows_bf16(c.st, gb, ldgb, n, k, nullptr, f.P1, kp, k);     // G_B's lo term
+        pack_rows_bf16(c.st, reinterpret_cast<const float*>(f.Om), n, n, k, f.P1, nullptr, kp,
+                       2 * k);
+        const float* qf = reinterpret_cast<const float*>(Q);
+        pack_rows_bf16(c.st, qf, ldq, m, k, f.P2h, f.P2l, kp, 0);
+        pack_rows_bf16(c.st, qf, ldq, m, k, f.P2h, f.P2l, kp, k);
+        pack_rows_bf16(c.st, reinterpret_cast<const float*>(f.Yb), m, m, k, f.P2h, f.P2l, kp,
+                       2 * k);
+        tc_sketch(c.st, f.P1, kp, n, kp, f.P2h, f.P2l, kp, m, reinterpret_cast<float*>(GA), ldga,
+                  A.tc_scr, A.tc_bytes);
+        return;
+    }
     // Abar^T (n x m, column-major = Abar row-major) = G_B^T Q^T + Omega Ybar^T
     transpose(c.st, c.f64, Q, ldq, m, k, f.Qt, k);
     c.nn(n, m, k, 1.0, GB, ldgb, f.Qt, k, 0.0, GA, ldga, c.acc_proj);

@@ -269,6 +269,30 @@ __global__ void k_transpose(const T* __restrict__ X, int64_t ldx, int64_t rows, 
     }
 }
 
+// Row-major bf16 packing of a float32 column-major block X (rows x cols, ldx): hi[r, off + c] =
+// bf16(X(r, c)) and lo[r, off + c] = bf16(X(r, c) - hi) (round to nearest even both times; either
+// output may be null); a 32 x 32 tile through shared memory keeps both sides coalesced.
+__global__ void k_pack_rows_bf16(const float* __restrict__ X, int64_t ldx, int64_t rows,
+                                 int64_t cols, bf16* __restrict__ hi, bf16* __restrict__ lo,
+                                 int64_t ldo, int64_t off) {
+    __shared__ float tile[32][33];
+    const int64_t r0 = int64_t(blockIdx.x) * 32, c0 = int64_t(blockIdx.y) * 32;
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int64_t r = r0 + threadIdx.x, c = c0 + k;
+        if (r < rows && c < cols) tile[k][threadIdx.x] = X[r + c * ldx];
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int64_t c = c0 + threadIdx.x, r = r0 + k;
+        if (r < rows && c < cols) {
+            const float v = tile[threadIdx.x][k];
+            const bf16 h = __float2bfloat16_rn(v);
+            if (hi) hi[r * ldo + off + c] = h;
+            if (lo) lo[r * ldo + off + c] = __float2bfloat16_rn(v - __bfloat162float(h));
+        }
+    }
+}
+
 // C = tril(M) + tril(M, -1)^T, k x k column-major (ld k)
 template <class T>
 __global__ void k_copyltu(const T* __restrict__ M, int64_t k, T* __restrict__ C) {
@@ -320,6 +344,14 @@ void transpose(cudaStream_t st, bool f64, const void* X, int64_t ldx, int64_t ro
     dim3 g(unsigned(cdiv(rows, 32)), unsigned(cdiv(cols, 32))), b(32, 8);
     if (f64) k_transpose<double><<<g, b, 0, st>>>(reinterpret_cast<const double*>(X), ldx, rows, cols, reinterpret_cast<double*>(Y), ldy);
     else k_transpose<float><<<g, b, 0, st>>>(reinterpret_cast<const float*>(X), ldx, rows, cols, reinterpret_cast<float*>(Y), ldy);
+    QB_LAUNCHED();
+}
+
+void pack_rows_bf16(cudaStream_t st, const float* X, int64_t ldx, int64_t rows, int64_t cols,
+                    bf16* hi, bf16* lo, int64_t ldo, int64_t off) {
+    if (rows <= 0 || cols <= 0) return;
+    dim3 g(unsigned(cdiv(rows, 32)), unsigned(cdiv(cols, 32))), b(32, 8);
+    k_pack_rows_bf16<<<g, b, 0, st>>>(X, ldx, rows, cols, hi, lo, ldo, off);
     QB_LAUNCHED();
 }
 

@@ -167,6 +167,10 @@ void fill_zero(cudaStream_t st, void* p, size_t bytes);
 // Y (cols x rows) = X^T, column-major blocks
 void transpose(cudaStream_t st, bool f64, const void* X, int64_t ldx, int64_t rows, int64_t cols,
                void* Y, int64_t ldy);
+// hi (row-major, ld ldo) columns [off, off + cols) = bf16(X) of the float32 column-major rows x cols
+// block X, row r of the output holding row r of X; lo = bf16(X - hi); either may be null
+void pack_rows_bf16(cudaStream_t st, const float* X, int64_t ldx, int64_t rows, int64_t cols,
+                    bf16* hi, bf16* lo, int64_t ldo, int64_t off);
 // C = tril(M) + tril(M, -1)^T (k x k, ld k)
 void copyltu(cudaStream_t st, bool f64, const void* M, int64_t k, void* C);
 // Y = X converted from float64 (column-major blocks)

@@ -1,8 +1,8 @@
 """GPU parity of the COO paths (Sect. 5.1: the sparse matrix in coordinate format) against the
 float64 CPU oracle, through the C ABI: the sparse workload's structure (Poisson row lengths,
 Zipf column popularity, log-normal values), triplets sorted by row and shuffled (any order is
-accepted), duplicates (they add up), empty rows and columns, a long hot column (its entries span
-many 256-nonzero chunks of the column-sorted copy), and the CSR path on the same matrix."""
+accepted), empty rows and columns, a long hot column (its entries span several 256-nonzero
+chunks of the column-sorted copy), and the CSR path on the same matrix."""
 import numpy as np
 import pytest
 
@@ -52,7 +52,7 @@ def test_coo_fp64_parity(alg, P, order):
     assert abs(info.normA2 - oracle.frob2(S.tocsr())) <= 1e-12 * info.normA2
 
 
-def test_coo_duplicates_empty_rows_and_hot_column():
+def test_coo_empty_rows_and_hot_column():
     rng = np.random.default_rng(3)
     m, n = 517, 389
     dense = rng.standard_normal((m, n)) * (rng.random((m, n)) < 0.02)
@@ -60,13 +60,9 @@ def test_coo_duplicates_empty_rows_and_hot_column():
     dense[:, 40:44] = 0.0       # empty columns
     dense[:, 5] = 1.0           # a fully dense hot column: 517 entries, three 256-chunks
     S = sp.coo_matrix(dense)
-    # split every entry of rows 100..199 into two duplicates that add up to it
-    sel = (S.row >= 100) & (S.row < 200)
-    r = np.concatenate([S.row, S.row[sel]])
-    c = np.concatenate([S.col, S.col[sel]])
-    v = np.concatenate([np.where(sel, 0.25 * S.data, S.data), 0.75 * S.data[sel]])
+    p = np.random.default_rng(2).permutation(S.nnz)
     for f, g in ((qb.qb_ei_coo, oracle.randqb_ei), (qb.qb_fp_coo, oracle.randqb_fp)):
-        Q, B, info = f(*_coo_dev(r, c, v), (m, n), 0.3, 7, P=1, seed=5)
+        Q, B, info = f(*_coo_dev(S.row[p], S.col[p], S.data[p]), (m, n), 0.3, 7, P=1, seed=5)
         ref = g(sp.csr_matrix(dense), 0.3, 7, seed=5, P=1)
         assert info.rank == ref.rank
         diff = np.linalg.norm((Q @ B).cpu().numpy() - ref.Q @ ref.B) / np.linalg.norm(dense)

@@ -48,11 +48,14 @@ def test_fig2_fp64(n, tau, lmax):
     sigma = synth.sigma_exp(n, tau)
     A = synth.dense_from_spectrum_torch(n, n, sigma, n, "cuda", dtype=torch.float64,
                                         work_dtype=torch.float64)
+    # tol 0: the loop runs until E drops below zero through rounding (the point where Fig. 2's
+    # log plot loses the indicator) or the rank cap
     Q, B, info = qb.qb_ei_dense(A, 0.0, 10, P=0, seed=20, rank_cap=lmax)
-    assert info.rank == lmax
-    ls = list(range(10, lmax + 1, lmax // 20))
-    rows = _sweep(A, Q, B, info.normA2, ls)
-    assert abs(rows[-1][1] * info.normA2 - info.err2_est) <= 1e-13 * info.normA2 or ls[-1] != lmax
+    assert info.rank >= lmax // 2
+    ls = list(range(10, info.rank + 1, max(10, info.rank // 20)))
+    rows = _sweep(A, Q, B, info.normA2, ls + [info.rank])
+    # the library's own E at exit is the float64 subtraction of all rows of B
+    assert abs(rows[-1][1] * info.normA2 - info.err2_est) <= 1e-13 * info.normA2
     thr = 4 * U64 / 0.01
     seen_above = seen_below = False
     for l, e, err2, orth in rows:
@@ -74,8 +77,8 @@ def test_fig2_mixed():
     hi, lo, norms = qb.quantize_bf16x2(A)
     Q, B, info = qb.qb_ei_dense(hi, 0.0, 10, P=0, seed=20, rank_cap=lmax, a_lo=lo,
                                 src_norm2=norms[0], prec="mixed")
-    assert info.rank == lmax
-    rows = _sweep(A, Q, B, norms[0], list(range(10, lmax + 1, 20)))
+    assert info.rank >= 100
+    rows = _sweep(A, Q, B, norms[0], list(range(10, info.rank + 1, 20)))
     thr = 4 * U32 / 0.01
     seen_above = False
     for l, e, err2, orth in rows:
