@@ -259,31 +259,48 @@ def run_batched(torch, qb, dev, stream):
     tols = [s.tol for s in specs]
     outs = [(torch.empty(min(s.m, s.n), s.m, device=dev), torch.empty(min(s.m, s.n), s.n, device=dev))
             for s in specs]
-    res = qb.qb_ei_batched(mats, tols, seed=9402, outs=outs)        # warm-up (and result)
+    import ctypes as C
+    from paper_1606_09402_gb300 import _lib
+    lib = _lib.load()
+    descs = (_lib.qb_dense * len(mats))(*[qb._dense_desc(A) for A in mats])
+    o = qb._opts(0.0, 16, 0, 9402, True, None, None, True, "mixed")
+    ws = torch.empty(lib.qb_ei_batched_workspace(len(mats), descs, C.byref(o)), dtype=torch.uint8,
+                     device=dev)
+    # warm-up: the first call tunes the A-streaming stages for this batch shape and captures the
+    # iteration graph; the timed calls reuse both
+    res = qb.qb_ei_batched(mats, tols, seed=9402, outs=outs, workspace=ws)
+    plan_first = qb.batched_last_plan()
     torch.cuda.synchronize()
     times = []
     for _ in range(3):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        res = qb.qb_ei_batched(mats, tols, seed=9402, outs=outs)
+        res = qb.qb_ei_batched(mats, tols, seed=9402, outs=outs, workspace=ws)
         e1.record(stream)
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1) / 1e3)
+    plan = qb.batched_last_plan()
     ranks = [r[2].rank for r in res]
     ok = sum(1 for r in res if r[2].converged)
     a_bytes = sum(4.0 * s.m * s.n for s in specs)
-    # true error of a sample of results (float64, verification only)
+    # true error of every result (float64, verification only)
     worst = 0.0
-    for t in range(0, 256, 32):
+    for t in range(len(specs)):
         A = mats[t].double()
         Q, B, _ = res[t]
         worst = max(worst, float(torch.linalg.norm(A - Q.double() @ B.double()) / torch.linalg.norm(A)) / tols[t])
-    return {"matrices": 256, "time_s": statistics.median(times), "converged": ok,
+    # bytes of A the A-streaming stages read: each block of matrix t reads A_t twice
+    a_read = sum(2.0 * 4.0 * s.m * s.n * r[2].blocks for s, r in zip(specs, res))
+    t_med = statistics.median(times)
+    pk, _ = peaks()
+    return {"matrices": len(specs), "time_s": t_med, "converged": ok,
             "rank_min": int(min(ranks)), "rank_max": int(max(ranks)),
             "blocks_total": int(sum(r[2].blocks for r in res)),
-            "a_bytes_per_sweep": a_bytes, "worst_err_over_tol_sampled": worst,
-            "note": "one graph launch per call; includes graph build/instantiate"}
+            "a_bytes_per_sweep": a_bytes, "a_bytes_read": a_read,
+            "a_read_gbs": a_read / t_med / 1e9, "a_read_frac_of_hbm": a_read / t_med / 1e9 / pk["hbm_gbs"],
+            "worst_err_over_tol": worst, "plan": plan, "plan_first_call": plan_first,
+            "note": "one graph launch per call; the timed calls reuse the graph and the tuned plan"}
 
 
 def run_sparse(torch, qb, dev, stream):

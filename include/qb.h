@@ -241,9 +241,25 @@ int32_t qb_apass_trans(const qb_dense* A, const void* V, int64_t ldv, int64_t w,
  * column-major m_t x cap_t (ldqs[t] >= m_t), B_t row-major cap_t x n_t (ldbs[t] >= n_t),
  * cap_t = min(m_t, n_t, rank_cap).  Q and B are float32; the indicator is float64 and the stop
  * test keeps the 2 u ||A_t||^2 margin of the mixed path.  infos[t] receives each result; the
- * return value is the worst status over the batch.  Synchronises the stream.
+ * return value is the worst status over the batch.  Synchronises the stream.  Calls that share a
+ * workspace must not overlap (the kept graph of a call reads the workspace it was captured on).
  * ------------------------------------------------------------------------------------------- */
 size_t qb_ei_batched_workspace(int32_t count, const qb_dense* As, const qb_opts* opts);
+/* Launch plan of the batched call's two A-streaming stages (the sketch Y = A Omega and the pass
+ * B_i = Y^T A): tile shape and grid size.  The first call that meets a batch-shape bucket (log2
+ * of the count, of the mean m and of the mean n) times every candidate on its own matrices (tile
+ * shapes 64 / 128 rows per sketch tile and 64 / 128 columns per B tile, 4 / 8 / 16 CTAs per SM;
+ * both stages are pure functions of their inputs, so the extra runs change no result) and keeps
+ * the fastest of each stage for the bucket; later calls reuse it.  The iteration graph of a call
+ * is kept (up to 4, keyed by workspace address, shapes, plan, seed and stop rule) and relaunched
+ * by a later call with the same key instead of being captured again.
+ *   qb_batched_set_plan(cfg): cfg = {rows per thread (1|2), columns per thread (1|2), sketch
+ *     CTAs per SM, B-pass CTAs per SM} pins the plan for later calls; NULL returns to the tuner.
+ *   qb_batched_last_plan(out, n): the last call's {rows per thread, columns per thread, sketch
+ *     grid, B-pass grid, 1 if it tuned, 1 if it reused a graph, tuner cache entries}; returns 7.
+ * The tile shape changes no summation order: results are identical under every plan. */
+int32_t qb_batched_set_plan(const int32_t* cfg);
+int32_t qb_batched_last_plan(int32_t* out, int32_t n);
 int32_t qb_ei_batched(int32_t count, const qb_dense* As, const double* tols,
                       const qb_opts* opts, void* const* Qs, const int64_t* ldqs,
                       void* const* Bs, const int64_t* ldbs, void* ws, size_t ws_bytes,

@@ -501,6 +501,28 @@ def qb_svd_from_qb(Q, B, want_u=True, want_v=True, stream=None):
     return (Ut.T if want_u else None), S, (Vt.T if want_v else None), int(sweeps.value)
 
 
+def batched_set_plan(cfg=None):
+    """Pin the batched call's launch plan: cfg = (rows per thread 1|2, columns per thread 1|2,
+    sketch CTAs per SM, B-pass CTAs per SM); None returns to the autotuner."""
+    lib = _lib.load()
+    if cfg is None:
+        rc = lib.qb_batched_set_plan(None)
+    else:
+        arr = (C.c_int32 * 4)(*[int(x) for x in cfg])
+        rc = lib.qb_batched_set_plan(arr)
+    if rc < 0:
+        raise QBError(rc, "qb_batched_set_plan")
+
+
+def batched_last_plan() -> dict:
+    """The last batched call's plan: tile shape, grids, whether it tuned and reused a graph."""
+    out = (C.c_int32 * 8)()
+    _lib.load().qb_batched_last_plan(out, 8)
+    keys = ("rows_per_thread", "cols_per_thread", "sketch_grid", "bpass_grid", "tuned",
+            "graph_reused", "tuner_entries")
+    return dict(zip(keys, (int(x) for x in out[:7])))
+
+
 def _autograd_function():
     torch = _torch()
 

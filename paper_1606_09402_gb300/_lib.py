@@ -108,6 +108,8 @@ _SIG = {
     "qb_svd_workspace": (C.c_size_t, [_I64, _I64, _I64, C.c_int32]),
     "qb_svd_from_qb": (C.c_int32, [_I64, _I64, _I64, C.c_int32, _P, _I64, _P, _I64, _P, _P, _I64,
                                    _P, _I64, _P, C.c_size_t, C.POINTER(C.c_int32), _P]),
+    "qb_batched_set_plan": (C.c_int32, [C.POINTER(C.c_int32)]),
+    "qb_batched_last_plan": (C.c_int32, [C.POINTER(C.c_int32), C.c_int32]),
     "qb_quantize_workspace": (C.c_size_t, [_I64, _I64]),
     "qb_quantize_bf16x2": (C.c_int32, [_P, _I64, _I64, _I64, _P, _P, _I64,
                                        C.POINTER(C.c_double), _P, C.c_size_t, _P]),

@@ -14,6 +14,10 @@
 #include "qb_internal.cuh"
 
 #include <algorithm>
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 namespace qb {
@@ -96,20 +100,27 @@ __global__ void __launch_bounds__(NT) k_b_omega(BDesc* D, Plan p, uint64_t seed)
     }
 }
 
-// Y (slot of Q at column k) = A Omega; tile = 64 rows x b, thread = (row, 4 columns)
+// Y (slot of Q at column k) = A Omega; tile = 64 RT rows x b, thread = (RT rows, 4 columns).
+// RT is a tile shape the autotuner picks per batch shape (more rows per thread reuse each Omega
+// value RT times from shared memory).
+template <int RT>
 __global__ void __launch_bounds__(NT) k_b_sketch(BDesc* D, Plan p) {
-    __shared__ float As[ROWS][65];
+    __shared__ float As[ROWS * RT][65];
     __shared__ float Os[64][BB];
     FOR_ITEMS(p) {
         const int t = find_matrix(p, item);
         BDesc& d = D[t];
         if (d.done) continue;
-        const int64_t r0 = (item - p.prefix[t]) * ROWS;
+        const int64_t r0 = (item - p.prefix[t]) * (ROWS * RT);
         const int row = threadIdx.x >> 2, cq = (threadIdx.x & 3) * 4;
-        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        float acc[RT][4];
+#pragma unroll
+        for (int r = 0; r < RT; ++r)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[r][q] = 0.f;
         for (int64_t k0 = 0; k0 < d.n; k0 += 64) {
             __syncthreads();
-            for (int e = threadIdx.x; e < ROWS * 64; e += NT) {
+            for (int e = threadIdx.x; e < ROWS * RT * 64; e += NT) {
                 const int i = e / 64, j = e % 64;
                 const int64_t gr = r0 + i, gc = k0 + j;
                 As[i][j] = (gr < d.m && gc < d.n) ? d.A[gr * d.lda + gc] : 0.f;
@@ -122,15 +133,24 @@ __global__ void __launch_bounds__(NT) k_b_sketch(BDesc* D, Plan p) {
             __syncthreads();
 #pragma unroll 8
             for (int j = 0; j < 64; ++j) {
-                const float a = As[row][j];
+                float o[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) acc[q] = fmaf(a, Os[j][cq + q], acc[q]);
+                for (int q = 0; q < 4; ++q) o[q] = Os[j][cq + q];
+#pragma unroll
+                for (int r = 0; r < RT; ++r) {
+                    const float a = As[row + ROWS * r][j];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[r][q] = fmaf(a, o[q], acc[r][q]);
+                }
             }
         }
-        const int64_t gr = r0 + row;
-        if (gr < d.m) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) d.Y[gr + (cq + q) * d.m] = acc[q];
+        for (int r = 0; r < RT; ++r) {
+            const int64_t gr = r0 + row + ROWS * r;
+            if (gr < d.m) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) d.Y[gr + (cq + q) * d.m] = acc[r][q];
+            }
         }
     }
 }
@@ -328,22 +348,28 @@ __global__ void __launch_bounds__(NT) k_b_apply(BDesc* D, Plan p) {
     }
 }
 
-// B_i (rows k..k+b of B) = Y^T A; tile = 64 columns of B; thread = (column, 4 rows)
+// B_i (rows k..k+b of B) = Y^T A; tile = 64 CT columns of B; thread = (CT columns, 4 rows).
+// CT is the autotuned tile shape of this stage.
+template <int CT>
 __global__ void __launch_bounds__(NT) k_b_bpass(BDesc* D, Plan p) {
-    __shared__ float As[64][65];
+    __shared__ float As[64][64 * CT + 1];
     __shared__ float Ys[64][BB];
     FOR_ITEMS(p) {
         const int t = find_matrix(p, item);
         BDesc& d = D[t];
         if (d.done) continue;
-        const int64_t c0 = (item - p.prefix[t]) * 64;
+        const int64_t c0 = (item - p.prefix[t]) * (64 * CT);
         const float* Y = d.Y;
         const int col = threadIdx.x & 63, rq = (threadIdx.x >> 6) * 4;
-        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        float acc[CT][4];
+#pragma unroll
+        for (int c = 0; c < CT; ++c)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[c][q] = 0.f;
         for (int64_t r0 = 0; r0 < d.m; r0 += 64) {
             __syncthreads();
-            for (int e = threadIdx.x; e < 64 * 64; e += NT) {
-                const int i = e / 64, j = e % 64;
+            for (int e = threadIdx.x; e < 64 * 64 * CT; e += NT) {
+                const int i = e / (64 * CT), j = e % (64 * CT);
                 const int64_t gr = r0 + i, gc = c0 + j;
                 As[i][j] = (gr < d.m && gc < d.n) ? d.A[gr * d.lda + gc] : 0.f;
             }
@@ -355,15 +381,24 @@ __global__ void __launch_bounds__(NT) k_b_bpass(BDesc* D, Plan p) {
             __syncthreads();
 #pragma unroll 8
             for (int i = 0; i < 64; ++i) {
-                const float a = As[i][col];
+                float y[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) acc[q] = fmaf(a, Ys[i][rq + q], acc[q]);
+                for (int q = 0; q < 4; ++q) y[q] = Ys[i][rq + q];
+#pragma unroll
+                for (int c = 0; c < CT; ++c) {
+                    const float a = As[i][col + 64 * c];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[c][q] = fmaf(a, y[q], acc[c][q]);
+                }
             }
         }
-        const int64_t gc = c0 + col;
-        if (gc < d.n) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) d.Bi[(rq + q) * d.n + gc] = acc[q];
+        for (int c = 0; c < CT; ++c) {
+            const int64_t gc = c0 + col + 64 * c;
+            if (gc < d.n) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) d.Bi[(rq + q) * d.n + gc] = acc[c][q];
+            }
         }
     }
 }
@@ -437,22 +472,60 @@ __global__ void k_b_cond(cudaGraphConditionalHandle h, int* active, int* iter, i
 }  // namespace
 
 // ------------------------------------------------------------------------------------ host side
-struct BatchedPlan {
-    std::vector<int64_t> pre_omega, pre_rows, pre_coefB, pre_coefQ, pre_cols;
-};
-
 namespace {
 void prefix(std::vector<int64_t>& v, const std::vector<int64_t>& tiles) {
     v.assign(tiles.size() + 1, 0);
     for (size_t i = 0; i < tiles.size(); ++i) v[i + 1] = v[i] + tiles[i];
 }
+
+// Tile prefixes kept in the workspace: Omega rows, 64-row tiles, coefficient tiles, 64-column
+// tiles, 128-row tiles (sketch, RT = 2), 128-column tiles (B pass, CT = 2).
+constexpr int NPRE = 6;
+enum { PRE_OMEGA = 0, PRE_ROWS, PRE_COEF, PRE_COLS, PRE_ROWS2, PRE_COLS2 };
+
+// Launch plan of the two stages that stream A (the sketch Y = A Omega and the B pass B_i = Y^T A):
+// tile shape (rows / columns per thread) and grid size.  The rest of the stages are fixed.
+struct BatchedCfg {
+    int rt = 1, ct = 1;      // tile shape: 64 rt rows per sketch tile, 64 ct columns per B tile
+    int gsk = 0, gbp = 0;    // CTAs of the two launches
+};
+
+// Autotuner: the first call that sees a batch shape bucket times every candidate of the two
+// A-streaming stages on the call's own matrices (both stages are pure functions of their inputs,
+// so running them extra times changes nothing) and keeps the fastest per stage; later calls of the
+// same bucket reuse the choice.  Bucket: (log2 of the matrix count, log2 of the mean m, log2 of
+// the mean n).
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, BatchedCfg> g_tune_cache;
+BatchedCfg g_pinned;            // rt == 0: autotune (set by qb_batched_set_plan)
+bool g_pinned_on = false;
+int32_t g_last_plan[8] = {0};   // rt, ct, gsk, gbp, tuned this call, graph reused, cache entries
+
+int ilog2c(double x) {
+    int e = 0;
+    while ((1LL << e) < int64_t(std::ceil(x))) ++e;
+    return e;
+}
+
+// Instantiated graphs of earlier calls, keyed by everything a graph bakes in (workspace address
+// and layout, shapes, plan, seed, stop rule): a repeated batch shape relaunches its graph.
+struct GraphEntry {
+    std::vector<int64_t> key;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int kernels_per_iter = 0;
+};
+std::mutex g_graph_mu;
+std::vector<GraphEntry> g_graphs;   // most recently used last
+constexpr size_t MAX_GRAPHS = 4;
+
 }  // namespace
 
 // Workspace layout (also used to measure it): descriptors, tile prefixes, flags, norm partials,
 // then per matrix Omega (n x b), Y (m x b), B_i (b x n), T (cap x b), W / R^-1 / row norms.
 struct BatchedWs {
     BDesc* D = nullptr;
-    int64_t* pre[5] = {};
+    int64_t* pre[NPRE] = {};
     int* flags = nullptr;
     double* part = nullptr;
     double* nrm = nullptr;
@@ -462,7 +535,7 @@ struct BatchedWs {
 void batched_reserve(Arena& ar, int32_t count, const qb_dense* As, int64_t cap_opt, BatchedWs& w,
                      std::vector<BDesc>* h) {
     w.D = ar.get<BDesc>(count);
-    for (int s = 0; s < 5; ++s) w.pre[s] = ar.get<int64_t>(count + 1);
+    for (int s = 0; s < NPRE; ++s) w.pre[s] = ar.get<int64_t>(count + 1);
     w.flags = ar.get<int>(16);
     w.part = ar.get<double>(1024);
     w.nrm = ar.get<double>(count);
@@ -492,6 +565,35 @@ size_t batched_workspace(int32_t count, const qb_dense* As, int64_t cap_opt) {
     return ar.used + 4096;
 }
 
+namespace {
+void launch_sketch(int rt, unsigned g, cudaStream_t s, BDesc* D, const Plan& p1, const Plan& p2) {
+    if (rt == 2) k_b_sketch<2><<<g, NT, 0, s>>>(D, p2);
+    else k_b_sketch<1><<<g, NT, 0, s>>>(D, p1);
+}
+void launch_bpass(int ct, unsigned g, cudaStream_t s, BDesc* D, const Plan& p1, const Plan& p2) {
+    if (ct == 2) k_b_bpass<2><<<g, NT, 0, s>>>(D, p2);
+    else k_b_bpass<1><<<g, NT, 0, s>>>(D, p1);
+}
+
+// Time `reps` launches of fn on st (CUDA events), after one untimed launch.
+template <class F>
+float time_launches(cudaStream_t st, F fn, int reps) {
+    cudaEvent_t e0, e1;
+    QB_CUDA(cudaEventCreate(&e0));
+    QB_CUDA(cudaEventCreate(&e1));
+    fn();
+    QB_CUDA(cudaEventRecord(e0, st));
+    for (int r = 0; r < reps; ++r) fn();
+    QB_CUDA(cudaEventRecord(e1, st));
+    QB_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    QB_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ms;
+}
+}  // namespace
+
 }  // namespace qb
 
 using namespace qb;
@@ -499,6 +601,26 @@ using namespace qb;
 extern "C" size_t qb_ei_batched_workspace(int32_t count, const qb_dense* As, const qb_opts* opts) {
     if (count <= 0 || !As || !opts) return 0;
     return batched_workspace(count, As, opts->rank_cap);
+}
+
+extern "C" int32_t qb_batched_set_plan(const int32_t* cfg) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (!cfg) {
+        g_pinned_on = false;
+        return QB_OK;
+    }
+    if ((cfg[0] != 1 && cfg[0] != 2) || (cfg[1] != 1 && cfg[1] != 2) || cfg[2] < 1 || cfg[3] < 1)
+        return QB_ERR_INVALID_ARG;
+    g_pinned = BatchedCfg{cfg[0], cfg[1], cfg[2], cfg[3]};
+    g_pinned_on = true;
+    return QB_OK;
+}
+
+extern "C" int32_t qb_batched_last_plan(int32_t* out, int32_t n) {
+    if (!out || n < 0) return QB_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (int i = 0; i < n && i < 8; ++i) out[i] = g_last_plan[i];
+    return 7;
 }
 
 extern "C" int32_t qb_ei_batched(int32_t count, const qb_dense* As, const double* tols,
@@ -527,8 +649,10 @@ extern "C" int32_t qb_ei_batched(int32_t count, const qb_dense* As, const double
         BDesc* dD = w.D;
         int64_t** pre = w.pre;
         int* flags = w.flags;
-        std::vector<int64_t> t_omega(count), t_rows(count), t_coefB(count), t_cols(count);
+        std::vector<int64_t> tiles[NPRE];
+        for (auto& v : tiles) v.resize(count);
         int64_t max_iter = 0;
+        double sum_m = 0, sum_n = 0;
         QB_CUDA(cudaMemsetAsync(w.nf, 0, 4 * sizeof(int), st));
         std::vector<double> nrm(count);
         for (int t = 0; t < count; ++t) {
@@ -541,11 +665,15 @@ extern "C" int32_t qb_ei_batched(int32_t count, const qb_dense* As, const double
             d.k = 0; d.blocks = 0; d.done = 0; d.pad = 0;
             if (std::isnan(a.src_norm2))
                 dense_norm2(st, XOp{X_F32, a.a, nullptr, a.ld}, a.m, a.n, w.part, w.nrm + t, w.nf);
-            t_omega[t] = cdiv(a.n, NT);
-            t_rows[t] = cdiv(a.m, ROWS);
-            t_coefB[t] = cdiv(d.cap, ROWS);
-            t_cols[t] = cdiv(a.n, 64);
+            tiles[PRE_OMEGA][t] = cdiv(a.n, NT);
+            tiles[PRE_ROWS][t] = cdiv(a.m, ROWS);
+            tiles[PRE_COEF][t] = cdiv(d.cap, ROWS);
+            tiles[PRE_COLS][t] = cdiv(a.n, 64);
+            tiles[PRE_ROWS2][t] = cdiv(a.m, 2 * ROWS);
+            tiles[PRE_COLS2][t] = cdiv(a.n, 128);
             max_iter = std::max<int64_t>(max_iter, cdiv(d.cap, BB));
+            sum_m += double(a.m);
+            sum_n += double(a.n);
         }
         QB_CUDA(cudaMemcpyAsync(nrm.data(), w.nrm, sizeof(double) * count, cudaMemcpyDeviceToHost, st));
         QB_CUDA(cudaStreamSynchronize(st));
@@ -561,35 +689,82 @@ extern "C" int32_t qb_ei_batched(int32_t count, const qb_dense* As, const double
             h[t].eps2 = eps * eps - 2.0 * 5.9604644775390625e-08 * nrm[t];
             if (nrm[t] == 0.0) h[t].done = 1;
         }
-        std::vector<int64_t> P[5];
-        prefix(P[0], t_omega);
-        prefix(P[1], t_rows);
-        prefix(P[2], t_coefB);
-        prefix(P[3], t_coefB);
-        prefix(P[4], t_cols);
+        std::vector<int64_t> P[NPRE];
+        for (int s2 = 0; s2 < NPRE; ++s2) prefix(P[s2], tiles[s2]);
         QB_CUDA(cudaMemcpyAsync(dD, h.data(), sizeof(BDesc) * count, cudaMemcpyHostToDevice, st));
-        for (int s = 0; s < 5; ++s)
-            QB_CUDA(cudaMemcpyAsync(pre[s], P[s].data(), sizeof(int64_t) * (count + 1),
+        for (int s2 = 0; s2 < NPRE; ++s2)
+            QB_CUDA(cudaMemcpyAsync(pre[s2], P[s2].data(), sizeof(int64_t) * (count + 1),
                                     cudaMemcpyHostToDevice, st));
         int init[2] = {1, 0};
         QB_CUDA(cudaMemcpyAsync(flags, init, sizeof init, cudaMemcpyHostToDevice, st));
         QB_CUDA(cudaStreamSynchronize(st));   // host vectors above die with this scope
 
-        const Plan pOm{pre[0], count}, pRows{pre[1], count}, pCoef{pre[2], count},
-            pCols{pre[4], count};
-        const int G = 2 * num_sms();
-        auto grid_for = [&](const std::vector<int64_t>& pv) {
-            return unsigned(std::max<int64_t>(1, std::min<int64_t>(pv.back(), 8LL * G)));
+        const Plan pOm{pre[PRE_OMEGA], count}, pRows{pre[PRE_ROWS], count},
+            pCoef{pre[PRE_COEF], count}, pCols{pre[PRE_COLS], count},
+            pRows2{pre[PRE_ROWS2], count}, pCols2{pre[PRE_COLS2], count};
+        const int S = num_sms();
+        const int G = 2 * S;
+        auto grid_cap = [&](int64_t tiles_total, int64_t want) {
+            return unsigned(std::max<int64_t>(1, std::min<int64_t>(tiles_total, want)));
         };
-        const unsigned gOm = grid_for(P[0]), gRows = grid_for(P[1]), gCoef = grid_for(P[2]),
-                       gCols = grid_for(P[4]), gMat = unsigned(std::min(count, 4 * num_sms()));
-        int kernels_per_iter = 0;
-        auto body = [&](cudaStream_t s) {
+        const unsigned gOm = grid_cap(P[PRE_OMEGA].back(), 8LL * G),
+                       gRows = grid_cap(P[PRE_ROWS].back(), 8LL * G),
+                       gCoef = grid_cap(P[PRE_COEF].back(), 8LL * G),
+                       gMat = unsigned(std::min(count, 4 * S));
+
+        // ---- plan of the A-streaming stages: pinned, cached, or tuned now
+        BatchedCfg cfg;
+        int tuned_now = 0;
+        const auto bucket = std::make_tuple(ilog2c(count), ilog2c(sum_m / count),
+                                            ilog2c(sum_n / count));
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            if (g_pinned_on) {
+                cfg = g_pinned;
+                cfg.gsk = int(grid_cap(P[cfg.rt == 2 ? PRE_ROWS2 : PRE_ROWS].back(),
+                                       int64_t(g_pinned.gsk) * S));
+                cfg.gbp = int(grid_cap(P[cfg.ct == 2 ? PRE_COLS2 : PRE_COLS].back(),
+                                       int64_t(g_pinned.gbp) * S));
+            } else {
+                auto it = g_tune_cache.find(bucket);
+                if (it != g_tune_cache.end()) cfg = it->second;
+            }
+        }
+        if (cfg.gsk == 0) {
+            // candidates: tile shape x {4, 8, 16} CTAs per SM, each timed over 2 launches on this
+            // batch after Omega has been drawn (the sketch reads it, the B pass reads Y)
+            k_b_omega<<<gOm, NT, 0, st>>>(dD, pOm, opts->seed);
+            QB_LAUNCHED();
+            float best_sk = 1e30f, best_bp = 1e30f;
+            for (int shape = 1; shape <= 2; ++shape) {
+                for (int per_sm : {4, 8, 16}) {
+                    const unsigned gs = grid_cap(P[shape == 2 ? PRE_ROWS2 : PRE_ROWS].back(),
+                                                 int64_t(per_sm) * S);
+                    const float ts = time_launches(st, [&] {
+                        launch_sketch(shape, gs, st, dD, pRows, pRows2);
+                        QB_LAUNCHED();
+                    }, 2);
+                    if (ts < best_sk) { best_sk = ts; cfg.rt = shape; cfg.gsk = int(gs); }
+                    const unsigned gb = grid_cap(P[shape == 2 ? PRE_COLS2 : PRE_COLS].back(),
+                                                 int64_t(per_sm) * S);
+                    const float tb = time_launches(st, [&] {
+                        launch_bpass(shape, gb, st, dD, pCols, pCols2);
+                        QB_LAUNCHED();
+                    }, 2);
+                    if (tb < best_bp) { best_bp = tb; cfg.ct = shape; cfg.gbp = int(gb); }
+                }
+            }
+            tuned_now = 1;
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tune_cache[bucket] = cfg;
+        }
+
+        auto body = [&](cudaStream_t s, int& kernels_per_iter) {
             kernels_per_iter = 0;
             auto L = [&]() { ++kernels_per_iter; QB_LAUNCHED(); };
             k_b_clear<<<1, 1, 0, s>>>(flags); L();
             k_b_omega<<<gOm, NT, 0, s>>>(dD, pOm, opts->seed); L();
-            k_b_sketch<<<gRows, NT, 0, s>>>(dD, pRows); L();
+            launch_sketch(cfg.rt, unsigned(cfg.gsk), s, dD, pRows, pRows2); L();
             k_b_coef<0><<<gCoef, NT, 0, s>>>(dD, pCoef); L();
             k_b_update<<<gRows, NT, 0, s>>>(dD, pRows); L();
             for (int pass = 0; pass < 2; ++pass) {
@@ -602,44 +777,86 @@ extern "C" int32_t qb_ei_batched(int32_t count, const qb_dense* As, const double
                     k_b_apply<<<gRows, NT, 0, s>>>(dD, pRows); L();
                 }
             }
-            k_b_bpass<<<gCols, NT, 0, s>>>(dD, pCols); L();
+            launch_bpass(cfg.ct, unsigned(cfg.gbp), s, dD, pCols, pCols2); L();
             k_b_indicator<<<gMat, NT, 0, s>>>(dD, count, flags, opts->row_by_row); L();
         };
 
-        // one iteration body under a conditional WHILE node
-        cudaGraph_t graph = nullptr;
+        // ---- the iteration under a conditional WHILE node: reuse the graph of an earlier call
+        // with the same key, else capture and instantiate one (kept for the next call)
+        std::vector<int64_t> key = {int64_t(reinterpret_cast<uintptr_t>(ws)), count,
+                                    int64_t(opts->seed), opts->row_by_row, max_iter, cfg.rt,
+                                    cfg.ct, cfg.gsk, cfg.gbp, int64_t(gOm), int64_t(gRows),
+                                    int64_t(gCoef), int64_t(gMat), S};
+        for (int t = 0; t < count; ++t) {
+            key.push_back(h[t].m);
+            key.push_back(h[t].n);
+            key.push_back(h[t].cap);
+        }
         cudaGraphExec_t exec = nullptr;
-        QB_CUDA(cudaGraphCreate(&graph, 0));
-        cudaGraphConditionalHandle handle;
-        QB_CUDA(cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault));
-        cudaGraphNodeParams cp = {};
-        cp.type = cudaGraphNodeTypeConditional;
-        cp.conditional.handle = handle;
-        cp.conditional.type = cudaGraphCondTypeWhile;
-        cp.conditional.size = 1;
-        cudaGraphNode_t cnode;
-        QB_CUDA(cudaGraphAddNode(&cnode, graph, nullptr, nullptr, 0, &cp));
-        cudaGraph_t bodyg = cp.conditional.phGraph_out[0];
-        cudaStream_t cs = nullptr;
-        QB_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-        QB_CUDA(cudaStreamBeginCaptureToGraph(cs, bodyg, nullptr, nullptr, 0,
-                                              cudaStreamCaptureModeThreadLocal));
-        body(cs);
-        k_b_cond<<<1, 1, 0, cs>>>(handle, flags, flags + 1, int(max_iter));
-        ++kernels_per_iter;
-        QB_CUDA(cudaGetLastError());
-        QB_CUDA(cudaStreamEndCapture(cs, &bodyg));
-        QB_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+        int kernels_per_iter = 0;
+        int reused = 0;
+        std::unique_lock<std::mutex> glk(g_graph_mu);
+        for (size_t i = 0; i < g_graphs.size(); ++i) {
+            if (g_graphs[i].key == key) {
+                GraphEntry e = g_graphs[i];
+                g_graphs.erase(g_graphs.begin() + int64_t(i));
+                g_graphs.push_back(e);
+                exec = e.exec;
+                kernels_per_iter = e.kernels_per_iter;
+                reused = 1;
+                break;
+            }
+        }
+        if (!exec) {
+            cudaGraph_t graph = nullptr;
+            QB_CUDA(cudaGraphCreate(&graph, 0));
+            cudaGraphConditionalHandle handle;
+            QB_CUDA(cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault));
+            cudaGraphNodeParams cp = {};
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = handle;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            cudaGraphNode_t cnode;
+            QB_CUDA(cudaGraphAddNode(&cnode, graph, nullptr, nullptr, 0, &cp));
+            cudaGraph_t bodyg = cp.conditional.phGraph_out[0];
+            cudaStream_t cs = nullptr;
+            QB_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+            QB_CUDA(cudaStreamBeginCaptureToGraph(cs, bodyg, nullptr, nullptr, 0,
+                                                  cudaStreamCaptureModeThreadLocal));
+            body(cs, kernels_per_iter);
+            k_b_cond<<<1, 1, 0, cs>>>(handle, flags, flags + 1, int(max_iter));
+            ++kernels_per_iter;
+            QB_CUDA(cudaGetLastError());
+            QB_CUDA(cudaStreamEndCapture(cs, &bodyg));
+            QB_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+            cudaStreamDestroy(cs);
+            GraphEntry e{key, graph, exec, kernels_per_iter};
+            g_graphs.push_back(e);
+            if (g_graphs.size() > MAX_GRAPHS) {
+                cudaGraphExecDestroy(g_graphs.front().exec);
+                cudaGraphDestroy(g_graphs.front().graph);
+                g_graphs.erase(g_graphs.begin());
+            }
+        }
         QB_CUDA(cudaGraphLaunch(exec, st));
+        glk.unlock();
         QB_CUDA(cudaStreamSynchronize(st));
         int iters = 0;
         QB_CUDA(cudaMemcpy(&iters, flags + 1, sizeof(int), cudaMemcpyDeviceToHost));
-        cudaGraphExecDestroy(exec);
-        cudaGraphDestroy(graph);
-        cudaStreamDestroy(cs);
-        // the capture counted one pass of kernels; the graph ran it `iters` times
-        for (int64_t i = 1; i < int64_t(iters); ++i)
+        // the capture counted no launches; the graph ran the body `iters` times
+        for (int64_t i = (reused ? 0 : 1); i < int64_t(iters); ++i)
             for (int q = 0; q < kernels_per_iter; ++q) count_launch();
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_last_plan[0] = cfg.rt;
+            g_last_plan[1] = cfg.ct;
+            g_last_plan[2] = cfg.gsk;
+            g_last_plan[3] = cfg.gbp;
+            g_last_plan[4] = tuned_now;
+            g_last_plan[5] = reused;
+            g_last_plan[6] = int32_t(g_tune_cache.size());
+        }
 
         std::vector<BDesc> out(count);
         QB_CUDA(cudaMemcpy(out.data(), dD, sizeof(BDesc) * count, cudaMemcpyDeviceToHost));

@@ -54,3 +54,44 @@ def test_batched_uneven_and_rank_cap():
         assert oracle.orth_loss(Qh) < 1e-4
         Bh = B.double().cpu().numpy()
         assert np.linalg.norm(Bh - Qh.T @ A) <= 1e-5 * np.linalg.norm(A)
+
+
+def test_batched_autotuner_choice_is_used_and_graph_reused():
+    """The first call on a new batch-shape bucket tunes the two A-streaming stages and records its
+    choice; the next call with the same shapes (and workspace) reuses both the choice and the
+    captured iteration graph and gives the same result bit for bit.  Every pinned plan gives the
+    same result too: the tile shape changes no summation order."""
+    specs, mats = _batch(10, 17, 300, 1400)
+    As = [torch.tensor(A).cuda() for A in mats]
+    tols = [s.tol for s in specs]
+    outs = [(torch.empty(min(A.shape), A.shape[0], device="cuda"),
+             torch.empty(min(A.shape), A.shape[1], device="cuda")) for A in mats]
+    import ctypes as C
+    from paper_1606_09402_gb300 import _lib
+    lib = _lib.load()
+    descs = (_lib.qb_dense * len(As))(*[qb._dense_desc(A) for A in As])
+    o = qb._opts(0.0, 16, 0, 40, True, None, None, True, "mixed")
+    ws = torch.empty(lib.qb_ei_batched_workspace(len(As), descs, C.byref(o)), dtype=torch.uint8,
+                     device="cuda")
+    qb.batched_set_plan(None)
+    r1 = qb.qb_ei_batched(As, tols, seed=40, outs=outs, workspace=ws)
+    p1 = qb.batched_last_plan()
+    snap = [(Q.clone(), B.clone(), i.rank) for Q, B, i in r1]
+    r2 = qb.qb_ei_batched(As, tols, seed=40, outs=outs, workspace=ws)
+    p2 = qb.batched_last_plan()
+    assert p2["tuned"] == 0 and p2["graph_reused"] == 1
+    for key in ("rows_per_thread", "cols_per_thread", "sketch_grid", "bpass_grid"):
+        assert p1[key] == p2[key], (key, p1, p2)
+    assert p1["rows_per_thread"] in (1, 2) and p1["cols_per_thread"] in (1, 2)
+    for (Q, B, i), (Qs, Bs, k) in zip(r2, snap):
+        assert i.rank == k and torch.equal(Q, Qs) and torch.equal(B, Bs)
+    try:
+        for cfg in [(1, 1, 4, 4), (2, 2, 16, 8), (2, 1, 8, 16)]:
+            qb.batched_set_plan(cfg)
+            r3 = qb.qb_ei_batched(As, tols, seed=40, outs=outs, workspace=ws)
+            p3 = qb.batched_last_plan()
+            assert (p3["rows_per_thread"], p3["cols_per_thread"]) == cfg[:2] and p3["tuned"] == 0
+            for (Q, B, i), (Qs, Bs, k) in zip(r3, snap):
+                assert i.rank == k and torch.equal(Q, Qs) and torch.equal(B, Bs), cfg
+    finally:
+        qb.batched_set_plan(None)
