@@ -170,6 +170,7 @@ __global__ void __launch_bounds__(NT) k_b_coef(BDesc* D, Plan p) {
         const float* Y = d.Y;
         const int row = threadIdx.x >> 2, cq = (threadIdx.x & 3) * 4;
         float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        float lo[4] = {0.f, 0.f, 0.f, 0.f};   // MODE 1: low parts of the float32-pair sums
         for (int64_t k0 = 0; k0 < K; k0 += 64) {
             __syncthreads();
             for (int e = threadIdx.x; e < ROWS * 64; e += NT) {
@@ -194,17 +195,35 @@ __global__ void __launch_bounds__(NT) k_b_coef(BDesc* D, Plan p) {
                 Vs[j][c] = v;
             }
             __syncthreads();
+            if (MODE == 0) {
 #pragma unroll 8
-            for (int j = 0; j < 64; ++j) {
-                const float a = Xs[row][j];
+                for (int j = 0; j < 64; ++j) {
+                    const float a = Xs[row][j];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) acc[q] = fmaf(a, Vs[j][cq + q], acc[q]);
+                    for (int q = 0; q < 4; ++q) acc[q] = fmaf(a, Vs[j][cq + q], acc[q]);
+                }
+            } else {
+                // the re-orthogonalisation coefficients Q^T Y: exact products (fma residual) and
+                // two-sum accumulation, so the coefficients carry ~u, not ~sqrt(m) u, of error;
+                // what they miss is left along Q and feeds ||Q^T Q - I|| into the indicator
+#pragma unroll 4
+                for (int j = 0; j < 64; ++j) {
+                    const float a = Xs[row][j];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float b = Vs[j][cq + q];
+                        const float p = a * b, pe = fmaf(a, b, -p);
+                        const float s2 = acc[q] + p, bb = s2 - acc[q];
+                        lo[q] += ((acc[q] - (s2 - bb)) + (p - bb)) + pe;
+                        acc[q] = s2;
+                    }
+                }
             }
         }
         const int64_t gr = r0 + row;
         if (gr < d.k) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) d.T[gr + (cq + q) * d.cap] = acc[q];
+            for (int q = 0; q < 4; ++q) d.T[gr + (cq + q) * d.cap] = acc[q] + lo[q];
         }
     }
 }

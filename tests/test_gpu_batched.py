@@ -95,3 +95,27 @@ def test_batched_autotuner_choice_is_used_and_graph_reused():
                 assert i.rank == k and torch.equal(Q, Qs) and torch.equal(B, Bs), cfg
     finally:
         qb.batched_set_plan(None)
+
+
+def test_batched_workload_every_matrix_meets_its_tolerance():
+    """The benchmark's batch itself (256 float32 matrices, m, n ~ U[256, 4096], sigma_j = s j^-2,
+    tol in {1e-2, 1e-3}): every converged matrix's true error is below its tolerance.  The stop
+    test keeps a 2 u ||A||^2 margin for the rounding of ||B||^2 (Theorem 3); it holds only while
+    Q stays orthonormal to ~u, since E misses tr(B^T (Q^T Q - I) B) of the true error."""
+    specs = synth.batched_specs(256, 1606)
+    mats = [synth.dense_from_spectrum_torch(s.m, s.n, synth.sigma_pow(min(s.m, s.n, 512), 2.0,
+                                                                      s.scale),
+                                            s.seed, "cuda", dtype=torch.float32) for s in specs]
+    res = qb.qb_ei_batched(mats, [s.tol for s in specs], seed=9402)
+    worst = 0.0
+    for t, (s, A, (Q, B, info)) in enumerate(zip(specs, mats, res)):
+        assert info.converged, (t, info)
+        A64 = A.double()
+        err = float(torch.linalg.norm(A64 - Q.double() @ B.double()) / torch.linalg.norm(A64))
+        worst = max(worst, err / s.tol)
+        assert err < s.tol, (t, s.m, s.n, s.tol, info.rank, err)
+        Qd = Q.double()
+        orth = float((Qd.T @ Qd - torch.eye(info.rank, dtype=torch.float64, device="cuda"))
+                     .abs().max())
+        assert orth <= 1e-6, (t, orth)
+    assert worst < 1.0
