@@ -382,6 +382,41 @@ def run_adjoint(torch, qb, dev, stream):
     return {"m": m, "n": n, "k": k, "forward_s": tf, "backward_s": tb}
 
 
+def run_paper_dense(torch, qb, dev, stream):
+    """The paper's dense runtime experiment (Sect. 5.1, Fig. 3): n x n with n = 32000, l = 200
+    columns, b = 20, P = 0 and 1.  The paper notes that the spectrum is immaterial for this
+    comparison; A = U diag(1/j) V^T with j <= 512 (U, V from seeded Gaussian QR).  Fixed rank: tol
+    0 and a rank cap of 200, so every run forms exactly 200 columns (status QB_NOT_CONVERGED).
+    Float64 path on the float64 A, mixed path on its bf16 hi + lo split.  The paper's times
+    (2 x 12-core Xeon E5-2630, MKL, float64, P = 0): randQB_FP 8.01 s, randQB_EI 13.47 s."""
+    import numpy as np
+
+    import synth
+    n = 32000
+    A64 = synth.dense_from_spectrum_torch(n, n, 1.0 / np.arange(1, 513), 3200, dev,
+                                          dtype=torch.float64)
+    hi, lo, norms = qb.quantize_bf16x2(A64)
+    out = {"n": n, "l": 200, "b": 20,
+           "paper_s": {"fp_P0": 8.01, "ei_P0": 13.47,
+                       "hardware": "2 x 12-core Intel Xeon E5-2630 @ 2.30 GHz, MKL, float64"}}
+    for prec in ("fp64", "mixed"):
+        for alg, f in (("ei", qb.qb_ei_dense), ("fp", qb.qb_fp_dense)):
+            for P in (0, 1):
+                if prec == "fp64":
+                    call = lambda: f(A64, 0.0, 20, P=P, seed=SEED_OMEGA, rank_cap=200)  # noqa: E731
+                else:
+                    call = lambda: f(hi, 0.0, 20, P=P, seed=SEED_OMEGA, rank_cap=200, a_lo=lo,  # noqa: E731
+                                     src_norm2=norms[0], prec="mixed")
+                _, _, info = call()
+                t = event_time(torch, call, 1 if prec == "fp64" else 3, stream)
+                out[f"{prec}_{alg}_P{P}"] = {"time_s": t, "rank": info.rank,
+                                             "passes": info.passes,
+                                             "err_rel_est": info.err_est / info.normA2 ** 0.5}
+    del A64, hi, lo
+    torch.cuda.empty_cache()
+    return out
+
+
 # ----------------------------------------------------------------------------- reference arm
 def run_reference(args, ws, rank):
     """The oracle's randQB_FP on the same workload, timed on the host cores: each timed step is one
@@ -556,6 +591,8 @@ def run_ours(args, ws, rank, local):
     adjoint = None if args.quick else run_adjoint(torch, qb, dev, stream)
     # ---- sparse: CSR 200000 x 100000, nnz ~ 2e7
     sparse = None if args.quick else run_sparse(torch, qb, dev, stream)
+    # ---- the paper's dense runtime shape: n = 32000, l = 200, b = 20
+    paper_dense = None if args.quick else run_paper_dense(torch, qb, dev, stream)
 
     # ---- end to end through the public API with host buffers (pinned)
     hi_h = hi.cpu().pin_memory()
@@ -632,6 +669,7 @@ def run_ours(args, ws, rank, local):
         "batched_ei_256": batched,
         "fixed_rank_adjoint_8192": adjoint,
         "sparse_csr_200000x100000": sparse,
+        "paper_dense_32000": paper_dense,
         "e2e": {"value": t_e2e, "unit": "s", "h2d_bytes_per_step": int(2 * hi.numel() * 2),
                 "d2h_bytes_per_step": int(d2h["b"])},
         "gpu_launches": gpu_launches,

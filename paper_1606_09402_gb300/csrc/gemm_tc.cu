@@ -235,7 +235,8 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
     uint64_t* empty = full + C::STAGES;
     uint64_t* tfull = empty + C::STAGES;   // [2]
     uint64_t* tempty = tfull + 2;          // [2]
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+    uint64_t* drain = tempty + 2;          // [1] MMA completion after a timed-out wait
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int G = gridDim.x, cta = blockIdx.x;
@@ -249,6 +250,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
             mbar_init(tfull + b, 1);
             mbar_init(tempty + b, 128);
         }
+        mbar_init(drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -277,12 +279,15 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
         SegWalk wk(sc, cta, G);
         Seg sg;
         constexpr uint32_t bytes = uint32_t(C::STAGE);
+        uint32_t armed = 0, armed_par = 0;   // stages with copies issued, and their phase parity
         while (ok && wk.next(sg)) {
             int r0, c0;
             unit_rc(sg.u, r0, c0);
             for (int kb = sg.k0; kb < sg.k1 && ok; ++kb) {
                 ok = mbar_wait(empty + stage, phase ^ 1, p.err);
                 if (!ok) break;
+                armed |= 1u << stage;
+                armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
                 mbar_expect_tx(full + stage, bytes);
                 unsigned char* st = smem + stage * C::STAGE;
                 const int k = kb * BK;
@@ -303,6 +308,11 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
                 if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
             }
         }
+        // a timed-out wait ends the loops early: let the bulk copies already issued land before
+        // the CTA exits (each wait bounded; a stage already consumed returns at once)
+        if (!ok)
+            for (int s2 = 0; s2 < C::STAGES; ++s2)
+                if (armed & (1u << s2)) mbar_wait(full + s2, (armed_par >> s2) & 1u, p.err);
     } else if (warp == 1 && lane == 0) {
         // ---------------------------------------------------------- MMA issuer
         constexpr uint32_t idesc = idesc_bf16(BN, TRANS);
@@ -349,6 +359,12 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
                 tphase[buf] ^= 1;
                 buf ^= 1;
             }
+        }
+        // after a timed-out wait, wait (bounded) for the MMAs already issued before the tensor
+        // memory is freed
+        if (!ok) {
+            tc_commit(drain);
+            mbar_wait(drain, 0, p.err);
         }
     } else if (warp >= 2) {
         // ---------------------------------------------------------- epilogue
@@ -490,7 +506,8 @@ k_tc_prec(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
     uint64_t* sempty = sfull + 2;          // [2]
     uint64_t* bfull = sempty + 2;          // [NSLOT] leading-product slots
     uint64_t* bempty = bfull + C::NSLOT;   // [NSLOT]
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bempty + C::NSLOT);
+    uint64_t* drain = bempty + C::NSLOT;   // [1] MMA completion after a timed-out wait
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int G = gridDim.x, cta = blockIdx.x;
@@ -507,6 +524,7 @@ k_tc_prec(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
             mbar_init(bfull + b, 1);
             mbar_init(bempty + b, PREC_EPI * 32);
         }
+        mbar_init(drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -531,11 +549,14 @@ k_tc_prec(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
         uint32_t phase = 0;
         SegWalk wk(sc, cta, G);
         Seg sg;
+        uint32_t armed = 0, armed_par = 0;   // stages with copies issued, and their phase parity
         while (ok && wk.next(sg)) {
             const int r0 = (sg.u / sc.tiles_n) * BM, c0 = (sg.u % sc.tiles_n) * BN;
             for (int kb = sg.k0; kb < sg.k1 && ok; ++kb) {
                 ok = mbar_wait(empty + stage, phase ^ 1, p.err);
                 if (!ok) break;
+                armed |= 1u << stage;
+                armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
                 mbar_expect_tx(full + stage, uint32_t(C::STAGE));
                 unsigned char* st = smem + stage * C::STAGE;
                 const int k = kb * BK;
@@ -558,6 +579,10 @@ k_tc_prec(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
                 if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
             }
         }
+        // a timed-out wait ends the loops early: let the bulk copies already issued land first
+        if (!ok)
+            for (int s2 = 0; s2 < C::STAGES; ++s2)
+                if (armed & (1u << s2)) mbar_wait(full + s2, (armed_par >> s2) & 1u, p.err);
     } else if (warp == 1 && lane == 0) {
         // ---------------------------------------------------------- MMA issuer
         constexpr uint32_t idesc = idesc_bf16(BN, TRANS);
@@ -631,6 +656,12 @@ k_tc_prec(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
                     if (++sbuf == C::NCHAIN) sbuf = 0;
                 }
             }
+        }
+        // after a timed-out wait, wait (bounded) for the MMAs already issued before the tensor
+        // memory is freed
+        if (!ok) {
+            tc_commit(drain);
+            mbar_wait(drain, 0, p.err);
         }
     } else if (warp >= 2) {
         // ---------------------------------------------------------- epilogue
