@@ -82,6 +82,20 @@ __device__ __forceinline__ float omega_f32(uint64_t seed, int64_t j, int64_t c) 
     return (c & 1) ? rho * s : rho * cs;
 }
 
+// Asynchronous 4-byte global -> shared copies (cp.async, any alignment): src_bytes 0 writes a
+// zero (used outside the matrix; src must still be a valid address).
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc, bool valid) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(gsrc),
+                 "r"(valid ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 #define FOR_ITEMS(plan)                                                             \
     for (int64_t item = blockIdx.x; item < (plan).prefix[(plan).count];           \
          item += gridDim.x)
@@ -102,47 +116,69 @@ __global__ void __launch_bounds__(NT) k_b_omega(BDesc* D, Plan p, uint64_t seed)
 
 // Y (slot of Q at column k) = A Omega; tile = 64 RT rows x b, thread = (RT rows, 4 columns).
 // RT is a tile shape the autotuner picks per batch shape (more rows per thread reuse each Omega
-// value RT times from shared memory).
+// value RT times from shared memory).  The k-tiles of A and Omega are staged with asynchronous
+// copies into two shared buffers, the next tile in flight while the current one is used.
+template <int RT>
+struct SkSmem {
+    float A[2][ROWS * RT][65];
+    float O[2][64][BB];
+};
+
 template <int RT>
 __global__ void __launch_bounds__(NT) k_b_sketch(BDesc* D, Plan p) {
-    __shared__ float As[ROWS * RT][65];
-    __shared__ float Os[64][BB];
+    extern __shared__ __align__(16) unsigned char sk_raw[];
+    SkSmem<RT>& sm = *reinterpret_cast<SkSmem<RT>*>(sk_raw);
     FOR_ITEMS(p) {
         const int t = find_matrix(p, item);
         BDesc& d = D[t];
         if (d.done) continue;
         const int64_t r0 = (item - p.prefix[t]) * (ROWS * RT);
         const int row = threadIdx.x >> 2, cq = (threadIdx.x & 3) * 4;
+        auto issue = [&](int buf, int64_t k0) {
+            for (int e = threadIdx.x; e < ROWS * RT * 64; e += NT) {
+                const int i = e / 64, j = e % 64;
+                const int64_t gr = r0 + i, gc = k0 + j;
+                const bool v = gr < d.m && gc < d.n;
+                cp_async4(&sm.A[buf][i][j], v ? d.A + gr * d.lda + gc : d.A, v);
+            }
+            for (int e = threadIdx.x; e < 64 * BB; e += NT) {
+                const int j = e % 64, c = e / 64;
+                const int64_t gc = k0 + j;
+                const bool v = gc < d.n;
+                cp_async4(&sm.O[buf][j][c], v ? d.Om + gc + c * d.n : d.Om, v);
+            }
+            cp_async_commit();
+        };
         float acc[RT][4];
 #pragma unroll
         for (int r = 0; r < RT; ++r)
 #pragma unroll
             for (int q = 0; q < 4; ++q) acc[r][q] = 0.f;
-        for (int64_t k0 = 0; k0 < d.n; k0 += 64) {
-            __syncthreads();
-            for (int e = threadIdx.x; e < ROWS * RT * 64; e += NT) {
-                const int i = e / 64, j = e % 64;
-                const int64_t gr = r0 + i, gc = k0 + j;
-                As[i][j] = (gr < d.m && gc < d.n) ? d.A[gr * d.lda + gc] : 0.f;
-            }
-            for (int e = threadIdx.x; e < 64 * BB; e += NT) {
-                const int j = e % 64, c = e / 64;
-                const int64_t gc = k0 + j;
-                Os[j][c] = gc < d.n ? d.Om[gc + c * d.n] : 0.f;
+        const int64_t nk = (d.n + 63) / 64;
+        __syncthreads();            // the buffers are free (previous item done with them)
+        issue(0, 0);
+        for (int64_t kt = 0; kt < nk; ++kt) {
+            const int buf = int(kt & 1);
+            if (kt + 1 < nk) {
+                issue(buf ^ 1, (kt + 1) * 64);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
             }
             __syncthreads();
 #pragma unroll 8
             for (int j = 0; j < 64; ++j) {
                 float o[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) o[q] = Os[j][cq + q];
+                for (int q = 0; q < 4; ++q) o[q] = sm.O[buf][j][cq + q];
 #pragma unroll
                 for (int r = 0; r < RT; ++r) {
-                    const float a = As[row + ROWS * r][j];
+                    const float a = sm.A[buf][row + ROWS * r][j];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) acc[r][q] = fmaf(a, o[q], acc[r][q]);
                 }
             }
+            __syncthreads();        // done reading buf before it is refilled
         }
 #pragma unroll
         for (int r = 0; r < RT; ++r) {
@@ -272,6 +308,8 @@ __global__ void __launch_bounds__(NT) k_b_update(BDesc* D, Plan p) {
 // (thread = one entry of the upper triangle), then the b x b Cholesky W = R^T R and R^-1 in
 // float64 by the first warp.  A pivot below 1e-12 of the largest is clamped (rank-deficient
 // block: its column comes out with norm <= 1 and adds ~0 to ||B||^2).
+// CHOL = false: only the Gram of the (final) block, stored symmetric in d.W for the indicator.
+template <bool CHOL>
 __global__ void __launch_bounds__(NT) k_b_gram_chol(BDesc* D, int count) {
     __shared__ double Ws[BB][BB + 1];
     __shared__ double Xs[BB][BB + 1];
@@ -300,6 +338,14 @@ __global__ void __launch_bounds__(NT) k_b_gram_chol(BDesc* D, int count) {
             Ws[a][c] = double(hi) + double(lo);
         }
         __syncthreads();
+        if (!CHOL) {
+            for (int e = threadIdx.x; e < BB * BB; e += NT) {
+                const int i = e % BB, j = e / BB;
+                d.W[e] = i <= j ? Ws[i][j] : Ws[j][i];
+            }
+            __syncthreads();
+            continue;
+        }
         if (threadIdx.x < 32) {
             const int lane = threadIdx.x;
             double dmax = 0.0;
@@ -368,11 +414,18 @@ __global__ void __launch_bounds__(NT) k_b_apply(BDesc* D, Plan p) {
 }
 
 // B_i (rows k..k+b of B) = Y^T A; tile = 64 CT columns of B; thread = (CT columns, 4 rows).
-// CT is the autotuned tile shape of this stage.
+// CT is the autotuned tile shape of this stage.  Row tiles of A and Y are staged with
+// asynchronous copies into two shared buffers (the next one in flight).
+template <int CT>
+struct BpSmem {
+    float A[2][64][64 * CT + 1];
+    float Y[2][64][BB];
+};
+
 template <int CT>
 __global__ void __launch_bounds__(NT) k_b_bpass(BDesc* D, Plan p) {
-    __shared__ float As[64][64 * CT + 1];
-    __shared__ float Ys[64][BB];
+    extern __shared__ __align__(16) unsigned char bp_raw[];
+    BpSmem<CT>& sm = *reinterpret_cast<BpSmem<CT>*>(bp_raw);
     FOR_ITEMS(p) {
         const int t = find_matrix(p, item);
         BDesc& d = D[t];
@@ -380,43 +433,71 @@ __global__ void __launch_bounds__(NT) k_b_bpass(BDesc* D, Plan p) {
         const int64_t c0 = (item - p.prefix[t]) * (64 * CT);
         const float* Y = d.Y;
         const int col = threadIdx.x & 63, rq = (threadIdx.x >> 6) * 4;
-        float acc[CT][4];
-#pragma unroll
-        for (int c = 0; c < CT; ++c)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[c][q] = 0.f;
-        for (int64_t r0 = 0; r0 < d.m; r0 += 64) {
-            __syncthreads();
+        auto issue = [&](int buf, int64_t r0) {
             for (int e = threadIdx.x; e < 64 * 64 * CT; e += NT) {
                 const int i = e / (64 * CT), j = e % (64 * CT);
                 const int64_t gr = r0 + i, gc = c0 + j;
-                As[i][j] = (gr < d.m && gc < d.n) ? d.A[gr * d.lda + gc] : 0.f;
+                const bool v = gr < d.m && gc < d.n;
+                cp_async4(&sm.A[buf][i][j], v ? d.A + gr * d.lda + gc : d.A, v);
             }
             for (int e = threadIdx.x; e < 64 * BB; e += NT) {
                 const int i = e % 64, c = e / 64;
                 const int64_t gr = r0 + i;
-                Ys[i][c] = gr < d.m ? Y[gr + c * d.m] : 0.f;
+                const bool v = gr < d.m;
+                cp_async4(&sm.Y[buf][i][c], v ? Y + gr + c * d.m : Y, v);
+            }
+            cp_async_commit();
+        };
+        // B_i feeds the indicator: E misses 2 <B, B - Q^T A> of the true error, so the sum over m
+        // rows is two-level (float32 within a 64-row tile, the tile sums into a float32 pair):
+        // ~u of error instead of the plain chain's ~sqrt(m) u
+        float acc[CT][4], hi[CT][4], lo[CT][4];
+#pragma unroll
+        for (int c = 0; c < CT; ++c)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[c][q] = hi[c][q] = lo[c][q] = 0.f;
+        const int64_t nr = (d.m + 63) / 64;
+        __syncthreads();
+        issue(0, 0);
+        for (int64_t rt = 0; rt < nr; ++rt) {
+            const int buf = int(rt & 1);
+            if (rt + 1 < nr) {
+                issue(buf ^ 1, (rt + 1) * 64);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
             }
             __syncthreads();
 #pragma unroll 8
             for (int i = 0; i < 64; ++i) {
                 float y[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) y[q] = Ys[i][rq + q];
+                for (int q = 0; q < 4; ++q) y[q] = sm.Y[buf][i][rq + q];
 #pragma unroll
                 for (int c = 0; c < CT; ++c) {
-                    const float a = As[i][col + 64 * c];
+                    const float a = sm.A[buf][i][col + 64 * c];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) acc[c][q] = fmaf(a, y[q], acc[c][q]);
                 }
             }
+            __syncthreads();
+#pragma unroll
+            for (int c = 0; c < CT; ++c)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {      // two-sum of the tile's sum into (hi, lo)
+                    const float v = acc[c][q];
+                    const float s2 = hi[c][q] + v, bb = s2 - hi[c][q];
+                    lo[c][q] += (hi[c][q] - (s2 - bb)) + (v - bb);
+                    hi[c][q] = s2;
+                    acc[c][q] = 0.f;
+                }
         }
 #pragma unroll
         for (int c = 0; c < CT; ++c) {
             const int64_t gc = c0 + col + 64 * c;
             if (gc < d.n) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) d.Bi[(rq + q) * d.n + gc] = acc[c][q];
+                for (int q = 0; q < 4; ++q) d.Bi[(rq + q) * d.n + gc] = hi[c][q] + lo[c][q];
             }
         }
     }
@@ -426,35 +507,41 @@ __global__ void __launch_bounds__(NT) k_b_bpass(BDesc* D, Plan p) {
 // new block to Q and rows to B, rank update; one CTA per matrix.
 __global__ void __launch_bounds__(NT) k_b_indicator(BDesc* D, int count, int* active,
                                                     int row_by_row) {
-    __shared__ double rn[BB];
+    __shared__ double G[BB][BB + 1];
     __shared__ int keep_s;
     for (int t = blockIdx.x; t < count; t += gridDim.x) {
         BDesc& d = D[t];
         if (d.done) continue;
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        for (int rr = warp; rr < BB; rr += NT / 32) {
+        // G = B_i B_i^T (float64), one warp per entry of the upper triangle
+        constexpr int PAIRS = BB * (BB + 1) / 2;
+        for (int pr = warp; pr < PAIRS; pr += NT / 32) {
+            int a = 0, q = pr;
+            while (q >= BB - a) { q -= BB - a; ++a; }
+            const int c = a + q;
             double s = 0.0;
-            for (int64_t c = lane; c < d.n; c += 32) {
-                const double v = d.Bi[rr * d.n + c];
-                s = fma(v, v, s);
-            }
+            for (int64_t x = lane; x < d.n; x += 32)
+                s = fma(double(d.Bi[a * d.n + x]), double(d.Bi[c * d.n + x]), s);
             for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-            if (lane == 0) rn[rr] = s;
+            if (lane == 0) { G[a][c] = s; G[c][a] = s; }
         }
         __syncthreads();
         if (threadIdx.x == 0) {
+            // Theorem 1 with a float32 Q: ||A - Q B||^2 = E + tr(B^T (Q^T Q - I) B) for B = Q^T A,
+            // so each kept row j of the block also adds (W_jj - 1) G_jj + 2 sum_{p<j} W_pj G_pj,
+            // W = Q_i^T Q_i (the final Gram of the block, exact-product sums; the terms between
+            // blocks are second order after the re-orthogonalisation)
             const int bi = int(d.cap - d.k < BB ? d.cap - d.k : int64_t(BB));
             double E = d.E;
             int keep = bi, stop = 0;
-            if (row_by_row) {
-                for (int j = 0; j < bi; ++j) {
-                    E -= rn[j];
-                    if (E < d.eps2) { keep = j + 1; stop = 1; break; }
-                }
-            } else {
-                for (int j = 0; j < bi; ++j) E -= rn[j];
-                stop = E < d.eps2;
+            for (int j = 0; j < bi; ++j) {
+                double corr = (d.W[j + j * BB] - 1.0) * G[j][j];
+                for (int pp = 0; pp < j; ++pp) corr += 2.0 * d.W[pp + j * BB] * G[pp][j];
+                E -= G[j][j];
+                E += corr;
+                if (row_by_row && E < d.eps2) { keep = j + 1; stop = 1; break; }
             }
+            if (!row_by_row) stop = E < d.eps2;
             d.E = E;
             keep_s = keep;
             if (stop) d.done = 1;
@@ -585,13 +672,31 @@ size_t batched_workspace(int32_t count, const qb_dense* As, int64_t cap_opt) {
 }
 
 namespace {
+// Raise a kernel's dynamic shared-memory limit once (per kernel, per process).
+template <int TAG>
+void allow_dyn_smem(const void* kern, size_t bytes) {
+    static std::once_flag once;
+    std::call_once(once, [&] {
+        QB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)));
+    });
+}
 void launch_sketch(int rt, unsigned g, cudaStream_t s, BDesc* D, const Plan& p1, const Plan& p2) {
-    if (rt == 2) k_b_sketch<2><<<g, NT, 0, s>>>(D, p2);
-    else k_b_sketch<1><<<g, NT, 0, s>>>(D, p1);
+    if (rt == 2) {
+        allow_dyn_smem<0>(reinterpret_cast<const void*>(k_b_sketch<2>), sizeof(SkSmem<2>));
+        k_b_sketch<2><<<g, NT, sizeof(SkSmem<2>), s>>>(D, p2);
+    } else {
+        allow_dyn_smem<1>(reinterpret_cast<const void*>(k_b_sketch<1>), sizeof(SkSmem<1>));
+        k_b_sketch<1><<<g, NT, sizeof(SkSmem<1>), s>>>(D, p1);
+    }
 }
 void launch_bpass(int ct, unsigned g, cudaStream_t s, BDesc* D, const Plan& p1, const Plan& p2) {
-    if (ct == 2) k_b_bpass<2><<<g, NT, 0, s>>>(D, p2);
-    else k_b_bpass<1><<<g, NT, 0, s>>>(D, p1);
+    if (ct == 2) {
+        allow_dyn_smem<2>(reinterpret_cast<const void*>(k_b_bpass<2>), sizeof(BpSmem<2>));
+        k_b_bpass<2><<<g, NT, sizeof(BpSmem<2>), s>>>(D, p2);
+    } else {
+        allow_dyn_smem<3>(reinterpret_cast<const void*>(k_b_bpass<1>), sizeof(BpSmem<1>));
+        k_b_bpass<1><<<g, NT, sizeof(BpSmem<1>), s>>>(D, p1);
+    }
 }
 
 // Time `reps` launches of fn on st (CUDA events), after one untimed launch.
@@ -792,10 +897,11 @@ extern "C" int32_t qb_ei_batched(int32_t count, const qb_dense* As, const double
                     k_b_update<<<gRows, NT, 0, s>>>(dD, pRows); L();
                 }
                 for (int q = 0; q < 2; ++q) {
-                    k_b_gram_chol<<<gMat, NT, 0, s>>>(dD, count); L();
+                    k_b_gram_chol<true><<<gMat, NT, 0, s>>>(dD, count); L();
                     k_b_apply<<<gRows, NT, 0, s>>>(dD, pRows); L();
                 }
             }
+            k_b_gram_chol<false><<<gMat, NT, 0, s>>>(dD, count); L();   // Q_i^T Q_i for E
             launch_bpass(cfg.ct, unsigned(cfg.gbp), s, dD, pCols, pCols2); L();
             k_b_indicator<<<gMat, NT, 0, s>>>(dD, count, flags, opts->row_by_row); L();
         };
