@@ -764,21 +764,32 @@ __global__ void k_row_norm2(const T* __restrict__ B, int64_t ldb, int64_t n, dou
 }
 
 // state[0] = E, state[1] = rows kept, state[2] = stop flag, state[3] = E before the block.
+// With Wq = Q_i^T Q_i and Gb = B_i B_i^T of the block (MAXB x MAXB, ld MAXB), row j also adds
+// (Wq_jj - 1) Gb_jj + 2 sum_{p<j} Wq_pj Gb_pj: for B = Q^T A, ||A - Q B||^2 = E +
+// tr(B^T (Q^T Q - I) B), and a float32 Q is orthonormal only to a few u, which on the leading
+// rows is a few u ||A||^2, as large as the stop margin.  (Terms between blocks are second order
+// after the re-orthogonalisation.)  rn[j] = Gb_jj then.
 __global__ void k_indicator(double* state, const double* rn, int rows, double eps2,
-                            int row_by_row) {
+                            int row_by_row, const double* Wq, const double* Gb) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     double E = state[0];
     state[3] = E;
     int keep = rows;
     int stop = 0;
+    auto row_term = [&](int j) {
+        if (!Wq) return rn[j];
+        double c = (Wq[j + j * MAXB] - 1.0) * Gb[j + j * MAXB];
+        for (int p = 0; p < j; ++p) c += 2.0 * Wq[p + j * MAXB] * Gb[p + j * MAXB];
+        return Gb[j + j * MAXB] - c;
+    };
     if (row_by_row) {
         for (int j = 0; j < rows; ++j) {
-            E -= rn[j];
+            E -= row_term(j);
             if (E < eps2) { keep = j + 1; stop = 1; break; }
         }
     } else {
         double s = 0.0;
-        for (int j = 0; j < rows; ++j) s += rn[j];
+        for (int j = 0; j < rows; ++j) s += row_term(j);
         E -= s;
         stop = E < eps2;
     }
@@ -925,8 +936,8 @@ void row_norm2(cudaStream_t st, bool f64, const void* B, int64_t ldb, int rows, 
 }
 
 void indicator(cudaStream_t st, double* state, const double* rn, int rows, double eps2,
-               int row_by_row) {
-    k_indicator<<<1, 32, 0, st>>>(state, rn, rows, eps2, row_by_row);
+               int row_by_row, const double* Wq, const double* Gb) {
+    k_indicator<<<1, 32, 0, st>>>(state, rn, rows, eps2, row_by_row, Wq, Gb);
     QB_LAUNCHED();
 }
 

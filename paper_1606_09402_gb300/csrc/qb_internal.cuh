@@ -219,9 +219,11 @@ void apply_rinv(cudaStream_t st, bool f64, void* P, int64_t ldp, int64_t m, int 
 // rn[j] = ||B(j, :)||^2 for rows j < rows of a row-major B (ld), float64 sums
 void row_norm2(cudaStream_t st, bool f64, const void* B, int64_t ldb, int rows, int64_t n,
                double* rn);
-// state = {E, keep, stop, ...}: E -= rn[j] row by row until E < eps2 (see Sect. 3.1)
+// state = {E, keep, stop, ...}: E -= rn[j] row by row until E < eps2 (see Sect. 3.1); with
+// Wq = Q_i^T Q_i and Gb = B_i B_i^T (MAXB x MAXB, nullable) the rows also carry the correction
+// for Q's departure from orthonormality, tr(B_i^T (Q_i^T Q_i - I) B_i), row by row
 void indicator(cudaStream_t st, double* state, const double* rn, int rows, double eps2,
-               int row_by_row);
+               int row_by_row, const double* Wq = nullptr, const double* Gb = nullptr);
 
 // ------------------------------------------------------------------------------------ CSR
 struct CsrDev {
