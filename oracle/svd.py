@@ -3,7 +3,8 @@
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).  With B = U~ S V~^T (LAPACK SVD of the
 small k x n B), A ~ Q B = (Q U~) S V~^T: the leading columns of Q U~ and V~ and the leading
 entries of S approximate the singular triplets of A.  Followed by randQB_FP at P = 0 (Algorithm 3,
-whose G and H take one sweep over a row-major A) this is the single-pass SVD of Sect. 5.3.
+whose G and H the paper forms in one sweep over a row-major A) this is the single-pass SVD of
+Sect. 5.3.
 """
 from __future__ import annotations
 

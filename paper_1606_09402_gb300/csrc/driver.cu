@@ -348,20 +348,10 @@ struct Ctx {
         }
     }
     struct Step { double E; int keep; int stop; };
-    // Qi: the block's final Q_i (m rows, ld ldq), for the mixed path's correction of E by
-    // tr(B_i^T (Q_i^T Q_i - I) B_i) (float32 Q is orthonormal to a few u only); the float64
-    // path subtracts the row norms as Algorithm 1 writes it.
-    Step indicator_step(const void* Bslot, int64_t ldb, int bi, int64_t n, double eps2, int rbr,
-                        const void* Qi = nullptr, int64_t ldq = 0, int64_t m = 0) {
+    Step indicator_step(const void* Bslot, int64_t ldb, int bi, int64_t n, double eps2, int rbr) {
         Scope sc(*this, PH_IND);
-        if (!f64 && Qi) {
-            gram(st, Qi, ldq, m, bi, false, ACC_DF, Racc, scr);       // W_q = Q_i^T Q_i
-            gram(st, Bslot, ldb, n, bi, false, ACC_DF, W, scr);       // G_b = B_i B_i^T
-            indicator(st, state, rn, bi, eps2, rbr, Racc, W);
-        } else {
-            row_norm2(st, f64, Bslot, ldb, bi, n, rn);
-            indicator(st, state, rn, bi, eps2, rbr);
-        }
+        row_norm2(st, f64, Bslot, ldb, bi, n, rn);
+        indicator(st, state, rn, bi, eps2, rbr);
         double h[3];
         QB_CUDA(cudaMemcpyAsync(h, state, sizeof h, cudaMemcpyDeviceToHost, st));
         QB_CUDA(cudaStreamSynchronize(st));
@@ -790,7 +780,7 @@ void run_ei(Ctx& c, AOp& A, const Plan& p, const qb_opts& o, Bufs& bf, void* Q, 
         A.apply_t(c, Y, ldq, bi, Bs, ldb, 3);
         out.passes += 1;
         c.shadow(k, bi, Y, ldq, m, Bs, ldb, n);
-        const Ctx::Step s = c.indicator_step(Bs, ldb, bi, n, eps2, o.row_by_row, Y, ldq, m);
+        const Ctx::Step s = c.indicator_step(Bs, ldb, bi, n, eps2, o.row_by_row);
         out.blocks += 1;
         out.E = s.E;
         k += s.keep;
@@ -908,7 +898,7 @@ void run_fp(Ctx& c, AOp& A, const Plan& p, const qb_opts& o, Bufs& bf, void* Q, 
                     c.copy_cols_(S, n, n, bi, Bs, ldb);
                 }
                 c.shadow(k, bi, Qi, ldq, m, Bs, ldb, n);
-                const Ctx::Step s = c.indicator_step(Bs, ldb, bi, n, eps2, o.row_by_row, Qi, ldq, m);
+                const Ctx::Step s = c.indicator_step(Bs, ldb, bi, n, eps2, o.row_by_row);
                 out.blocks += 1;
                 out.E = s.E;
                 k += s.keep;
