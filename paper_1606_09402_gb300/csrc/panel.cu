@@ -8,21 +8,21 @@ namespace {
 
 constexpr int LDS = MAXB + 1;
 
-// Cholesky of a bi x bi Gram W (bi <= 64) by one CTA: W = L D L^T (L unit lower), from which
-// R = D^1/2 L^T (W = R^T R) and R^-1 = L^-T D^-1/2.  Breakdown: a pivot d <= tau_rel * max_diag(W)
-// (or NaN) is replaced by tau_rel * max_diag (or the smallest normal number) and flags[1] is
-// raised; the column it produces has norm <= 1.  weak_rel > 0: *weak is set when some pivot
-// d_j < weak_rel * W[j][j] (a conditioning test).
+// Cholesky of a bi x bi Gram W (bi <= 64) by one CTA (at least CHOL_THREADS threads): W = R^T R
+// (upper R) factored in TF, R^-1 formed in TI.
+// Breakdown: a pivot d <= tau_rel * max_diag(W) (or NaN) is replaced by tau_rel * max_diag (or
+// the smallest normal number) and flags[1] is raised; the column it produces has norm <= 1.
 //
-// Blocked in two 32 x 32 blocks:
-//   W11 = L11 D1 L11^T                      one warp, Gaussian elimination by lane columns
-//   U   = L11^-1 W12                        (the eliminated rows 0..31 at columns 32..)
-//   S   = W22 - U^T D1^-1 U                 (Schur complement)
-//   S   = L22 D2 L22^T                      one warp
-//   L^-1 = [[L11^-1, 0], [-L22^-1 L21 L11^-1, L22^-1]],  L21 = (D1^-1 U)^T
-// Inside a warp the elimination needs no block barrier: lane c holds column c of the block and
-// of its L^-1, step j broadcasts row j (shuffles) and every lane updates its own column.  A block
-// narrower than 32 is padded with the identity (the pivot tests skip the padding).
+// One elimination sweep gives both factors: W = L D L^T (L unit lower), R = D^1/2 L^T and
+// R^-1 = L^-T D^-1/2.  Step j removes row j from the rows a > j of [W | I] (Gaussian elimination
+// without pivoting, multipliers m_a = W[j][a] / d_j read from the symmetric upper part), so the
+// trailing upper triangle becomes the Schur complement and the right half becomes L^-1.
+//
+// Work split: the 64 x 64 matrices are cut into 4 x 4 tiles held in registers.  Threads 0..135
+// own the upper tiles of W in row-major order (so the tiles that are finished form a prefix and
+// whole warps drop out), threads 160..295 the lower tiles of L^-1.  After step j the owners of
+// row j + 1 publish it (W in TF and in TI, L^-1 in TI) to shared memory, the owner of its diagonal
+// also its pivot; one barrier per step.
 constexpr int CLD = MAXB + 4;          // shared row stride: rows stay 16-byte aligned
 // Pivot test of the adaptive factorisation: a float32 factor is kept when every pivot keeps at
 // least this fraction of its column's squared norm (kappa of the panel below about 100, so the
@@ -30,172 +30,201 @@ constexpr int CLD = MAXB + 4;          // shared row stride: rows stay 16-byte a
 // second pass restores it); otherwise the panel is refactored in float64.
 constexpr double CHOL_WEAK_REL = 1e-4;
 constexpr int CHOL_THREADS = 320;
-constexpr unsigned FULLW = 0xffffffffu;
+constexpr int CHOL_TILES = 136;        // 4 x 4 tiles in a triangle of the 16 x 16 tile grid
+constexpr int CHOL_L0 = 160;           // first thread of the L^-1 tiles
 
 template <class TF, class TI>
-struct CholBuf {
-    TF (*S)[CLD];    // eliminated rows: S[j][c] = W'[j][c] for j <= c (W'[j][j] = d_j)
-    TI (*Li)[CLD];   // L^-1, lower part Li[a][c] (a >= c)
-    TF (*Z)[33];     // 32 x 32 scratch: the Schur complement
-    TI (*T)[33];     // 32 x 32 scratch: L21 L11^-1
+struct CholShared {
+    TF (*S)[CLD];    // rows W'[j][.] of the elimination as they are finished (TF)
+    TI (*Sf)[CLD];   // the same rows in TI (multipliers of the L^-1 update)
+    TI (*Li)[CLD];   // rows of L^-1 as they are finished
     TF* dpiv;        // [MAXB] pivots d_j
+    TF* invd;        // [MAXB] 1 / d_j
     TF* idiag;       // [MAXB] 1 / sqrt(d_j)
     TF* diag0;       // [MAXB] diagonal of W
     TF* dmax;        // [1]
-    int* weak;       // [1]
+    int* weak;       // [1] set when some pivot fell below weak_rel * W[j][j]
 };
 
-// One warp eliminates the block whose column c lane c holds in w (rows >= nb padded with the
-// identity).  Returns in w[i] (i < c) the eliminated rows W'[i][c] and in w[c] the pivot d_c, and
-// writes the multipliers L[c][j] = W'[j][c] / d_j (j < c) to Lm[c][j].
-template <class TF, class TI>
-__device__ __forceinline__ void warp_ldlt(TF (&w)[32], TI (*Lm)[33], int lane, int nb, TF d0c,
-                                          TF tau_dmax, TF floor_piv, TF weak_rel, bool& weak,
-                                          bool& brk) {
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-        TF d = __shfl_sync(FULLW, w[j], j);
-        if (j < nb) {
-            const TF d0 = __shfl_sync(FULLW, d0c, j);
-            if (!(d >= weak_rel * d0)) weak = true;
-            if (!(d > tau_dmax)) {
-                d = floor_piv;
-                weak = true;
-                brk = true;
-            }
-        }
-        if (lane == j) w[j] = d;
-        const TF inv = TF(1) / d;
-        const TF wjc = w[j];
-        if (lane > j) Lm[lane][j] = TI(wjc * inv);
-        // rows i > j: W[i][c] -= (W'[j][i] / d_j) W'[j][c]
-#pragma unroll
-        for (int i = j + 1; i < 32; ++i) {
-            const TF sj = __shfl_sync(FULLW, w[j], i) * inv;
-            w[i] = fma(-sj, wjc, w[i]);
-        }
-    }
+// tile t of a triangle of the 16 x 16 tile grid, row-major: (ti, tj) with ti <= tj
+__device__ __forceinline__ void tri_tile(int t, int& ti, int& tj) {
+    ti = 0;
+    while (t >= 16 - ti) { t -= 16 - ti; ++ti; }
+    tj = ti + t;
 }
 
-// load(i, j) returns W[i][j] for i <= j < bi.  On return (after a barrier) b.S, b.Li, b.dpiv,
-// b.idiag hold the factor (see CholBuf).
+template <class T>
+__device__ __forceinline__ void ld4(const T* p, T (&v)[4]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = p[q];
+}
+template <>
+__device__ __forceinline__ void ld4<float>(const float* p, float (&v)[4]) {
+    const float4 x = *reinterpret_cast<const float4*>(p);
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+}
+template <class T>
+__device__ __forceinline__ void st4(T* p, const T (&v)[4]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) p[q] = v[q];
+}
+template <>
+__device__ __forceinline__ void st4<float>(float* p, const float (&v)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+
+// load(i, j) returns W[i][j] for i <= j < bi.  On return (after a barrier) S rows hold W'[j][.]
+// in their upper part, dpiv / idiag the pivots, and an L^-1 tile owner (threadIdx.x in
+// [CHOL_L0, CHOL_L0 + 136)) has in l[r][q] the entry L^-1[4 lr + r][4 lc + q] (lr >= lc).
+// weak_rel > 0: *sh.weak is set when a pivot d_j < weak_rel * W[j][j] (a conditioning test).
+//
+// The tile updates need no per-element predicates: the multiplier of a row a <= j is zero, the
+// entries of row j beyond bi are zero, row j of L^-1 is zero beyond column j, and the lower part
+// of the diagonal tiles of W (which picks up rounding garbage) is never read.
 template <class TF, class TI, class Load>
-__device__ __noinline__ void chol_fast(int bi, double tau_rel, double weak_rel, int* flags,
-                                       Load load, CholBuf<TF, TI> b) {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int n1 = bi < 32 ? bi : 32, n2 = bi - n1;
-    if (warp == 0) {
-        const TF g0 = lane < bi ? TF(load(lane, lane)) : TF(0);
-        const TF g1 = 32 + lane < bi ? TF(load(32 + lane, 32 + lane)) : TF(0);
-        b.diag0[lane] = g0;
-        b.diag0[32 + lane] = g1;
-        TF mx = g0 > g1 ? g0 : g1;
+__device__ void chol_core(int bi, double tau_rel, double weak_rel, int* flags, Load load,
+                          CholShared<TF, TI> sh, TI (&l)[4][4], int& lr, int& lc) {
+    TF (*S)[CLD] = sh.S;
+    TI (*Sf)[CLD] = sh.Sf;
+    TI (*Li)[CLD] = sh.Li;
+    const int tid = threadIdx.x;
+    const bool wown = tid < CHOL_TILES;
+    const bool lown = tid >= CHOL_L0 && tid < CHOL_L0 + CHOL_TILES;
+    int wi = 0, wj = 0;                // W tile (rows 4 wi.., cols 4 wj..), wi <= wj
+    if (wown) tri_tile(tid, wi, wj);
+    lr = 0;
+    lc = 0;                            // L^-1 tile (rows 4 lr.., cols 4 lc..), lr >= lc
+    if (lown) tri_tile(tid - CHOL_L0, lc, lr);
+    TF w[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int a = 4 * wi + r, c = 4 * wj + q;
+            w[r][q] = (wown && a <= c && c < bi) ? TF(load(a, c)) : TF(0);
+            const int la = 4 * lr + r, lcc = 4 * lc + q;
+            l[r][q] = (lown && la == lcc && la < bi) ? TI(1) : TI(0);
+        }
+    if (wown) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            TI f[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) f[q] = TI(w[r][q]);
+            st4(&S[4 * wi + r][4 * wj], w[r]);
+            st4(&Sf[4 * wi + r][4 * wj], f);
+            if (wi == wj) sh.diag0[4 * wi + r] = w[r][r];
+        }
+    }
+    if (lown) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) st4(&Li[4 * lr + r][4 * lc], l[r]);
+    }
+    if (tid == 0) sh.weak[0] = 0;
+    __syncthreads();
+    if (tid < 32) {
+        TF m = TF(0);
+        for (int i = tid; i < bi; i += 32) m = sh.diag0[i] > m ? sh.diag0[i] : m;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            const TF v = __shfl_xor_sync(FULLW, mx, o);
-            mx = v > mx ? v : mx;
+            const TF v = __shfl_xor_sync(0xffffffffu, m, o);
+            m = v > m ? v : m;
         }
-        if (lane == 0) {
-            *b.dmax = mx;
-            *b.weak = 0;
-        }
+        if (tid == 0) sh.dmax[0] = m;
     }
     __syncthreads();
-    const TF dmax = *b.dmax;
+    const TF dmax = sh.dmax[0];
     const TF tiny = sizeof(TF) == 8 ? TF(2.2250738585072014e-308) : TF(1.1754943508222875e-38);
-    const TF tau_dmax = TF(tau_rel) * dmax;
-    const TF floor_piv = tau_dmax > tiny ? tau_dmax : tiny;
-    auto block = [&](int off, int nb, auto get) {
-        // warp 0 factors the nb x nb block at (off, off) whose entries get(i, c) returns
-        TF w[32];
-#pragma unroll
-        for (int i = 0; i < 32; ++i)
-            w[i] = (i < nb && lane < nb) ? get(i < lane ? i : lane, i < lane ? lane : i)
-                                         : (i == lane ? TF(1) : TF(0));
-        bool wk = false, brk = false;
-        warp_ldlt<TF, TI>(w, b.T, lane, nb, b.diag0[off + lane], tau_dmax, floor_piv,
-                          TF(weak_rel), wk, brk);
-        TF dl = TF(0);
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-            if (i <= lane) b.S[off + i][off + lane] = w[i];
-            if (i == lane) dl = w[i];      // a register select, not an indexed load
+    const TF floor_piv = TF(tau_rel) * dmax > tiny ? TF(tau_rel) * dmax : tiny;
+    // pivot of row j from its (updated) diagonal value; called by one thread
+    auto pivot = [&](int j, TF d) {
+        if (!(d >= TF(weak_rel) * sh.diag0[j])) sh.weak[0] = 1;
+        if (!(d > TF(tau_rel) * dmax)) {
+            d = floor_piv;
+            sh.weak[0] = 1;
+            if (flags) atomicOr(flags + 1, 1);
         }
-        b.dpiv[off + lane] = dl;
-        if (__any_sync(FULLW, wk) && lane == 0) *b.weak = 1;
-        if (__any_sync(FULLW, brk) && lane == 0 && flags) atomicOr(flags + 1, 1);
-        __syncwarp();
-        // column c of the block's L^-1 by forward substitution: x_i = [i == c] - sum_{p<i} L[i][p] x_p
-        TI x[32];
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-            TI acc = i == lane ? TI(1) : TI(0);
-#pragma unroll
-            for (int q = 0; q < i; ++q) acc = fma(-b.T[i][q], x[q], acc);
-            x[i] = acc;
-            if (i >= lane) b.Li[off + i][off + lane] = acc;
-        }
-        __syncwarp();
+        sh.dpiv[j] = d;
+        sh.invd[j] = TF(1) / d;
     };
-    if (warp == 0) block(0, n1, [&](int i, int c) { return TF(load(i, c)); });
+    if (tid == 0 && bi > 0) pivot(0, S[0][0]);
     __syncthreads();
-    if (n2 > 0) {
-        // U = L11^-1 W12 by forward substitution, one column per thread: W'[j][32 + c] =
-        // W[j][32 + c] - sum_{p < j} (W'[p][j] / d_p) W'[p][32 + c]
-        if (tid < n2) {
-            const int c = 32 + tid;
-            for (int j = 0; j < 32; ++j) {
-                TF u = TF(load(j, c));
-                for (int q = 0; q < j; ++q) u = fma(-(b.S[q][j] / b.dpiv[q]), b.S[q][c], u);
-                b.S[j][c] = u;
+    for (int j = 0; j < bi; ++j) {
+        const int jn = j + 1;
+        if (wown && 4 * wi + 3 > j) {
+            // W'[a][c] -= W'[j][a] * (W'[j][c] / d_j) for j < a <= c
+            const TF inv = sh.invd[j];
+            TF m[4], t[4];
+            ld4(&S[j][4 * wi], m);
+            ld4(&S[j][4 * wj], t);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) m[r] = 4 * wi + r > j ? m[r] : TF(0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) t[q] *= inv;
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) w[r][q] = fma(-m[r], t[q], w[r][q]);
+            if ((jn >> 2) == wi) {
+                const int r = jn & 3;
+                TF v[4];
+                TI f[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    v[q] = r == 0 ? w[0][q] : r == 1 ? w[1][q] : r == 2 ? w[2][q] : w[3][q];
+                    f[q] = TI(v[q]);
+                }
+                st4(&S[jn][4 * wj], v);
+                st4(&Sf[jn][4 * wj], f);
+                if (wi == wj && jn < bi) pivot(jn, r == 0 ? v[0] : r == 1 ? v[1] : r == 2 ? v[2] : v[3]);
             }
         }
-        __syncthreads();
-        // Schur complement Z = W22 - U^T D1^-1 U (upper part)
-        for (int e = tid; e < 32 * 32; e += blockDim.x) {
-            const int a = e % 32, c = e / 32;
-            if (a > c || c >= n2) continue;
-            TF z = TF(load(32 + a, 32 + c));
-            for (int j = 0; j < 32; ++j) z = fma(-(b.S[j][32 + a] / b.dpiv[j]), b.S[j][32 + c], z);
-            b.Z[a][c] = z;
+        if (lown && 4 * lr + 3 > j && 4 * lc <= j) {
+            // L^-1[a][c] -= (W'[j][a] / d_j) * L^-1[j][c] for a > j >= c
+            const TI inv = TI(sh.invd[j]);
+            TI m[4], u[4];
+            ld4(&Sf[j][4 * lr], m);
+            ld4(&Li[j][4 * lc], u);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) m[r] = 4 * lr + r > j ? m[r] * inv : TI(0);
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) l[r][q] = fma(-m[r], u[q], l[r][q]);
+        }
+        if (lown && (jn >> 2) == lr) {
+            const int r = jn & 3;
+            TI v[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                v[q] = r == 0 ? l[0][q] : r == 1 ? l[1][q] : r == 2 ? l[2][q] : l[3][q];
+            st4(&Li[jn][4 * lc], v);
         }
         __syncthreads();
-        if (warp == 0) block(32, n2, [&](int i, int c) { return b.Z[i][c]; });
-        __syncthreads();
-        // T = L21 L11^-1 with L21[a][j] = W'[j][32 + a] / d_j: T[a][c] = sum_{j >= c} L21[a][j] Linv11[j][c]
-        for (int e = tid; e < 32 * 32; e += blockDim.x) {
-            const int a = e / 32, c = e % 32;
-            TI t = TI(0);
-            if (a < n2)
-                for (int j = c; j < 32; ++j)
-                    t = fma(TI(b.S[j][32 + a] / b.dpiv[j]), b.Li[j][c], t);
-            b.T[a][c] = t;
-        }
-        __syncthreads();
-        // Linv21 = -Linv22 T
-        for (int e = tid; e < 32 * 32; e += blockDim.x) {
-            const int a = e / 32, c = e % 32;
-            if (a >= n2) continue;
-            TI v = TI(0);
-            for (int q = 0; q <= a; ++q) v = fma(b.Li[32 + a][32 + q], b.T[q][c], v);
-            b.Li[32 + a][c] = -v;
-        }
     }
-    if (tid < bi) b.idiag[tid] = TF(1) / sqrt(b.dpiv[tid]);
+    if (tid < bi) sh.idiag[tid] = TF(1) / sqrt(sh.dpiv[tid]);
     __syncthreads();
 }
 
 // Rinv = R^-1 (and R, R_acc <- R R_acc when given), all MAXB x MAXB column-major, from the state
-// chol_fast leaves.  X: MAXB x CLD scratch of TF.
+// chol_core leaves.  X: MAXB x CLD scratch of TF.
 template <class TF, class TI>
-__device__ void chol_outputs(int bi, TF (*S)[CLD], TI (*Li)[CLD], TF (*X)[CLD], const TF* dpiv,
-                             const TF* idiag, double* Rout, double* Rinv, double* Racc) {
+__device__ void chol_outputs(int bi, const TI (&l)[4][4], int lr, int lc, TF (*S)[CLD],
+                             TF (*X)[CLD], const TF* dpiv, const TF* idiag, double* Rout,
+                             double* Rinv, double* Racc) {
     const int tid = threadIdx.x;
     if (Rinv) {
-        // R^-1[c][a] = L^-1[a][c] / sqrt(d_a) for c <= a < bi, zero elsewhere
-        for (int e = tid; e < MAXB * MAXB; e += blockDim.x) {
-            const int c = e % MAXB, a = e / MAXB;
-            Rinv[e] = (a < bi && c <= a) ? double(Li[a][c] * TI(idiag[a])) : 0.0;
+        // R^-1[c][a] = L^-1[a][c] / sqrt(d_a); strictly lower tiles of R^-1 are zero
+        for (int e = tid; e < MAXB * MAXB; e += blockDim.x)
+            if (((e % MAXB) >> 2) > ((e / MAXB) >> 2)) Rinv[e] = 0.0;
+        if (tid >= CHOL_L0 && tid < CHOL_L0 + CHOL_TILES) {
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int a = 4 * lr + r, c = 4 * lc + q;
+                    Rinv[c + a * MAXB] = (a < bi && c < bi) ? double(l[r][q] * TI(idiag[a])) : 0.0;
+                }
         }
     }
     if (!Rout && !Racc) return;
@@ -236,7 +265,6 @@ __device__ void chol_outputs(int bi, TF (*S)[CLD], TI (*Li)[CLD], TF (*X)[CLD], 
 
 
 // Standalone factorisation.  ADAPT: float32 first, float64 (TF) when a pivot is weak.
-// Shared memory: S (TF), X (TF), Zr (TI-sized region holding the TF Schur block), Li (TI).
 template <class TF, class TI, bool ADAPT>
 __global__ void __launch_bounds__(CHOL_THREADS)
 k_chol(const double* __restrict__ W, int bi, double tau_rel, double* __restrict__ Rout,
@@ -244,36 +272,38 @@ k_chol(const double* __restrict__ W, int bi, double tau_rel, double* __restrict_
     extern __shared__ __align__(16) unsigned char chol_smem[];
     TF (*S)[CLD] = reinterpret_cast<TF (*)[CLD]>(chol_smem);
     TF (*X)[CLD] = reinterpret_cast<TF (*)[CLD]>(chol_smem + sizeof(TF) * MAXB * CLD);
-    unsigned char* zr = chol_smem + 2 * sizeof(TF) * MAXB * CLD;
+    TI (*Sf)[CLD] = reinterpret_cast<TI (*)[CLD]>(chol_smem + 2 * sizeof(TF) * MAXB * CLD);
     TI (*Li)[CLD] = reinterpret_cast<TI (*)[CLD]>(chol_smem + (2 * sizeof(TF) + sizeof(TI)) * MAXB * CLD);
     __shared__ TF dpiv[MAXB];
+    __shared__ TF invd[MAXB];
     __shared__ TF idiag[MAXB];
     __shared__ TF diag0[MAXB];
     __shared__ TF dmax_s;
     __shared__ int weak;
     auto ldw = [&](int i, int j) { return W[i + j * MAXB]; };
+    TI l[4][4];
+    int lr, lc;
     if (ADAPT) {
-        // float32 attempt in the same shared memory (float views; TI is float here)
+        // float32 attempt in the same shared memory (float views of S, X; TI is float here)
         float (*Sg)[CLD] = reinterpret_cast<float (*)[CLD]>(chol_smem);
         float (*Xg)[CLD] = reinterpret_cast<float (*)[CLD]>(chol_smem + sizeof(float) * MAXB * CLD);
-        __shared__ float fpiv[MAXB], fidiag[MAXB], fdiag0[MAXB], fdmax;
-        chol_fast<float, float>(bi, tau_rel, CHOL_WEAK_REL, nullptr, ldw,
-                                CholBuf<float, float>{Sg, reinterpret_cast<float (*)[CLD]>(Li),
-                                                      reinterpret_cast<float (*)[33]>(zr),
-                                                      reinterpret_cast<float (*)[33]>(X),
-                                                      fpiv, fidiag, fdiag0, &fdmax, &weak});
+        __shared__ float fpiv[MAXB], finvd[MAXB], fidiag[MAXB], fdiag0[MAXB], fdmax;
+        float lf[4][4];
+        chol_core<float, float>(bi, tau_rel, CHOL_WEAK_REL, nullptr, ldw,
+                                CholShared<float, float>{Sg, reinterpret_cast<float (*)[CLD]>(Sf),
+                                                         reinterpret_cast<float (*)[CLD]>(Li),
+                                                         fpiv, finvd, fidiag, fdiag0, &fdmax, &weak},
+                                lf, lr, lc);
         if (!weak) {
-            chol_outputs<float, float>(bi, Sg, reinterpret_cast<float (*)[CLD]>(Li), Xg, fpiv,
-                                       fidiag, Rout, Rinv, Racc);
+            chol_outputs<float, float>(bi, lf, lr, lc, Sg, Xg, fpiv, fidiag, Rout, Rinv, Racc);
             return;
         }
         __syncthreads();
     }
-    chol_fast<TF, TI>(bi, tau_rel, 0.0, flags, ldw,
-                      CholBuf<TF, TI>{S, Li, reinterpret_cast<TF (*)[33]>(zr),
-                                      reinterpret_cast<TI (*)[33]>(X), dpiv, idiag, diag0, &dmax_s,
-                                      &weak});
-    chol_outputs<TF, TI>(bi, S, Li, X, dpiv, idiag, Rout, Rinv, Racc);
+    chol_core<TF, TI>(bi, tau_rel, 0.0, flags, ldw,
+                      CholShared<TF, TI>{S, Sf, Li, dpiv, invd, idiag, diag0, &dmax_s, &weak}, l,
+                      lr, lc);
+    chol_outputs<TF, TI>(bi, l, lr, lc, S, X, dpiv, idiag, Rout, Rinv, Racc);
 }
 
 // ---------------------------------------------------------------- fused CholeskyQR (float32 panel)
@@ -393,8 +423,8 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) k_cholqr_coop(CoopArgs p) {
             Pc[i][j] = p.rinv_prev ? float(p.rinv_prev[e]) : (i == j ? 1.f : 0.f);
         }
     }
-    __shared__ float fpiv[MAXB], fidiag[MAXB], fdiag0[MAXB], fdmax;
-    __shared__ double dpiv[MAXB], didiag[MAXB], ddiag0[MAXB], ddmax;
+    __shared__ float fpiv[MAXB], finvd[MAXB], fidiag[MAXB], fdiag0[MAXB], fdmax;
+    __shared__ double dpiv[MAXB], dinvd[MAXB], didiag[MAXB], ddiag0[MAXB], ddmax;
     __shared__ int weak_s;
     __shared__ double red[16][32];
     const int tid = threadIdx.x;
@@ -539,14 +569,15 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) k_cholqr_coop(CoopArgs p) {
         if (!coop_sync(p.bar, p.err)) return;
         reduce();
         if (!coop_sync(p.bar, p.err)) return;
-        // ---- every CTA factors the summed Gram (Schur block in the Sf region, L21 L11^-1 in Rs,
-        // which is written only after the factor)
+        // ---- every CTA factors the summed Gram
+        float l[4][4];
+        int lr, lc;
         float (*Sfl)[CLD] = reinterpret_cast<float (*)[CLD]>(sreg);
-        chol_fast<float, float>(bi, p.tau, PRECISE ? CHOL_WEAK_REL : 0.0,
+        chol_core<float, float>(bi, p.tau, PRECISE ? CHOL_WEAK_REL : 0.0,
                                 (cta == 0 && !PRECISE) ? p.flags : nullptr, ldw,
-                                CholBuf<float, float>{Sfl, Li, reinterpret_cast<float (*)[33]>(Sf),
-                                                      reinterpret_cast<float (*)[33]>(Rs), fpiv,
-                                                      fidiag, fdiag0, &fdmax, &weak_s});
+                                CholShared<float, float>{Sfl, Sf, Li, fpiv, finvd, fidiag, fdiag0,
+                                                         &fdmax, &weak_s},
+                                l, lr, lc);
         bool dbl = false;
         if (PRECISE && weak_s) {
             // ill-conditioned panel: exact-product Gram, float64 factor
@@ -556,17 +587,25 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) k_cholqr_coop(CoopArgs p) {
             reduce();
             if (!coop_sync(p.bar, p.err)) return;
             double (*Sd)[CLD] = reinterpret_cast<double (*)[CLD]>(sreg);
-            chol_fast<double, float>(bi, p.tau, 0.0, cta == 0 ? p.flags : nullptr, ldw,
-                                     CholBuf<double, float>{Sd, Li,
-                                                            reinterpret_cast<double (*)[33]>(Sf),
-                                                            reinterpret_cast<float (*)[33]>(Rs),
-                                                            dpiv, didiag, ddiag0, &ddmax, &weak_s});
+            chol_core<double, float>(bi, p.tau, 0.0, cta == 0 ? p.flags : nullptr, ldw,
+                                     CholShared<double, float>{Sd, Sf, Li, dpiv, dinvd, didiag,
+                                                               ddiag0, &ddmax, &weak_s},
+                                     l, lr, lc);
         }
-        // R^-1[c][a] = L^-1[a][c] / sqrt(d_a) (c <= a < bi), zero elsewhere
+        // R^-1[c][a] = L^-1[a][c] / sqrt(d_a); strictly lower tiles are zero
         for (int e = tid; e < MAXB * MAXB; e += COOP_THREADS) {
-            const int c = e % MAXB, a = e / MAXB;
-            const float id = dbl ? float(didiag[a]) : fidiag[a];
-            Rs[c][a] = (a < bi && c <= a) ? Li[a][c] * id : 0.f;
+            const int i = e % MAXB, jj = e / MAXB;
+            if ((i >> 2) > (jj >> 2)) Rs[i][jj] = 0.f;
+        }
+        if (tid >= CHOL_L0 && tid < CHOL_L0 + CHOL_TILES) {
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int a = 4 * lr + r, c = 4 * lc + q;
+                    const float id = dbl ? float(didiag[a < MAXB ? a : 0]) : fidiag[a < MAXB ? a : 0];
+                    Rs[c][a] = (a < bi && c < bi) ? l[r][q] * id : 0.f;
+                }
         }
         __syncthreads();
         if (chain) {
