@@ -120,8 +120,8 @@ __global__ void __launch_bounds__(NT) k_b_omega(BDesc* D, Plan p, uint64_t seed)
 // copies into two shared buffers, the next tile in flight while the current one is used.
 template <int RT>
 struct SkSmem {
+    alignas(16) float O[2][64][BB];    // first: its rows are read as float4
     float A[2][ROWS * RT][65];
-    float O[2][64][BB];
 };
 
 template <int RT>
@@ -134,19 +134,24 @@ __global__ void __launch_bounds__(NT) k_b_sketch(BDesc* D, Plan p) {
         if (d.done) continue;
         const int64_t r0 = (item - p.prefix[t]) * (ROWS * RT);
         const int row = threadIdx.x >> 2, cq = (threadIdx.x & 3) * 4;
+        // copies: a warp takes 32 consecutive columns of a row (coalesced); thread t walks the
+        // rows t/64 + 4q of column t%64 of the A tile and the columns t/64 + 4q of row t%64 of
+        // the Omega tile with a fixed pointer step
+        const int cj = threadIdx.x & 63, ci = threadIdx.x >> 6;
         auto issue = [&](int buf, int64_t k0) {
-            for (int e = threadIdx.x; e < ROWS * RT * 64; e += NT) {
-                const int i = e / 64, j = e % 64;
-                const int64_t gr = r0 + i, gc = k0 + j;
-                const bool v = gr < d.m && gc < d.n;
-                cp_async4(&sm.A[buf][i][j], v ? d.A + gr * d.lda + gc : d.A, v);
+            const bool cok = k0 + cj < d.n;
+            const int64_t rleft = d.m - (r0 + ci);     // rows of this thread's walk inside A
+            const float* src = d.A + (rleft > 0 ? (r0 + ci) * d.lda : 0) + k0 + cj;
+            float* dst = &sm.A[buf][ci][cj];
+#pragma unroll
+            for (int q = 0; q < ROWS * RT / 4; ++q) {
+                const bool v = cok && 4 * q < rleft;
+                cp_async4(dst + q * 4 * 65, v ? src + q * 4 * d.lda : d.A, v);
             }
-            for (int e = threadIdx.x; e < 64 * BB; e += NT) {
-                const int j = e % 64, c = e / 64;
-                const int64_t gc = k0 + j;
-                const bool v = gc < d.n;
-                cp_async4(&sm.O[buf][j][c], v ? d.Om + gc + c * d.n : d.Om, v);
-            }
+            const float* osrc = d.Om + int64_t(ci) * d.n + k0 + cj;
+#pragma unroll
+            for (int q = 0; q < BB / 4; ++q)
+                cp_async4(&sm.O[buf][cj][ci + 4 * q], cok ? osrc + q * 4 * d.n : d.Om, cok);
             cp_async_commit();
         };
         float acc[RT][4];
@@ -168,9 +173,8 @@ __global__ void __launch_bounds__(NT) k_b_sketch(BDesc* D, Plan p) {
             __syncthreads();
 #pragma unroll 8
             for (int j = 0; j < 64; ++j) {
-                float o[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) o[q] = sm.O[buf][j][cq + q];
+                const float4 o4 = *reinterpret_cast<const float4*>(&sm.O[buf][j][cq]);
+                const float o[4] = {o4.x, o4.y, o4.z, o4.w};
 #pragma unroll
                 for (int r = 0; r < RT; ++r) {
                     const float a = sm.A[buf][row + ROWS * r][j];
@@ -418,8 +422,8 @@ __global__ void __launch_bounds__(NT) k_b_apply(BDesc* D, Plan p) {
 // asynchronous copies into two shared buffers (the next one in flight).
 template <int CT>
 struct BpSmem {
+    alignas(16) float Y[2][64][BB];    // first: its rows are read as float4
     float A[2][64][64 * CT + 1];
-    float Y[2][64][BB];
 };
 
 template <int CT>
@@ -433,19 +437,29 @@ __global__ void __launch_bounds__(NT) k_b_bpass(BDesc* D, Plan p) {
         const int64_t c0 = (item - p.prefix[t]) * (64 * CT);
         const float* Y = d.Y;
         const int col = threadIdx.x & 63, rq = (threadIdx.x >> 6) * 4;
+        // copies: a warp takes 32 consecutive columns of a row (coalesced); thread t walks the
+        // rows t/64 + 4q of columns t%64 + 64c of the A tile and the columns t/64 + 4q of row t%64
+        // of the Y tile with a fixed pointer step
+        const int cj = threadIdx.x & 63, ci = threadIdx.x >> 6;
         auto issue = [&](int buf, int64_t r0) {
-            for (int e = threadIdx.x; e < 64 * 64 * CT; e += NT) {
-                const int i = e / (64 * CT), j = e % (64 * CT);
-                const int64_t gr = r0 + i, gc = c0 + j;
-                const bool v = gr < d.m && gc < d.n;
-                cp_async4(&sm.A[buf][i][j], v ? d.A + gr * d.lda + gc : d.A, v);
+            const int64_t rleft = d.m - (r0 + ci);
+            const float* src = d.A + (rleft > 0 ? (r0 + ci) * d.lda : 0) + c0 + cj;
+            float* dst = &sm.A[buf][ci][cj];
+#pragma unroll
+            for (int c = 0; c < CT; ++c) {
+                const bool cok = c0 + cj + 64 * c < d.n;
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const bool v = cok && 4 * q < rleft;
+                    cp_async4(dst + q * 4 * (64 * CT + 1) + 64 * c,
+                              v ? src + q * 4 * d.lda + 64 * c : d.A, v);
+                }
             }
-            for (int e = threadIdx.x; e < 64 * BB; e += NT) {
-                const int i = e % 64, c = e / 64;
-                const int64_t gr = r0 + i;
-                const bool v = gr < d.m;
-                cp_async4(&sm.Y[buf][i][c], v ? Y + gr + c * d.m : Y, v);
-            }
+            const bool yok = r0 + cj < d.m;
+            const float* ysrc = Y + int64_t(ci) * d.m + r0 + cj;
+#pragma unroll
+            for (int q = 0; q < BB / 4; ++q)
+                cp_async4(&sm.Y[buf][cj][ci + 4 * q], yok ? ysrc + q * 4 * d.m : Y, yok);
             cp_async_commit();
         };
         // B_i feeds the indicator: E misses 2 <B, B - Q^T A> of the true error, so the sum over m
@@ -470,9 +484,8 @@ __global__ void __launch_bounds__(NT) k_b_bpass(BDesc* D, Plan p) {
             __syncthreads();
 #pragma unroll 8
             for (int i = 0; i < 64; ++i) {
-                float y[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) y[q] = sm.Y[buf][i][rq + q];
+                const float4 y4 = *reinterpret_cast<const float4*>(&sm.Y[buf][i][rq]);
+                const float y[4] = {y4.x, y4.y, y4.z, y4.w};
 #pragma unroll
                 for (int c = 0; c < CT; ++c) {
                     const float a = sm.A[buf][i][col + 64 * c];
