@@ -1,6 +1,7 @@
 // CholeskyQR panel pieces (b x b float64 Cholesky, triangular inverse, R accumulation, applying
 // R^-1 to an m x b panel) and the Frobenius-norm indicator of Theorem 1 with the row-by-row
 // stopping rule of Sect. 3.1.
+#include <type_traits>
 #include "qb_internal.cuh"
 
 namespace qb {
@@ -20,9 +21,12 @@ constexpr int LDS = MAXB + 1;
 //
 // Work split: the 64 x 64 matrices are cut into 4 x 4 tiles held in registers.  Threads 0..135
 // own the upper tiles of W in row-major order (so the tiles that are finished form a prefix and
-// whole warps drop out), threads 160..295 the lower tiles of L^-1.  After step j the owners of
-// row j + 1 publish it (W in TF and in TI, L^-1 in TI) to shared memory, the owner of its diagonal
-// also its pivot; one barrier per step.
+// whole warps drop out), threads 160..295 the lower tiles of L^-1.  The elimination takes two
+// pivots per barrier: before the double step (j, j + 1) row j is final in shared memory and row
+// j + 1 waits there for the update by row j; every thread applies that update itself to the
+// entries of row j + 1 it needs (the same arithmetic its owner does), so the two rank-one updates
+// of a tile run back to back.  The owners then publish rows j + 1, j + 2 (final) and j + 3
+// (pending), the owner of the diagonal of row j + 2 also its pivot.
 constexpr int CLD = MAXB + 4;          // shared row stride: rows stay 16-byte aligned
 // Pivot test of the adaptive factorisation: a float32 factor is kept when every pivot keeps at
 // least this fraction of its column's squared norm (kappa of the panel below about 100, so the
@@ -36,7 +40,7 @@ constexpr int CHOL_L0 = 160;           // first thread of the L^-1 tiles
 template <class TF, class TI>
 struct CholShared {
     TF (*S)[CLD];    // rows W'[j][.] of the elimination as they are finished (TF)
-    TI (*Sf)[CLD];   // the same rows in TI (multipliers of the L^-1 update)
+    TI (*Sf)[CLD];   // scratch of MAXB rows of TI: holds the two-slot rings of pending rows
     TI (*Li)[CLD];   // rows of L^-1 as they are finished
     TF* dpiv;        // [MAXB] pivots d_j
     TF* invd;        // [MAXB] 1 / d_j
@@ -81,12 +85,18 @@ __device__ __forceinline__ void st4<float>(float* p, const float (&v)[4]) {
 // The tile updates need no per-element predicates: the multiplier of a row a <= j is zero, the
 // entries of row j beyond bi are zero, row j of L^-1 is zero beyond column j, and the lower part
 // of the diagonal tiles of W (which picks up rounding garbage) is never read.
+// correctly rounded reciprocal (the same value as 1 / x in IEEE division)
+__device__ __forceinline__ float rcp_rn(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp_rn(double x) { return __drcp_rn(x); }
+
 template <class TF, class TI, class Load>
 __device__ void chol_core(int bi, double tau_rel, double weak_rel, int* flags, Load load,
                           CholShared<TF, TI> sh, TI (&l)[4][4], int& lr, int& lc) {
     TF (*S)[CLD] = sh.S;
-    TI (*Sf)[CLD] = sh.Sf;
     TI (*Li)[CLD] = sh.Li;
+    // rings of the pending row (j + 1 before its update by row j): W in TF, L^-1 in TI
+    TF (*PW)[CLD] = reinterpret_cast<TF (*)[CLD]>(sh.Sf);
+    TI (*PL)[CLD] = reinterpret_cast<TI (*)[CLD]>(reinterpret_cast<TF*>(sh.Sf) + 2 * CLD);
     const int tid = threadIdx.x;
     const bool wown = tid < CHOL_TILES;
     const bool lown = tid >= CHOL_L0 && tid < CHOL_L0 + CHOL_TILES;
@@ -105,20 +115,19 @@ __device__ void chol_core(int bi, double tau_rel, double weak_rel, int* flags, L
             const int la = 4 * lr + r, lcc = 4 * lc + q;
             l[r][q] = (lown && la == lcc && la < bi) ? TI(1) : TI(0);
         }
+    // initial state: every row of W and L^-1 in shared memory, row 1 also in ring slot 0
     if (wown) {
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-            TI f[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) f[q] = TI(w[r][q]);
             st4(&S[4 * wi + r][4 * wj], w[r]);
-            st4(&Sf[4 * wi + r][4 * wj], f);
             if (wi == wj) sh.diag0[4 * wi + r] = w[r][r];
         }
+        if (wi == 0) st4(&PW[0][4 * wj], w[1]);
     }
     if (lown) {
 #pragma unroll
         for (int r = 0; r < 4; ++r) st4(&Li[4 * lr + r][4 * lc], l[r]);
+        if (lr == 0) st4(&PL[0][4 * lc], l[1]);
     }
     if (tid == 0) sh.weak[0] = 0;
     __syncthreads();
@@ -136,71 +145,129 @@ __device__ void chol_core(int bi, double tau_rel, double weak_rel, int* flags, L
     const TF dmax = sh.dmax[0];
     const TF tiny = sizeof(TF) == 8 ? TF(2.2250738585072014e-308) : TF(1.1754943508222875e-38);
     const TF floor_piv = TF(tau_rel) * dmax > tiny ? TF(tau_rel) * dmax : tiny;
-    // pivot of row j from its (updated) diagonal value; called by one thread
-    auto pivot = [&](int j, TF d) {
+    const TF tau_dmax = TF(tau_rel) * dmax;
+    // pivot of row j from its (updated) diagonal value d: the value used (d, or the floor when d
+    // does not exceed tau_rel * dmax) and, by the calling thread, the weak / breakdown flags
+    auto piv_value = [&](TF d) { return d > tau_dmax ? d : floor_piv; };
+    auto pivot = [&](int j, TF d, bool inv) {
         if (!(d >= TF(weak_rel) * sh.diag0[j])) sh.weak[0] = 1;
-        if (!(d > TF(tau_rel) * dmax)) {
-            d = floor_piv;
+        if (!(d > tau_dmax)) {
             sh.weak[0] = 1;
             if (flags) atomicOr(flags + 1, 1);
         }
+        d = piv_value(d);
         sh.dpiv[j] = d;
-        sh.invd[j] = TF(1) / d;
+        if (inv) sh.invd[j] = rcp_rn(d);
     };
-    if (tid == 0 && bi > 0) pivot(0, S[0][0]);
+    if (tid == 0 && bi > 0) pivot(0, S[0][0], true);
     __syncthreads();
-    for (int j = 0; j < bi; ++j) {
-        const int jn = j + 1;
-        if (wown && 4 * wi + 3 > j) {
-            // W'[a][c] -= W'[j][a] * (W'[j][c] / d_j) for j < a <= c
-            const TF inv = sh.invd[j];
-            TF m[4], t[4];
-            ld4(&S[j][4 * wi], m);
-            ld4(&S[j][4 * wj], t);
+    // double step (j, k = j + 1) with j = j0 + JJ, j0 a multiple of 4 and JJ in {0, 2} fixed at
+    // compile time, so the rows a tile publishes and masks are known statically.  Row k's update
+    // by row j, vk(x) = W'[k][x] - W'[j][k] (W'[j][x] / d_j), is the arithmetic its owner does.
+    auto dstep = [&](auto jj_c, int j0) {
+        constexpr int JJ = decltype(jj_c)::value;
+        constexpr int SLOT = JJ >> 1;                 // ring slot of the pending row k
+        const int j = j0 + JJ, k = j + 1, tr = j0 >> 2;
+        const bool two = k < bi;
+        const TF invj = sh.invd[j];
+        const TF sjk = two ? S[j][k] : TF(0);
+        TF invk = TF(0);
+        if (two) {
+            const TF dk = fma(-sjk, sjk * invj, PW[SLOT][k]);
+            invk = rcp_rn(piv_value(dk));
+            if (tid == 0) pivot(k, dk, false);       // 1 / d_k is not read from shared memory
+        }
+        if (wown && wi >= tr) {
+            // W'[a][c] -= W'[j][a] (W'[j][c] / d_j), then -= W'[k][a] (W'[k][c] / d_k), j < a <= c
+            const bool dr = wi == tr;                 // the tile holds rows j and k
+            TF mj[4], tj[4];
+            ld4(&S[j][4 * wi], mj);
+            ld4(&S[j][4 * wj], tj);
 #pragma unroll
-            for (int r = 0; r < 4; ++r) m[r] = 4 * wi + r > j ? m[r] : TF(0);
+            for (int q = 0; q < 4; ++q) tj[q] *= invj;
+            const bool second = two && (!dr || JJ == 0);
+            TF mk[4], tk[4];
+            if (second) {
+                TF pr[4], pc[4];
+                ld4(&PW[SLOT][4 * wi], pr);
+                ld4(&PW[SLOT][4 * wj], pc);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) t[q] *= inv;
+                for (int r = 0; r < 4; ++r) {
+                    mk[r] = fma(-sjk, mj[r] * invj, pr[r]);
+                    if (r <= JJ + 1) mk[r] = dr ? TF(0) : mk[r];
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) tk[q] = fma(-sjk, tj[q], pc[q]) * invk;
+            }
+#pragma unroll
+            for (int r = 0; r <= JJ; ++r) mj[r] = dr ? TF(0) : mj[r];
 #pragma unroll
             for (int r = 0; r < 4; ++r)
 #pragma unroll
-                for (int q = 0; q < 4; ++q) w[r][q] = fma(-m[r], t[q], w[r][q]);
-            if ((jn >> 2) == wi) {
-                const int r = jn & 3;
-                TF v[4];
-                TI f[4];
+                for (int q = 0; q < 4; ++q) w[r][q] = fma(-mj[r], tj[q], w[r][q]);
+            if (second) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    v[q] = r == 0 ? w[0][q] : r == 1 ? w[1][q] : r == 2 ? w[2][q] : w[3][q];
-                    f[q] = TI(v[q]);
-                }
-                st4(&S[jn][4 * wj], v);
-                st4(&Sf[jn][4 * wj], f);
-                if (wi == wj && jn < bi) pivot(jn, r == 0 ? v[0] : r == 1 ? v[1] : r == 2 ? v[2] : v[3]);
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) w[r][q] = fma(-mk[r], tk[q], w[r][q]);
             }
         }
-        if (lown && 4 * lr + 3 > j && 4 * lc <= j) {
-            // L^-1[a][c] -= (W'[j][a] / d_j) * L^-1[j][c] for a > j >= c
-            const TI inv = TI(sh.invd[j]);
+        if (lown && lr >= tr && lc <= tr) {
+            // L^-1[a][c] -= (W'[j][a] / d_j) L^-1[j][c], then the same with row k, a > j >= c
+            const bool dr = lr == tr;
+            const TI ij = TI(invj);
             TI m[4], u[4];
-            ld4(&Sf[j][4 * lr], m);
+            TF sr[4];
+            ld4(&S[j][4 * lr], sr);
             ld4(&Li[j][4 * lc], u);
 #pragma unroll
-            for (int r = 0; r < 4; ++r) m[r] = 4 * lr + r > j ? m[r] * inv : TI(0);
+            for (int r = 0; r < 4; ++r) m[r] = TI(sr[r]) * ij;
+#pragma unroll
+            for (int r = 0; r <= JJ; ++r) m[r] = dr ? TI(0) : m[r];
 #pragma unroll
             for (int r = 0; r < 4; ++r)
 #pragma unroll
                 for (int q = 0; q < 4; ++q) l[r][q] = fma(-m[r], u[q], l[r][q]);
-        }
-        if (lown && (jn >> 2) == lr) {
-            const int r = jn & 3;
-            TI v[4];
+            if (two && (!dr || JJ == 0)) {
+                TF pr[4];
+                TI pl[4], uk[4], mk[4];
+                ld4(&PW[SLOT][4 * lr], pr);
+                ld4(&PL[SLOT][4 * lc], pl);
+                const TI mjk = TI(sjk) * ij;
+                const TI ik = TI(invk);
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                v[q] = r == 0 ? l[0][q] : r == 1 ? l[1][q] : r == 2 ? l[2][q] : l[3][q];
-            st4(&Li[jn][4 * lc], v);
+                for (int q = 0; q < 4; ++q) uk[q] = fma(-mjk, u[q], pl[q]);
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    mk[r] = TI(fma(-sjk, sr[r] * invj, pr[r])) * ik;
+                    if (r <= JJ + 1) mk[r] = dr ? TI(0) : mk[r];
+                }
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) l[r][q] = fma(-mk[r], uk[q], l[r][q]);
+            }
+        }
+        // rows k and j + 2 are final, row j + 3 waits for its update by row j + 2
+        constexpr int R2 = (JJ + 2) & 3, R3 = (JJ + 3) & 3, T2 = (JJ + 2) >> 2, T3 = (JJ + 3) >> 2;
+        if (wown) {
+            if (wi == tr) st4(&S[k][4 * wj], w[JJ + 1]);
+            if (wi == tr + T2) {
+                st4(&S[j + 2][4 * wj], w[R2]);
+                if (wi == wj && j + 2 < bi) pivot(j + 2, w[R2][R2], true);
+            }
+            if (wi == tr + T3) st4(&PW[SLOT ^ 1][4 * wj], w[R3]);
+        }
+        if (lown) {
+            if (lr == tr) st4(&Li[k][4 * lc], l[JJ + 1]);
+            if (lr == tr + T2) st4(&Li[j + 2][4 * lc], l[R2]);
+            if (lr == tr + T3) st4(&PL[SLOT ^ 1][4 * lc], l[R3]);
         }
         __syncthreads();
+    };
+    for (int j0 = 0; j0 < bi; j0 += 4) {
+        dstep(std::integral_constant<int, 0>{}, j0);
+        if (j0 + 2 < bi) dstep(std::integral_constant<int, 2>{}, j0);
     }
     if (tid < bi) sh.idiag[tid] = TF(1) / sqrt(sh.dpiv[tid]);
     __syncthreads();
@@ -325,10 +392,18 @@ k_chol(const double* __restrict__ W, int bi, double tau_rel, double* __restrict_
 constexpr int COOP_THREADS = 512;
 constexpr int COOP_ROWS = 440;      // rows per CTA held in shared memory
 constexpr int COOP_MAX_CTAS = 256;
-constexpr int PLD = MAXB + 1;       // shared row stride of the panel slice
+// The panel slice is held column by column (rows contiguous, so the global loads and stores are
+// coalesced and 8 consecutive rows are two float4 reads).  Column c starts at pcol(c) =
+// c TLD + 4 (c / 4): TLD is a multiple of 32 words, so the start lies on bank 4 (c / 4) mod 32 and
+// the float4 reads of eight consecutive column quadruples at one row hit distinct banks (the
+// Gram's access pattern).  The skew only grows, so columns never overlap (TLD >= COOP_ROWS).
+constexpr int TLD = 448;
+constexpr int PT_FLOATS = MAXB * TLD + MAXB;
+static_assert(TLD % 32 == 0 && TLD >= COOP_ROWS && COOP_ROWS % 8 == 0, "panel slice layout");
+__device__ __forceinline__ int pcol(int c) { return c * TLD + 4 * (c >> 2); }
 constexpr uint64_t COOP_WAIT_NS = 2000000000ull;
-// dynamic shared memory: panel slice, then S (float64 size), Sf, Li, Rs
-constexpr size_t COOP_SMEM = sizeof(float) * COOP_ROWS * PLD + sizeof(double) * MAXB * CLD +
+// dynamic shared memory: panel slice, then S (float64 size), Sf, Li, Rs, Pc
+constexpr size_t COOP_SMEM = sizeof(float) * PT_FLOATS + sizeof(double) * MAXB * CLD +
                              4 * sizeof(float) * MAXB * CLD;
 
 struct CoopArgs {
@@ -404,23 +479,57 @@ __device__ __forceinline__ void df_add_sum(float& hi, float& lo, float v) {
     hi = s;
 }
 
+// Rs = R^-1 (row-major, CLD stride) from the factor's L^-1 tiles: R^-1[c][a] = L^-1[a][c] / sqrt(d_a);
+// strictly lower tiles are zero
+template <class TF>
+__device__ __forceinline__ void coop_write_rinv(int bi, const float (&l)[4][4], int lr, int lc,
+                                                const TF* idiag, float (*Rs)[CLD]) {
+    const int tid = threadIdx.x;
+    for (int e = tid; e < MAXB * MAXB; e += COOP_THREADS) {
+        const int i = e % MAXB, jj = e / MAXB;
+        if ((i >> 2) > (jj >> 2)) Rs[i][jj] = 0.f;
+    }
+    if (tid >= CHOL_L0 && tid < CHOL_L0 + CHOL_TILES) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int a = 4 * lr + r, c = 4 * lc + q;
+                const float id = float(idiag[a < MAXB ? a : 0]);
+                Rs[c][a] = (a < bi && c < bi) ? l[r][q] * id : 0.f;
+            }
+    }
+}
+
+// the float64 refactor of an ill-conditioned panel; kept out of line so that the float32 path of
+// the fused kernel keeps its registers
+__device__ __noinline__ void coop_factor_f64(int bi, double tau, int* flags, const double* wred,
+                                             CholShared<double, float> sh, float (*Rs)[CLD]) {
+    float l[4][4];
+    int lr, lc;
+    auto ldw = [&](int i, int j) { return __ldcg(wred + i + j * MAXB); };
+    chol_core<double, float>(bi, tau, 0.0, flags, ldw, sh, l, lr, lc);
+    coop_write_rinv(bi, l, lr, lc, sh.idiag, Rs);
+}
+
 template <bool PRECISE>
 __global__ void __launch_bounds__(COOP_THREADS, 1) k_cholqr_coop(CoopArgs p) {
     extern __shared__ __align__(16) unsigned char coop_smem[];
-    float (*Ps)[PLD] = reinterpret_cast<float (*)[PLD]>(coop_smem);
-    unsigned char* rest = coop_smem + sizeof(float) * COOP_ROWS * PLD;
+    float* Pt = reinterpret_cast<float*>(coop_smem);
+    unsigned char* rest = coop_smem + sizeof(float) * PT_FLOATS;
     unsigned char* sreg = rest;                                           // S (float or double)
     float (*Sf)[CLD] = reinterpret_cast<float (*)[CLD]>(rest + sizeof(double) * MAXB * CLD);
     float (*Li)[CLD] = reinterpret_cast<float (*)[CLD]>(rest + (sizeof(double) + sizeof(float)) * MAXB * CLD);
     float (*Rs)[CLD] = reinterpret_cast<float (*)[CLD]>(rest + (sizeof(double) + 2 * sizeof(float)) * MAXB * CLD);
     float (*Pc)[CLD] = reinterpret_cast<float (*)[CLD]>(rest + (sizeof(double) + 3 * sizeof(float)) * MAXB * CLD);
-    double* scratch = reinterpret_cast<double*>(rest);   // Gram combine space (S and Sf regions)
-    // CTA 0 keeps the running product rinv_prev R_1^-1 R_2^-1 ... of the passes
+    double* scratch = reinterpret_cast<double*>(rest);   // Gram combine space (S, Sf, Li regions)
+    // CTA 0 keeps the running product rinv_prev R_1^-1 R_2^-1 ... of the passes, transposed
+    // (Pc[j][i] holds entry (i, j)) so that the product reads it without bank conflicts
     const bool chain = blockIdx.x == 0 && p.rinv_out != nullptr;
     if (chain) {
         for (int e = threadIdx.x; e < MAXB * MAXB; e += COOP_THREADS) {
             const int i = e % MAXB, j = e / MAXB;
-            Pc[i][j] = p.rinv_prev ? float(p.rinv_prev[e]) : (i == j ? 1.f : 0.f);
+            Pc[j][i] = p.rinv_prev ? float(p.rinv_prev[e]) : (i == j ? 1.f : 0.f);
         }
     }
     __shared__ float fpiv[MAXB], finvd[MAXB], fidiag[MAXB], fdiag0[MAXB], fdmax;
@@ -428,6 +537,7 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) k_cholqr_coop(CoopArgs p) {
     __shared__ int weak_s;
     __shared__ double red[16][32];
     const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
     const int G = gridDim.x, cta = blockIdx.x;
     const int bi = p.bi;
     const int64_t r0 = int64_t(cta) * p.rows_per;
@@ -437,50 +547,60 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) k_cholqr_coop(CoopArgs p) {
     // (each phase re-reads it from global memory); a slice of one tile stays resident throughout.
     const int ntile = nr > 0 ? (nr + COOP_ROWS - 1) / COOP_ROWS : 1;
     auto tile_rows = [&](int t) { return min(COOP_ROWS, nr - t * COOP_ROWS); };
+    // rows up to the next multiple of 8 (zeros past the tile and in the columns >= bi) are
+    // written so that the float4 reads of the Gram and the row update see zeros there
+    // (warp w takes columns w, w + 16, w + 32, w + 48; its lanes consecutive rows)
     auto load_tile = [&](int t) {
-        const int tn = tile_rows(t);
+        const int tn = tile_rows(t), tn8 = (tn + 7) & ~7;
         const int64_t rb = r0 + int64_t(t) * COOP_ROWS;
-        for (int e = tid; e < tn * MAXB; e += COOP_THREADS) {
-            const int r = e % tn, col = e / tn;
-            Ps[r][col] = col < bi ? p.P[rb + r + int64_t(col) * p.ldp] : 0.f;
+#pragma unroll
+        for (int cc = 0; cc < MAXB / 16; ++cc) {
+            const int col = warp + 16 * cc;
+            const bool cok = col < bi;
+            const float* src = p.P + rb + int64_t(cok ? col : 0) * p.ldp;
+            float* dst = Pt + pcol(col);
+#pragma unroll 4
+            for (int r = lane; r < tn8; r += 32) dst[r] = (cok && r < tn) ? src[r] : 0.f;
         }
     };
     // write the tile back; the final write also emits the optional bf16 shadow
     auto store_tile = [&](int t, bool final) {
         const int tn = tile_rows(t);
         const int64_t rb = r0 + int64_t(t) * COOP_ROWS;
-        for (int e = tid; e < tn * MAXB; e += COOP_THREADS) {
-            const int r = e % tn, col = e / tn;
-            if (col >= bi) continue;
-            const float v = Ps[r][col];
-            p.P[rb + r + int64_t(col) * p.ldp] = v;
-            if (final && p.out_hi) {
-                const bf16 h = __float2bfloat16_rn(v);
-                p.out_hi[rb + r + int64_t(col) * p.ldo] = h;
-                if (p.out_lo)
-                    p.out_lo[rb + r + int64_t(col) * p.ldo] = __float2bfloat16_rn(v - __bfloat162float(h));
+        for (int col = warp; col < bi; col += COOP_THREADS / 32) {
+            const float* src = Pt + pcol(col);
+#pragma unroll 4
+            for (int r = lane; r < tn; r += 32) {
+                const float v = src[r];
+                const int64_t g = rb + r;
+                p.P[g + int64_t(col) * p.ldp] = v;
+                if (final && p.out_hi) {
+                    const bf16 h = __float2bfloat16_rn(v);
+                    p.out_hi[g + int64_t(col) * p.ldo] = h;
+                    if (p.out_lo)
+                        p.out_lo[g + int64_t(col) * p.ldo] = __float2bfloat16_rn(v - __bfloat162float(h));
+                }
             }
         }
     };
     if (ntile == 1) load_tile(0);
-    // Gram block of thread t < 3 * 136: the (t % 136)-th 4 x 4 block of the upper triangle over
-    // rows t / 136, t / 136 + 3, ...
-    const int blk = tid % 136, grp = tid / 136;
-    int gi = 0, gj = 0;
-    {
-        int t = blk;
-        while (t >= 16 - gi) { t -= 16 - gi; ++gi; }
-        gj = gi + t;
-    }
+    // Gram: warp w < 12 computes the 16 x 32 block GB[w % 6] of the upper part of the 64 x 64 Gram
+    // over one half of the slice's rows (w / 6); lane (ti, tj) = (lane / 8, lane % 8) owns the
+    // 4 x 4 sub-block at rows 4 ti, columns 4 tj of it.  Per 4 rows a thread reads 8 float4 and
+    // does 64 FMAs.
+    const bool gw = warp < 12;
+    const int gblk = warp % 6, ghalf = warp / 6;
+    const int gi0 = 16 * (gblk < 2 ? gblk : gblk - 2) + 4 * (lane >> 3);
+    const int gj0 = 32 * (gblk < 2 ? 0 : 1) + 4 * (lane & 7);
     // partial Gram of the slice into p.part[cta]; mode 0 float32, 1 two-level, 2 exact products
-    auto gram = [&](int mode) {
+    auto gram = [&](auto mode_c) {
+        constexpr int mode = decltype(mode_c)::value;
         __syncthreads();
         float hi[4][4], lo[4][4], ch[4][4];
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
             for (int b = 0; b < 4; ++b) hi[a][b] = lo[a][b] = ch[a][b] = 0.f;
-        int cnt = 0;
         for (int t = 0; t < ntile; ++t) {
             if (ntile > 1) {
                 __syncthreads();
@@ -488,59 +608,57 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) k_cholqr_coop(CoopArgs p) {
                 __syncthreads();
             }
             const int tn = ntile > 1 ? tile_rows(t) : nr;
-            if (grp >= 3) continue;
-            for (int r = grp; r < tn; r += 3) {
-                float x[4], y[4];
+            if (!gw) continue;
+            const int nch = (tn + 3) >> 2, cmid = (nch + 1) >> 1;
+            const int cb = ghalf == 0 ? 0 : cmid, ce = ghalf == 0 ? cmid : nch;
+            for (int c4 = cb; c4 < ce; ++c4) {
+                const int r = 4 * c4;
+                float4 x[4], y[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    x[q] = Ps[r][gi * 4 + q];
-                    y[q] = Ps[r][gj * 4 + q];
+                    x[q] = *reinterpret_cast<const float4*>(Pt + pcol(gi0 + q) + r);
+                    y[q] = *reinterpret_cast<const float4*>(Pt + pcol(gj0 + q) + r);
                 }
-                if (mode == 2) {
 #pragma unroll
-                    for (int a = 0; a < 4; ++a)
+                for (int rr = 0; rr < 4; ++rr) {
 #pragma unroll
-                        for (int b = 0; b < 4; ++b) df_add(hi[a][b], lo[a][b], x[a], y[b]);
-                } else {
+                    for (int a = 0; a < 4; ++a) {
+                        const float xa = rr == 0 ? x[a].x : rr == 1 ? x[a].y : rr == 2 ? x[a].z : x[a].w;
 #pragma unroll
-                    for (int a = 0; a < 4; ++a)
-#pragma unroll
-                        for (int b = 0; b < 4; ++b) ch[a][b] = fmaf(x[a], y[b], ch[a][b]);
-                    if (mode == 1 && ++cnt == 8) {
-                        cnt = 0;
-#pragma unroll
-                        for (int a = 0; a < 4; ++a)
-#pragma unroll
-                            for (int b = 0; b < 4; ++b) {
-                                df_add_sum(hi[a][b], lo[a][b], ch[a][b]);
-                                ch[a][b] = 0.f;
-                            }
+                        for (int b = 0; b < 4; ++b) {
+                            const float yb = rr == 0 ? y[b].x : rr == 1 ? y[b].y : rr == 2 ? y[b].z : y[b].w;
+                            if (mode == 2) df_add(hi[a][b], lo[a][b], xa, yb);
+                            else ch[a][b] = fmaf(xa, yb, ch[a][b]);
+                        }
                     }
+                }
+                if (mode == 1 && ((c4 - cb) & 1)) {   // fold every 8 rows into the float32 pair
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) {
+                            df_add_sum(hi[a][b], lo[a][b], ch[a][b]);
+                            ch[a][b] = 0.f;
+                        }
                 }
             }
         }
-        // the Gram scratch aliases S / Sf, free here: the factor of the previous pass is done
+        // the Gram scratch aliases S / Sf / Li, free here: the factor of the previous pass is done
         __syncthreads();
-        if (grp < 3) {
+        if (gw) {
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
                 for (int b = 0; b < 4; ++b) {
                     const double v = mode == 0 ? double(ch[a][b])
                                                : double(hi[a][b]) + double(lo[a][b]) + double(ch[a][b]);
-                    scratch[(grp * 136 + blk) * 16 + a * 4 + b] = v;
+                    scratch[ghalf * MAXB * MAXB + (gi0 + a) + (gj0 + b) * MAXB] = v;
                 }
         }
         __syncthreads();
-        if (tid < 136) {
-            double* out = p.part + int64_t(cta) * MAXB * MAXB;
-#pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                const double v = scratch[blk * 16 + q] + scratch[(136 + blk) * 16 + q] +
-                                 scratch[(272 + blk) * 16 + q];
-                out[(gi * 4 + q / 4) + (gj * 4 + q % 4) * MAXB] = v;
-            }
-        }
+        double* out = p.part + int64_t(cta) * MAXB * MAXB;
+        for (int e = tid; e < MAXB * MAXB; e += COOP_THREADS)
+            if ((e & (MAXB - 1)) <= (e / MAXB)) out[e] = scratch[e] + scratch[MAXB * MAXB + e];
     };
     // sum the partials: this CTA owns an equal share of the upper entries
     auto reduce = [&]() {
@@ -550,8 +668,22 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) k_cholqr_coop(CoopArgs p) {
         for (int eb = e0; eb < e1; eb += 32) {
             const int e = eb + lane;
             double v = 0.0;
-            if (e < e1 && e % MAXB <= e / MAXB)
-                for (int q = sub; q < G; q += 16) v += __ldcg(p.part + int64_t(q) * MAXB * MAXB + e);
+            if (e < e1 && e % MAXB <= e / MAXB) {
+                // partials sub, sub + 16, ... in that order, four loads in flight
+                const double* src = p.part + e;
+                int q = sub;
+                for (; q + 48 < G; q += 64) {
+                    const double a0 = __ldcg(src + int64_t(q) * MAXB * MAXB);
+                    const double a1 = __ldcg(src + int64_t(q + 16) * MAXB * MAXB);
+                    const double a2 = __ldcg(src + int64_t(q + 32) * MAXB * MAXB);
+                    const double a3 = __ldcg(src + int64_t(q + 48) * MAXB * MAXB);
+                    v += a0;
+                    v += a1;
+                    v += a2;
+                    v += a3;
+                }
+                for (; q < G; q += 16) v += __ldcg(src + int64_t(q) * MAXB * MAXB);
+            }
             red[sub][lane] = v;
             __syncthreads();
             if (sub == 0 && e < e1) {
@@ -565,47 +697,33 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) k_cholqr_coop(CoopArgs p) {
     };
     auto ldw = [&](int i, int j) { return __ldcg(p.wred + i + j * MAXB); };
     for (int pass = 0; pass < p.passes; ++pass) {
-        gram(PRECISE ? 1 : 0);
+        gram(std::integral_constant<int, PRECISE ? 1 : 0>{});
         if (!coop_sync(p.bar, p.err)) return;
         reduce();
         if (!coop_sync(p.bar, p.err)) return;
         // ---- every CTA factors the summed Gram
-        float l[4][4];
-        int lr, lc;
-        float (*Sfl)[CLD] = reinterpret_cast<float (*)[CLD]>(sreg);
-        chol_core<float, float>(bi, p.tau, PRECISE ? CHOL_WEAK_REL : 0.0,
-                                (cta == 0 && !PRECISE) ? p.flags : nullptr, ldw,
-                                CholShared<float, float>{Sfl, Sf, Li, fpiv, finvd, fidiag, fdiag0,
-                                                         &fdmax, &weak_s},
-                                l, lr, lc);
-        bool dbl = false;
+        {
+            float l[4][4];
+            int lr, lc;
+            float (*Sfl)[CLD] = reinterpret_cast<float (*)[CLD]>(sreg);
+            chol_core<float, float>(bi, p.tau, PRECISE ? CHOL_WEAK_REL : 0.0,
+                                    (cta == 0 && !PRECISE) ? p.flags : nullptr, ldw,
+                                    CholShared<float, float>{Sfl, Sf, Li, fpiv, finvd, fidiag,
+                                                             fdiag0, &fdmax, &weak_s},
+                                    l, lr, lc);
+            coop_write_rinv(bi, l, lr, lc, fidiag, Rs);
+        }
         if (PRECISE && weak_s) {
-            // ill-conditioned panel: exact-product Gram, float64 factor
-            dbl = true;
-            gram(2);
+            // ill-conditioned panel: exact-product Gram, float64 factor (replaces Rs)
+            gram(std::integral_constant<int, 2>{});
             if (!coop_sync(p.bar, p.err)) return;
             reduce();
             if (!coop_sync(p.bar, p.err)) return;
-            double (*Sd)[CLD] = reinterpret_cast<double (*)[CLD]>(sreg);
-            chol_core<double, float>(bi, p.tau, 0.0, cta == 0 ? p.flags : nullptr, ldw,
-                                     CholShared<double, float>{Sd, Sf, Li, dpiv, dinvd, didiag,
-                                                               ddiag0, &ddmax, &weak_s},
-                                     l, lr, lc);
-        }
-        // R^-1[c][a] = L^-1[a][c] / sqrt(d_a); strictly lower tiles are zero
-        for (int e = tid; e < MAXB * MAXB; e += COOP_THREADS) {
-            const int i = e % MAXB, jj = e / MAXB;
-            if ((i >> 2) > (jj >> 2)) Rs[i][jj] = 0.f;
-        }
-        if (tid >= CHOL_L0 && tid < CHOL_L0 + CHOL_TILES) {
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int a = 4 * lr + r, c = 4 * lc + q;
-                    const float id = dbl ? float(didiag[a < MAXB ? a : 0]) : fidiag[a < MAXB ? a : 0];
-                    Rs[c][a] = (a < bi && c < bi) ? l[r][q] * id : 0.f;
-                }
+            coop_factor_f64(bi, p.tau, cta == 0 ? p.flags : nullptr, p.wred,
+                            CholShared<double, float>{reinterpret_cast<double (*)[CLD]>(sreg), Sf,
+                                                      Li, dpiv, dinvd, didiag, ddiag0, &ddmax,
+                                                      &weak_s},
+                            Rs);
         }
         __syncthreads();
         if (chain) {
@@ -615,15 +733,26 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) k_cholqr_coop(CoopArgs p) {
 #pragma unroll
             for (int q = 0; q < 8; ++q) acc[q] = 0.f;
             for (int l2 = 0; l2 < MAXB; ++l2) {
-                const float v = Pc[i][l2];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) acc[q] = fmaf(v, Rs[l2][c0 + q], acc[q]);
+                const float v = Pc[l2][i];
+                const float4 r0v = *reinterpret_cast<const float4*>(&Rs[l2][c0]);
+                const float4 r1v = *reinterpret_cast<const float4*>(&Rs[l2][c0 + 4]);
+                acc[0] = fmaf(v, r0v.x, acc[0]);
+                acc[1] = fmaf(v, r0v.y, acc[1]);
+                acc[2] = fmaf(v, r0v.z, acc[2]);
+                acc[3] = fmaf(v, r0v.w, acc[3]);
+                acc[4] = fmaf(v, r1v.x, acc[4]);
+                acc[5] = fmaf(v, r1v.y, acc[5]);
+                acc[6] = fmaf(v, r1v.z, acc[6]);
+                acc[7] = fmaf(v, r1v.w, acc[7]);
             }
             __syncthreads();
 #pragma unroll
-            for (int q = 0; q < 8; ++q) Pc[i][c0 + q] = acc[q];
+            for (int q = 0; q < 8; ++q) Pc[c0 + q][i] = acc[q];
         }
-        // ---- rows <- rows * R^-1, 128 rows at a time (thread: one row, 16 columns)
+        // ---- rows <- rows * R^-1 (R^-1 upper triangular).  Warp block (RG, CG) = 32 rows x 32
+        // columns; lane (lane / 8, lane % 8) computes rows 8 rg .. 8 rg + 7 and columns
+        // 4 cg .. 4 cg + 3 with terms q2 < 32 (CG + 1) (the others are zero), in the order
+        // q2 = 0, 1, ...  Every row of a round is read before any of it is written.
         const bool last = pass + 1 == p.passes;
         for (int t = 0; t < ntile; ++t) {
             if (ntile > 1) {
@@ -632,33 +761,49 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) k_cholqr_coop(CoopArgs p) {
                 __syncthreads();
             }
             const int tn = ntile > 1 ? tile_rows(t) : nr;
-            const int i = tid & 127, c0 = (tid >> 7) * 16;
-            for (int rb = 0; rb < tn; rb += 128) {
-                const int r = rb + i;
-                float acc[16];
+            const int nrg = (tn + 7) >> 3, nblk = ((nrg + 3) >> 2) * 2;
+            for (int base = 0; base < nblk; base += COOP_THREADS / 32) {
+                const int bw = base + warp, CG = bw & 1;
+                const int rg = 4 * (bw >> 1) + (lane >> 3), cg = 8 * CG + (lane & 7);
+                const bool act = bw < nblk && rg < nrg;
+                float acc[8][4];
 #pragma unroll
-                for (int q = 0; q < 16; ++q) acc[q] = 0.f;
-                if (r < tn) {
-                    for (int q2 = 0; q2 < bi; ++q2) {
-                        const float v = Ps[r][q2];
+                for (int rr = 0; rr < 8; ++rr)
 #pragma unroll
-                        for (int q = 0; q < 16; ++q) acc[q] = fmaf(v, Rs[q2][c0 + q], acc[q]);
+                    for (int c = 0; c < 4; ++c) acc[rr][c] = 0.f;
+                if (act) {
+                    const int qmax = min(bi, 32 * CG + 32);
+                    for (int q2 = 0; q2 < qmax; ++q2) {
+                        const float4 u0 = *reinterpret_cast<const float4*>(Pt + pcol(q2) + 8 * rg);
+                        const float4 u1 = *reinterpret_cast<const float4*>(Pt + pcol(q2) + 8 * rg + 4);
+                        const float4 rv = *reinterpret_cast<const float4*>(&Rs[q2][4 * cg]);
+                        const float u[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+                        const float w4[4] = {rv.x, rv.y, rv.z, rv.w};
+#pragma unroll
+                        for (int rr = 0; rr < 8; ++rr)
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) acc[rr][c] = fmaf(u[rr], w4[c], acc[rr][c]);
                     }
                 }
                 __syncthreads();
-                if (r < tn) {
+                if (act) {
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) Ps[r][c0 + q] = acc[q];
+                    for (int c = 0; c < 4; ++c) {
+                        float* dst = Pt + pcol(4 * cg + c) + 8 * rg;
+#pragma unroll
+                        for (int rr = 0; rr < 8; ++rr)
+                            if (8 * rg + rr < tn) dst[rr] = acc[rr][c];
+                    }
                 }
-                __syncthreads();
             }
+            __syncthreads();
             if (ntile > 1) store_tile(t, last);
         }
     }
     __syncthreads();
     if (chain) {
         for (int e = tid; e < MAXB * MAXB; e += COOP_THREADS)
-            p.rinv_out[e] = double(Pc[e % MAXB][e / MAXB]);
+            p.rinv_out[e] = double(Pc[e / MAXB][e % MAXB]);
     }
     if (ntile == 1) store_tile(0, true);
 }
