@@ -85,8 +85,10 @@ __device__ __forceinline__ void st4<float>(float* p, const float (&v)[4]) {
 // The tile updates need no per-element predicates: the multiplier of a row a <= j is zero, the
 // entries of row j beyond bi are zero, row j of L^-1 is zero beyond column j, and the lower part
 // of the diagonal tiles of W (which picks up rounding garbage) is never read.
-// correctly rounded reciprocal (the same value as 1 / x in IEEE division)
-__device__ __forceinline__ float rcp_rn(float x) { return __frcp_rn(x); }
+// reciprocal of a pivot: float32 by the fast hardware reciprocal (an error of ~2 ulp in a
+// multiplier is rounding of the elimination itself, and the float32 factor feeds CholeskyQR2),
+// float64 correctly rounded (the float64 path's parity with the float64 oracle)
+__device__ __forceinline__ float rcp_rn(float x) { return __fdividef(1.f, x); }
 __device__ __forceinline__ double rcp_rn(double x) { return __drcp_rn(x); }
 
 template <class TF, class TI, class Load>
@@ -94,9 +96,10 @@ __device__ void chol_core(int bi, double tau_rel, double weak_rel, int* flags, L
                           CholShared<TF, TI> sh, TI (&l)[4][4], int& lr, int& lc) {
     TF (*S)[CLD] = sh.S;
     TI (*Li)[CLD] = sh.Li;
-    // rings of the pending row (j + 1 before its update by row j): W in TF, L^-1 in TI
+    // two-slot rings (rows 0..3 and 4..7) of the pending tile row: its four rows of W and of
+    // L^-1 before the updates of their own quad step
     TF (*PW)[CLD] = reinterpret_cast<TF (*)[CLD]>(sh.Sf);
-    TI (*PL)[CLD] = reinterpret_cast<TI (*)[CLD]>(reinterpret_cast<TF*>(sh.Sf) + 2 * CLD);
+    TI (*PL)[CLD] = reinterpret_cast<TI (*)[CLD]>(reinterpret_cast<TF*>(sh.Sf) + 8 * CLD);
     const int tid = threadIdx.x;
     const bool wown = tid < CHOL_TILES;
     const bool lown = tid >= CHOL_L0 && tid < CHOL_L0 + CHOL_TILES;
@@ -115,19 +118,17 @@ __device__ void chol_core(int bi, double tau_rel, double weak_rel, int* flags, L
             const int la = 4 * lr + r, lcc = 4 * lc + q;
             l[r][q] = (lown && la == lcc && la < bi) ? TI(1) : TI(0);
         }
-    // initial state: every row of W and L^-1 in shared memory, row 1 also in ring slot 0
+    // initial state: tile row 0 pending in slot 0
     if (wown) {
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-            st4(&S[4 * wi + r][4 * wj], w[r]);
             if (wi == wj) sh.diag0[4 * wi + r] = w[r][r];
+            if (wi == 0) st4(&PW[r][4 * wj], w[r]);
         }
-        if (wi == 0) st4(&PW[0][4 * wj], w[1]);
     }
-    if (lown) {
+    if (lown && lr == 0) {
 #pragma unroll
-        for (int r = 0; r < 4; ++r) st4(&Li[4 * lr + r][4 * lc], l[r]);
-        if (lr == 0) st4(&PL[0][4 * lc], l[1]);
+        for (int r = 0; r < 4; ++r) st4(&PL[r][4 * lc], l[r]);
     }
     if (tid == 0) sh.weak[0] = 0;
     __syncthreads();
@@ -146,128 +147,154 @@ __device__ void chol_core(int bi, double tau_rel, double weak_rel, int* flags, L
     const TF tiny = sizeof(TF) == 8 ? TF(2.2250738585072014e-308) : TF(1.1754943508222875e-38);
     const TF floor_piv = TF(tau_rel) * dmax > tiny ? TF(tau_rel) * dmax : tiny;
     const TF tau_dmax = TF(tau_rel) * dmax;
-    // pivot of row j from its (updated) diagonal value d: the value used (d, or the floor when d
-    // does not exceed tau_rel * dmax) and, by the calling thread, the weak / breakdown flags
+    const TF weak_t = TF(weak_rel);
+    // the pivot used for a diagonal value d: d, or the floor when d does not exceed tau_rel * dmax
     auto piv_value = [&](TF d) { return d > tau_dmax ? d : floor_piv; };
-    auto pivot = [&](int j, TF d, bool inv) {
-        if (!(d >= TF(weak_rel) * sh.diag0[j])) sh.weak[0] = 1;
-        if (!(d > tau_dmax)) {
-            sh.weak[0] = 1;
-            if (flags) atomicOr(flags + 1, 1);
-        }
-        d = piv_value(d);
-        sh.dpiv[j] = d;
-        if (inv) sh.invd[j] = rcp_rn(d);
-    };
-    if (tid == 0 && bi > 0) pivot(0, S[0][0], true);
-    __syncthreads();
-    // double step (j, k = j + 1) with j = j0 + JJ, j0 a multiple of 4 and JJ in {0, 2} fixed at
-    // compile time, so the rows a tile publishes and masks are known statically.  Row k's update
-    // by row j, vk(x) = W'[k][x] - W'[j][k] (W'[j][x] / d_j), is the arithmetic its owner does.
-    auto dstep = [&](auto jj_c, int j0) {
-        constexpr int JJ = decltype(jj_c)::value;
-        constexpr int SLOT = JJ >> 1;                 // ring slot of the pending row k
-        const int j = j0 + JJ, k = j + 1, tr = j0 >> 2;
-        const bool two = k < bi;
-        const TF invj = sh.invd[j];
-        const TF sjk = two ? S[j][k] : TF(0);
-        TF invk = TF(0);
-        if (two) {
-            const TF dk = fma(-sjk, sjk * invj, PW[SLOT][k]);
-            invk = rcp_rn(piv_value(dk));
-            if (tid == 0) pivot(k, dk, false);       // 1 / d_k is not read from shared memory
-        }
-        if (wown && wi >= tr) {
-            // W'[a][c] -= W'[j][a] (W'[j][c] / d_j), then -= W'[k][a] (W'[k][c] / d_k), j < a <= c
-            const bool dr = wi == tr;                 // the tile holds rows j and k
-            TF mj[4], tj[4];
-            ld4(&S[j][4 * wi], mj);
-            ld4(&S[j][4 * wj], tj);
+    // quad step t: the four pivots of tile row t per block barrier.  Every thread factors the
+    // pending 4 x 4 diagonal block itself and applies the block rows to the entries it needs, in
+    // the arithmetic of the one-pivot-per-step elimination (the same operations in the same
+    // order, so the result is bit-identical to it):
+    //   W'[a][c] -= W'[p][a] (W'[p][c] / d_p),   L^-1[a][c] -= (W'[p][a] / d_p) L^-1[p][c],
+    // for the pivots p = 4t .. 4t + 3 in turn (a > p).
+    for (int t = 0; 4 * t < bi; ++t) {
+        const int j = 4 * t, slot = (t & 1) * 4, nslot = 4 - slot;
+        TF bl[4][4];                  // the diagonal block; row p final once p pivots are applied
 #pragma unroll
-            for (int q = 0; q < 4; ++q) tj[q] *= invj;
-            const bool second = two && (!dr || JJ == 0);
-            TF mk[4], tk[4];
-            if (second) {
-                TF pr[4], pc[4];
-                ld4(&PW[SLOT][4 * wi], pr);
-                ld4(&PW[SLOT][4 * wj], pc);
+        for (int i = 0; i < 4; ++i) ld4(&PW[slot + i][j], bl[i]);
+        TF inv[4];
 #pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    mk[r] = fma(-sjk, mj[r] * invj, pr[r]);
-                    if (r <= JJ + 1) mk[r] = dr ? TF(0) : mk[r];
+        for (int p = 0; p < 4; ++p) {
+            inv[p] = rcp_rn(piv_value(bl[p][p]));
+#pragma unroll
+            for (int i = p + 1; i < 4; ++i)
+#pragma unroll
+                for (int i2 = i; i2 < 4; ++i2) bl[i][i2] = fma(-bl[p][i], bl[p][i2] * inv[p], bl[i][i2]);
+        }
+        if (tid == 0) {
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                if (j + p < bi) {
+                    const TF d = bl[p][p];
+                    if (!(d >= weak_t * sh.diag0[j + p])) sh.weak[0] = 1;
+                    if (!(d > tau_dmax)) {
+                        sh.weak[0] = 1;
+                        if (flags) atomicOr(flags + 1, 1);
+                    }
+                    sh.dpiv[j + p] = piv_value(d);
                 }
+            }
+        }
+        if (wown && wi > t) {
+            // the block rows at this tile's rows (vr: W'[j+p][4 wi + r]) and columns
+            // (vc: W'[j+p][4 wj + q] / d_p), from their pending values
+            TF vr[4][4], vc[4][4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) tk[q] = fma(-sjk, tj[q], pc[q]) * invk;
+            for (int p = 0; p < 4; ++p) {
+                ld4(&PW[slot + p][4 * wi], vr[p]);
+                ld4(&PW[slot + p][4 * wj], vc[p]);
             }
 #pragma unroll
-            for (int r = 0; r <= JJ; ++r) mj[r] = dr ? TF(0) : mj[r];
+            for (int p = 0; p < 4; ++p) {
+                TF tr[4];
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
+                for (int r = 0; r < 4; ++r) tr[r] = vr[p][r] * inv[p];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) w[r][q] = fma(-mj[r], tj[q], w[r][q]);
-            if (second) {
+                for (int q = 0; q < 4; ++q) vc[p][q] *= inv[p];
+#pragma unroll
+                for (int i = p + 1; i < 4; ++i) {
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) vr[i][r] = fma(-bl[p][i], tr[r], vr[i][r]);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) vc[i][q] = fma(-bl[p][i], vc[p][q], vc[i][q]);
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
 #pragma unroll
                 for (int r = 0; r < 4; ++r)
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) w[r][q] = fma(-mk[r], tk[q], w[r][q]);
+                    for (int q = 0; q < 4; ++q) w[r][q] = fma(-vr[p][r], vc[p][q], w[r][q]);
+        } else if (wown && wi == t) {
+            // this tile's rows are the block rows: their updates within the block
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                TF tq[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) tq[q] = w[p][q] * inv[p];
+#pragma unroll
+                for (int i = p + 1; i < 4; ++i)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) w[i][q] = fma(-bl[p][i], tq[q], w[i][q]);
             }
         }
-        if (lown && lr >= tr && lc <= tr) {
-            // L^-1[a][c] -= (W'[j][a] / d_j) L^-1[j][c], then the same with row k, a > j >= c
-            const bool dr = lr == tr;
-            const TI ij = TI(invj);
-            TI m[4], u[4];
-            TF sr[4];
-            ld4(&S[j][4 * lr], sr);
-            ld4(&Li[j][4 * lc], u);
+        if (lown && lr > t && lc <= t) {
+            // final L^-1 block rows at this tile's columns (lf) and the multipliers' W' values at
+            // its rows (vr), from their pending values
+            TI lf[4][4];
+            TF vr[4][4];
 #pragma unroll
-            for (int r = 0; r < 4; ++r) m[r] = TI(sr[r]) * ij;
+            for (int p = 0; p < 4; ++p) {
+                ld4(&PL[slot + p][4 * lc], lf[p]);
+                ld4(&PW[slot + p][4 * lr], vr[p]);
+            }
 #pragma unroll
-            for (int r = 0; r <= JJ; ++r) m[r] = dr ? TI(0) : m[r];
+            for (int p = 0; p < 4; ++p) {
+                const TI mm0 = TI(inv[p]);
+                TF tr[4];
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
+                for (int r = 0; r < 4; ++r) tr[r] = vr[p][r] * inv[p];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) l[r][q] = fma(-m[r], u[q], l[r][q]);
-            if (two && (!dr || JJ == 0)) {
-                TF pr[4];
-                TI pl[4], uk[4], mk[4];
-                ld4(&PW[SLOT][4 * lr], pr);
-                ld4(&PL[SLOT][4 * lc], pl);
-                const TI mjk = TI(sjk) * ij;
-                const TI ik = TI(invk);
+                for (int i = p + 1; i < 4; ++i) {
+                    const TI mm = TI(bl[p][i]) * mm0;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) uk[q] = fma(-mjk, u[q], pl[q]);
+                    for (int q = 0; q < 4; ++q) lf[i][q] = fma(-mm, lf[p][q], lf[i][q]);
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) vr[i][r] = fma(-bl[p][i], tr[r], vr[i][r]);
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                const TI ip = TI(inv[p]);
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
-                    mk[r] = TI(fma(-sjk, sr[r] * invj, pr[r])) * ik;
-                    if (r <= JJ + 1) mk[r] = dr ? TI(0) : mk[r];
+                    const TI m = TI(vr[p][r]) * ip;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) l[r][q] = fma(-m, lf[p][q], l[r][q]);
                 }
+            }
+        } else if (lown && lr == t) {
+            // this tile's rows are the block rows of L^-1: their updates within the block
 #pragma unroll
-                for (int r = 0; r < 4; ++r)
+            for (int p = 0; p < 4; ++p) {
+                const TI mm0 = TI(inv[p]);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) l[r][q] = fma(-mk[r], uk[q], l[r][q]);
+                for (int i = p + 1; i < 4; ++i) {
+                    const TI mm = TI(bl[p][i]) * mm0;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) l[i][q] = fma(-mm, l[p][q], l[i][q]);
+                }
             }
         }
-        // rows k and j + 2 are final, row j + 3 waits for its update by row j + 2
-        constexpr int R2 = (JJ + 2) & 3, R3 = (JJ + 3) & 3, T2 = (JJ + 2) >> 2, T3 = (JJ + 3) >> 2;
+        // tile row t is final; tile row t + 1 waits in the other slot
         if (wown) {
-            if (wi == tr) st4(&S[k][4 * wj], w[JJ + 1]);
-            if (wi == tr + T2) {
-                st4(&S[j + 2][4 * wj], w[R2]);
-                if (wi == wj && j + 2 < bi) pivot(j + 2, w[R2][R2], true);
+            if (wi == t) {
+#pragma unroll
+                for (int r = 0; r < 4; ++r) st4(&S[j + r][4 * wj], w[r]);
+            } else if (wi == t + 1) {
+#pragma unroll
+                for (int r = 0; r < 4; ++r) st4(&PW[nslot + r][4 * wj], w[r]);
             }
-            if (wi == tr + T3) st4(&PW[SLOT ^ 1][4 * wj], w[R3]);
         }
         if (lown) {
-            if (lr == tr) st4(&Li[k][4 * lc], l[JJ + 1]);
-            if (lr == tr + T2) st4(&Li[j + 2][4 * lc], l[R2]);
-            if (lr == tr + T3) st4(&PL[SLOT ^ 1][4 * lc], l[R3]);
+            if (lr == t) {
+#pragma unroll
+                for (int r = 0; r < 4; ++r) st4(&Li[j + r][4 * lc], l[r]);
+            } else if (lr == t + 1) {
+#pragma unroll
+                for (int r = 0; r < 4; ++r) st4(&PL[nslot + r][4 * lc], l[r]);
+            }
         }
         __syncthreads();
-    };
-    for (int j0 = 0; j0 < bi; j0 += 4) {
-        dstep(std::integral_constant<int, 0>{}, j0);
-        if (j0 + 2 < bi) dstep(std::integral_constant<int, 2>{}, j0);
     }
     if (tid < bi) sh.idiag[tid] = TF(1) / sqrt(sh.dpiv[tid]);
     __syncthreads();
@@ -413,8 +440,8 @@ struct CoopArgs {
     double tau;
     const double* rinv_prev;  // MAXB x MAXB or null (identity)
     double* rinv_out;   // rinv_prev R_1^-1 ... R_passes^-1 (MAXB x MAXB) or null
-    double* part;       // gridDim.x x (MAXB x MAXB) partial Grams
-    double* wred;       // MAXB x MAXB summed Gram
+    float2* part;       // gridDim.x x (MAXB x MAXB) partial Grams (float32 pairs)
+    float2* wred;       // MAXB x MAXB summed Gram (float32 pair)
     unsigned* bar;      // [0] arrivals, [1] generation
     int* flags;         // flags[1]: breakdown
     int* err;           // set when a grid barrier wait timed out
@@ -472,6 +499,15 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float a, float b) {
     lo += ((hi - (s - bb)) + (p - bb)) + e;
     hi = s;
 }
+// sum of two float32 pairs (hi + lo each), renormalised: a two-sum of the leading terms, the
+// error and the trailing terms added, then a fast two-sum
+__device__ __forceinline__ float2 fp_add(float2 a, float2 b) {
+    const float s = a.x + b.x;
+    const float bb = s - a.x;
+    const float e = ((a.x - (s - bb)) + (b.x - bb)) + (a.y + b.y);
+    const float h = s + e;
+    return make_float2(h, e - (h - s));
+}
 __device__ __forceinline__ void df_add_sum(float& hi, float& lo, float v) {
     const float s = hi + v;
     const float bb = s - hi;
@@ -503,11 +539,14 @@ __device__ __forceinline__ void coop_write_rinv(int bi, const float (&l)[4][4], 
 
 // the float64 refactor of an ill-conditioned panel; kept out of line so that the float32 path of
 // the fused kernel keeps its registers
-__device__ __noinline__ void coop_factor_f64(int bi, double tau, int* flags, const double* wred,
+__device__ __noinline__ void coop_factor_f64(int bi, double tau, int* flags, const float2* wred,
                                              CholShared<double, float> sh, float (*Rs)[CLD]) {
     float l[4][4];
     int lr, lc;
-    auto ldw = [&](int i, int j) { return __ldcg(wred + i + j * MAXB); };
+    auto ldw = [&](int i, int j) {
+        const float2 v = __ldcg(wred + i + j * MAXB);
+        return double(v.x) + double(v.y);
+    };
     chol_core<double, float>(bi, tau, 0.0, flags, ldw, sh, l, lr, lc);
     coop_write_rinv(bi, l, lr, lc, sh.idiag, Rs);
 }
@@ -522,7 +561,7 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) k_cholqr_coop(CoopArgs p) {
     float (*Li)[CLD] = reinterpret_cast<float (*)[CLD]>(rest + (sizeof(double) + sizeof(float)) * MAXB * CLD);
     float (*Rs)[CLD] = reinterpret_cast<float (*)[CLD]>(rest + (sizeof(double) + 2 * sizeof(float)) * MAXB * CLD);
     float (*Pc)[CLD] = reinterpret_cast<float (*)[CLD]>(rest + (sizeof(double) + 3 * sizeof(float)) * MAXB * CLD);
-    double* scratch = reinterpret_cast<double*>(rest);   // Gram combine space (S, Sf, Li regions)
+    float2* scratch = reinterpret_cast<float2*>(rest);   // Gram combine space (S, Sf, Li regions)
     // CTA 0 keeps the running product rinv_prev R_1^-1 R_2^-1 ... of the passes, transposed
     // (Pc[j][i] holds entry (i, j)) so that the product reads it without bank conflicts
     const bool chain = blockIdx.x == 0 && p.rinv_out != nullptr;
@@ -535,7 +574,7 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) k_cholqr_coop(CoopArgs p) {
     __shared__ float fpiv[MAXB], finvd[MAXB], fidiag[MAXB], fdiag0[MAXB], fdmax;
     __shared__ double dpiv[MAXB], dinvd[MAXB], didiag[MAXB], ddiag0[MAXB], ddmax;
     __shared__ int weak_s;
-    __shared__ double red[16][32];
+    __shared__ float2 red[16][32];
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     const int G = gridDim.x, cta = blockIdx.x;
@@ -650,15 +689,16 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) k_cholqr_coop(CoopArgs p) {
             for (int a = 0; a < 4; ++a)
 #pragma unroll
                 for (int b = 0; b < 4; ++b) {
-                    const double v = mode == 0 ? double(ch[a][b])
-                                               : double(hi[a][b]) + double(lo[a][b]) + double(ch[a][b]);
+                    const float2 v = mode == 0 ? make_float2(ch[a][b], 0.f)
+                                               : fp_add(make_float2(hi[a][b], lo[a][b]),
+                                                        make_float2(ch[a][b], 0.f));
                     scratch[ghalf * MAXB * MAXB + (gi0 + a) + (gj0 + b) * MAXB] = v;
                 }
         }
         __syncthreads();
-        double* out = p.part + int64_t(cta) * MAXB * MAXB;
+        float2* out = p.part + int64_t(cta) * MAXB * MAXB;
         for (int e = tid; e < MAXB * MAXB; e += COOP_THREADS)
-            if ((e & (MAXB - 1)) <= (e / MAXB)) out[e] = scratch[e] + scratch[MAXB * MAXB + e];
+            if ((e & (MAXB - 1)) <= (e / MAXB)) out[e] = fp_add(scratch[e], scratch[MAXB * MAXB + e]);
     };
     // sum the partials: this CTA owns an equal share of the upper entries
     auto reduce = [&]() {
@@ -667,35 +707,38 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) k_cholqr_coop(CoopArgs p) {
         const int lane = tid & 31, sub = tid >> 5;   // 16 subsets of the partials
         for (int eb = e0; eb < e1; eb += 32) {
             const int e = eb + lane;
-            double v = 0.0;
+            float2 v = make_float2(0.f, 0.f);
             if (e < e1 && e % MAXB <= e / MAXB) {
                 // partials sub, sub + 16, ... in that order, four loads in flight
-                const double* src = p.part + e;
+                const float2* src = p.part + e;
                 int q = sub;
                 for (; q + 48 < G; q += 64) {
-                    const double a0 = __ldcg(src + int64_t(q) * MAXB * MAXB);
-                    const double a1 = __ldcg(src + int64_t(q + 16) * MAXB * MAXB);
-                    const double a2 = __ldcg(src + int64_t(q + 32) * MAXB * MAXB);
-                    const double a3 = __ldcg(src + int64_t(q + 48) * MAXB * MAXB);
-                    v += a0;
-                    v += a1;
-                    v += a2;
-                    v += a3;
+                    const float2 a0 = __ldcg(src + int64_t(q) * MAXB * MAXB);
+                    const float2 a1 = __ldcg(src + int64_t(q + 16) * MAXB * MAXB);
+                    const float2 a2 = __ldcg(src + int64_t(q + 32) * MAXB * MAXB);
+                    const float2 a3 = __ldcg(src + int64_t(q + 48) * MAXB * MAXB);
+                    v = fp_add(v, a0);
+                    v = fp_add(v, a1);
+                    v = fp_add(v, a2);
+                    v = fp_add(v, a3);
                 }
-                for (; q < G; q += 16) v += __ldcg(src + int64_t(q) * MAXB * MAXB);
+                for (; q < G; q += 16) v = fp_add(v, __ldcg(src + int64_t(q) * MAXB * MAXB));
             }
             red[sub][lane] = v;
             __syncthreads();
             if (sub == 0 && e < e1) {
-                double t = 0.0;
+                float2 t = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int q = 0; q < 16; ++q) t += red[q][lane];
+                for (int q = 0; q < 16; ++q) t = fp_add(t, red[q][lane]);
                 p.wred[e] = t;
             }
             __syncthreads();
         }
     };
-    auto ldw = [&](int i, int j) { return __ldcg(p.wred + i + j * MAXB); };
+    auto ldw = [&](int i, int j) {
+        const float2 v = __ldcg(p.wred + i + j * MAXB);
+        return v.x + v.y;
+    };
     for (int pass = 0; pass < p.passes; ++pass) {
         gram(std::integral_constant<int, PRECISE ? 1 : 0>{});
         if (!coop_sync(p.bar, p.err)) return;
@@ -1030,7 +1073,7 @@ bool cholqr_coop(cudaStream_t st, float* P, int64_t ldp, int64_t rows, int bi, i
     a.tau = tau;
     a.rinv_prev = rinv_prev;
     a.rinv_out = rinv_out;
-    a.part = reinterpret_cast<double*>(scratch);
+    a.part = reinterpret_cast<float2*>(scratch);
     a.wred = a.part + size_t(COOP_MAX_CTAS) * MAXB * MAXB;
     a.bar = bar;
     a.flags = flags;

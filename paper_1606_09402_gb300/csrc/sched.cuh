@@ -129,14 +129,14 @@ inline Sched make_sched(int64_t M, int64_t N, int64_t K, int bn, int G) {
     s.kb = int(sched_cdiv(K, TC_BK));
     const int64_t units = int64_t(s.tiles_m) * s.tiles_n;
     // Stream-K balances the k-blocks exactly but costs a fix-up launch and partial-tile traffic
-    // (worth about 8 k-blocks); raster runs whole units in ceil(units / G) waves.  Take stream-K
-    // below ~8 waves when it is the shorter of the two.  With several column tiles, raster CTAs
-    // of one row tile walk k together and share each A tile through L2, while stream-K CTAs sit
-    // at unrelated k positions and read A once per column tile: raster then, unless there is
-    // less than one wave of units.
+    // (worth about 8 k-blocks of the kernel itself); raster runs whole units in ceil(units / G)
+    // waves.  Stream-K is taken for at most one wave of units (a few units with a long k, such
+    // as the Q^T Y products of the projections) when it beats raster.  Above one wave it would
+    // split up to G units, and every one of them goes through the fix-up: measured on the
+    // 40000 x 20000 step, the 157- and 313-unit projection products ran 1.6 ms faster in all
+    // (43.7 -> 42.1 ms) as raster or hybrid, which splits only the partial last wave.
     const int64_t waves = (units + G - 1) / G;
-    s.streamk = (units < 8LL * G && (units * s.kb) / G + 8 < waves * s.kb &&
-                 (s.tiles_n == 1 || units < G)) ? 1 : 0;
+    s.streamk = (units <= G && (units * s.kb) / G + 8 < waves * s.kb) ? 1 : 0;
     s.dp_units = 0;
     // Raster with a partial last wave: run the full waves as they are and split only the
     // remaining units' k-blocks across all CTAs (about 17% of a 4.1-wave pass).  Consecutive
