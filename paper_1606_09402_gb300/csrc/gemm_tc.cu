@@ -685,9 +685,11 @@ k_tc_prec(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
             float* pslot = sg.slot >= 0
                                ? p.part + ((int64_t(cta) * 2 + sg.slot) * BN + h * HC) * BM
                                : nullptr;
-            float accr[HC];
+            // the running sums, two columns per packed float32 pair add (round-to-nearest per
+            // element, so the same sums as scalar adds at half the instructions)
+            float2 acc2[HC / 2];
 #pragma unroll
-            for (int j = 0; j < HC; ++j) accr[j] = 0.f;
+            for (int j = 0; j < HC / 2; ++j) acc2[j] = make_float2(0.f, 0.f);
             for (int k0 = sg.k0; k0 < sg.k1 && ok; k0 += PREC_CHUNK) {
                 const int k1 = min(sg.k1, k0 + PREC_CHUNK);
                 for (int kb = k0; kb < k1 && ok; ++kb) {
@@ -699,7 +701,8 @@ k_tc_prec(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
                             float v[64];
                             tmem_ld64(tm_big + lane_off + uint32_t(slot * BN) + col_off, v);
 #pragma unroll
-                            for (int j = 0; j < 64; ++j) accr[j] += v[j];
+                            for (int j = 0; j < 32; ++j)
+                                acc2[j] = __fadd2_rn(acc2[j], make_float2(v[2 * j], v[2 * j + 1]));
                         } else {
 #pragma unroll
                             for (int cc = 0; cc < HC; cc += 32) {
@@ -707,7 +710,9 @@ k_tc_prec(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
                                 tmem_ld32(tm_big + lane_off + uint32_t(slot * BN) + col_off +
                                               uint32_t(cc), v);
 #pragma unroll
-                                for (int j = 0; j < 32; ++j) accr[cc + j] += v[j];
+                                for (int j = 0; j < 16; ++j)
+                                    acc2[cc / 2 + j] = __fadd2_rn(acc2[cc / 2 + j],
+                                                                  make_float2(v[2 * j], v[2 * j + 1]));
                             }
                         }
                         tc_fence_before();
@@ -726,7 +731,9 @@ k_tc_prec(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
                         float v[32];
                         tmem_ld32(tm_small + lane_off + uint32_t(sbuf * BN) + col_off + uint32_t(cc), v);
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) accr[cc + j] += v[j];
+                        for (int j = 0; j < 16; ++j)
+                            acc2[cc / 2 + j] = __fadd2_rn(acc2[cc / 2 + j],
+                                                          make_float2(v[2 * j], v[2 * j + 1]));
                     }
                     tc_fence_before();
                     mbar_arrive(sempty + sbuf);
@@ -735,6 +742,12 @@ k_tc_prec(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
                 }
             }
             if (!ok) break;
+            float accr[HC];
+#pragma unroll
+            for (int j = 0; j < HC / 2; ++j) {
+                accr[2 * j] = acc2[j].x;
+                accr[2 * j + 1] = acc2[j].y;
+            }
             if (pslot) {
 #pragma unroll
                 for (int j = 0; j < HC; ++j) pslot[int64_t(j) * BM + row] = accr[j];
