@@ -335,7 +335,11 @@ struct Ctx {
                 return !f64 && coop(Pj, ld, rows, bj, passes, h, slo, xb_ld);
             };
             project(j0, Pj, bj);
-            if (fused(2, again ? nullptr : shi)) shadow = !again;
+            // a panel that is projected again gets one CholeskyQR pass before the second
+            // projection and one after it (the second pass restores float32 orthogonality);
+            // a panel that is not projected again gets both passes here
+            if (fused(again ? 1 : 2, again ? nullptr : shi)) shadow = !again;
+            else if (again && !f64) cholqr(Pj, ld, rows, bj, false, true);
             else cholqr2(Pj, ld, rows, bj, false, true);
             if (again) {
                 project(j0, Pj, bj);
