@@ -177,11 +177,11 @@ struct Ctx {
     // product of the inverses joins the Rchain: multiplied into the last slot when that slot came
     // from this path too (the slots are applied in order, so a product of consecutive ones is the
     // same), else into a new slot.
-    bool coop_precise(void* P, int64_t ld, int64_t rows, int bi, bool acc_r) {
+    bool coop_precise(void* P, int64_t ld, int64_t rows, int bi, bool acc_r, int passes = 2) {
         if (f64 || (acc_r && nchain >= 4)) return false;
         const bool merge = acc_r && nchain > 0 && chain_fused;
         double* slot = acc_r ? Rchain + size_t(merge ? nchain - 1 : nchain) * MAXB * MAXB : nullptr;
-        if (!cholqr_coop(st, reinterpret_cast<float*>(P), ld, rows, bi, 2, true, tau,
+        if (!cholqr_coop(st, reinterpret_cast<float*>(P), ld, rows, bi, passes, true, tau,
                          merge ? slot : nullptr, slot, coop_scr, coop_bytes,
                          reinterpret_cast<unsigned*>(flags + 4), flags, flags + 2))
             return false;
@@ -215,6 +215,18 @@ struct Ctx {
         if (!sketch && coop_precise(P, ld, rows, bi, acc_r)) return;
         cholqr(P, ld, rows, bi, acc_r, sketch);
         cholqr(P, ld, rows, bi, acc_r, sketch);
+    }
+    // orth(P) of a block that is re-orthogonalised and orthonormalised again right after: one
+    // CholeskyQR pass on the mixed path (the passes after the re-orthogonalisation restore
+    // float32 orthogonality), CholeskyQR2 on the float64 path
+    void cholqr_pre(void* P, int64_t ld, int64_t rows, int bi, bool acc_r) {
+        if (f64) {
+            cholqr2(P, ld, rows, bi, acc_r);
+            return;
+        }
+        Scope sc(*this, PH_CHOLQR);
+        if (coop_precise(P, ld, rows, bi, acc_r, 1)) return;
+        cholqr(P, ld, rows, bi, acc_r);
     }
     // P <- P - Qk (Qk^T P), Qk = first k columns of Q (ld ldq); T: k x bi scratch (ld k)
     void project_out(const void* Q, int64_t ldq, int64_t k, void* P, int64_t ldp, int64_t rows, int bi,
@@ -774,7 +786,8 @@ void run_ei(Ctx& c, AOp& A, const Plan& p, const qb_opts& o, Bufs& bf, void* Q, 
                 c.q_t(k, bi, Q, ldq, m, -1.0, bf.T1, k, Y, ldq, c.acc_proj);      // Y -= Q (.)
             }
         }
-        c.cholqr2(Y, ldq, m, bi, false);                                          // Q_i = orth(Y)
+        if (k > 0) c.cholqr_pre(Y, ldq, m, bi, false);                            // Q_i = orth(Y)
+        else c.cholqr2(Y, ldq, m, bi, false);
         if (k > 0) {                                                              // re-orthogonalise
             c.reorth_q(k, Q, ldq, m, Y, ldq, bi, bf.T1);
             c.cholqr2(Y, ldq, m, bi, false);
@@ -878,7 +891,8 @@ void run_fp(Ctx& c, AOp& A, const Plan& p, const qb_opts& o, Bufs& bf, void* Q, 
                 c.copy_cols_(bf.Ys, m, m, bi, Qi, ldq);
                 c.nchain = 0;
                 c.chain_fused = false;
-                c.cholqr2(Qi, ldq, m, bi, true);
+                if (k > 0) c.cholqr_pre(Qi, ldq, m, bi, true);
+                else c.cholqr2(Qi, ldq, m, bi, true);
                 if (k > 0) {
                     // [Q_i, R~_i] = qr(Q_i - Q (Q^T Q_i)), R_i = R~_i R_i
                     c.reorth_q(k, Q, ldq, m, Qi, ldq, bi, bf.C2);
@@ -895,8 +909,9 @@ void run_fp(Ctx& c, AOp& A, const Plan& p, const qb_opts& o, Bufs& bf, void* Q, 
                         c.qt_x(k, bi, Q, ldq, m, bf.Ys, m, 1.0, bf.C2, k, c.acc_fine); // += Q^T Y_i
                         c.bt_t(k, bi, B, ldb, n, -1.0, bf.C2, k, S, n, c.acc_fine);    // S^T -= B^T C2
                     }
-                    // B_i = R_i^-T S  <=>  B_i^T = S^T R_i^-1, R_i = R~_2 R~_1 R_2 R_1 (the four
-                    // CholeskyQR factors): apply R_1^-1, R_2^-1, R~_1^-1, R~_2^-1 in turn
+                    // B_i = R_i^-T S  <=>  B_i^T = S^T R_i^-1, R_i the product of the CholeskyQR
+                    // factors (R~_2 R~_1 R_1 on the mixed path, R~_2 R~_1 R_2 R_1 on the float64
+                    // path): apply their inverses in turn (Rchain, consecutive fused ones merged)
                     for (int f = 0; f < c.nchain; ++f)
                         apply_rinv(c.st, c.f64, S, n, n, bi, c.Rchain + size_t(f) * MAXB * MAXB);
                     c.copy_cols_(S, n, n, bi, Bs, ldb);
