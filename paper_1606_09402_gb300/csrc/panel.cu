@@ -809,23 +809,27 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) k_cholqr_coop(CoopArgs p) {
                 const int bw = base + warp, CG = bw & 1;
                 const int rg = 4 * (bw >> 1) + (lane >> 3), cg = 8 * CG + (lane & 7);
                 const bool act = bw < nblk && rg < nrg;
-                float acc[8][4];
+                // acc[rp][c] holds rows 8 rg + 2 rp and 8 rg + 2 rp + 1 of column 4 cg + c: packed
+                // float32-pair FMAs (round-to-nearest per element, the same sums as scalar FMAs)
+                float2 acc[4][4];
 #pragma unroll
-                for (int rr = 0; rr < 8; ++rr)
+                for (int rp = 0; rp < 4; ++rp)
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) acc[rr][c] = 0.f;
+                    for (int c = 0; c < 4; ++c) acc[rp][c] = make_float2(0.f, 0.f);
                 if (act) {
                     const int qmax = min(bi, 32 * CG + 32);
                     for (int q2 = 0; q2 < qmax; ++q2) {
                         const float4 u0 = *reinterpret_cast<const float4*>(Pt + pcol(q2) + 8 * rg);
                         const float4 u1 = *reinterpret_cast<const float4*>(Pt + pcol(q2) + 8 * rg + 4);
                         const float4 rv = *reinterpret_cast<const float4*>(&Rs[q2][4 * cg]);
-                        const float u[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
-                        const float w4[4] = {rv.x, rv.y, rv.z, rv.w};
+                        const float2 u[4] = {make_float2(u0.x, u0.y), make_float2(u0.z, u0.w),
+                                             make_float2(u1.x, u1.y), make_float2(u1.z, u1.w)};
+                        const float2 w2[4] = {make_float2(rv.x, rv.x), make_float2(rv.y, rv.y),
+                                              make_float2(rv.z, rv.z), make_float2(rv.w, rv.w)};
 #pragma unroll
-                        for (int rr = 0; rr < 8; ++rr)
+                        for (int rp = 0; rp < 4; ++rp)
 #pragma unroll
-                            for (int c = 0; c < 4; ++c) acc[rr][c] = fmaf(u[rr], w4[c], acc[rr][c]);
+                            for (int c = 0; c < 4; ++c) acc[rp][c] = __ffma2_rn(u[rp], w2[c], acc[rp][c]);
                     }
                 }
                 __syncthreads();
@@ -834,8 +838,10 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) k_cholqr_coop(CoopArgs p) {
                     for (int c = 0; c < 4; ++c) {
                         float* dst = Pt + pcol(4 * cg + c) + 8 * rg;
 #pragma unroll
-                        for (int rr = 0; rr < 8; ++rr)
-                            if (8 * rg + rr < tn) dst[rr] = acc[rr][c];
+                        for (int rp = 0; rp < 4; ++rp) {
+                            if (8 * rg + 2 * rp < tn) dst[2 * rp] = acc[rp][c].x;
+                            if (8 * rg + 2 * rp + 1 < tn) dst[2 * rp + 1] = acc[rp][c].y;
+                        }
                     }
                 }
             }
