@@ -349,9 +349,12 @@ struct Ctx {
             project(j0, Pj, bj);
             // a panel that is projected again gets one CholeskyQR pass before the second
             // projection and one after it (the second pass restores float32 orthogonality);
-            // a panel that is not projected again gets both passes here
-            if (fused(again ? 1 : 2, again ? nullptr : shi)) shadow = !again;
-            else if (again && !f64) cholqr(Pj, ld, rows, bj, false, true);
+            // without re-orthogonalisation (G of the power scheme, which only has to be a
+            // well-conditioned basis for the next application of A^T) one pass in all on the
+            // mixed path; otherwise CholeskyQR2 here
+            const bool one = again || !reorth;
+            if (fused(one ? 1 : 2, again ? nullptr : shi)) shadow = !again;
+            else if (one && !f64) cholqr(Pj, ld, rows, bj, false, true);
             else cholqr2(Pj, ld, rows, bj, false, true);
             if (again) {
                 project(j0, Pj, bj);
