@@ -77,7 +77,11 @@ typedef enum {
 /* Dense row-major A.  dtype QB_BF16X2 stores A = a_hi + a_lo as two bf16 arrays with the same
  * ld (see qb_quantize_bf16x2); sketch passes read a_hi only, the passes that form B_i (EI) or
  * H (FP) read both.  src_norm2 = ||A_src||_F^2 of the float64 source the bf16 arrays were made
- * from; pass a NaN to have the library compute ||A||_F^2 from the stored A. */
+ * from; pass a NaN to have the library compute ||A||_F^2 from the stored A.
+ * a_lo_ready: NULL, or a cudaEvent_t (as void*) recorded after the last write of a_lo on another
+ * stream.  The call makes its stream wait on the event right before its first read of a_lo, so
+ * a_lo may still be arriving (a host-to-device copy on a second stream) while the sketches of
+ * randQB_FP's power scheme run on a_hi.  Ignored by the batched path. */
 typedef struct {
     int64_t m, n, ld;
     int32_t dtype;
@@ -85,6 +89,7 @@ typedef struct {
     const void* a;
     const void* a_lo;
     double src_norm2;
+    const void* a_lo_ready;
 } qb_dense;
 
 /* CSR A: rowptr[m+1], colind[nnz] (int32, zero-based, any order inside a row), val[nnz] of

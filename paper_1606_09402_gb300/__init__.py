@@ -120,7 +120,7 @@ def _info(rc, inf):
 
 
 def _dense_call(fn, name, A, tol, b, P, seed, relative, rank_cap, l_tilde, row_by_row, prec,
-                a_lo, src_norm2, stream, out, workspace, flags=0):
+                a_lo, src_norm2, stream, out, workspace, flags=0, a_lo_ready=None):
     torch = _torch()
     lib = _lib.load()
     _check_dev(A, a_lo)
@@ -133,7 +133,8 @@ def _dense_call(fn, name, A, tol, b, P, seed, relative, rank_cap, l_tilde, row_b
         dt = _dtype_code(A)
     d = _lib.qb_dense(m=m, n=n, ld=A.stride(0), dtype=dt, reserved=0, a=A.data_ptr(),
                       a_lo=a_lo.data_ptr() if a_lo is not None else None,
-                      src_norm2=float("nan") if src_norm2 is None else float(src_norm2))
+                      src_norm2=float("nan") if src_norm2 is None else float(src_norm2),
+                      a_lo_ready=a_lo_ready.cuda_event if a_lo_ready is not None else None)
     o = _opts(tol, b, P, seed, relative, rank_cap, l_tilde, row_by_row, prec, flags)
     algo = 1 if name.startswith("qb_fp") else 0
     wsb = lib.qb_dense_workspace(C.byref(d), C.byref(o), algo)
@@ -157,22 +158,25 @@ def _dense_call(fn, name, A, tol, b, P, seed, relative, rank_cap, l_tilde, row_b
 
 def qb_ei_dense(A, tol, b, P=0, seed=0, relative=True, rank_cap=None, row_by_row=True,
                 prec="fp64", a_lo=None, src_norm2=None, stream=None, out=None, workspace=None,
-                flags=0):
+                flags=0, a_lo_ready=None):
     """randQB_EI (Algorithm 2) on a dense row-major A; returns (Q, B, QBInfo).
 
-    Q is an m x rank view (column-major storage), B a rank x n row-major view."""
+    Q is an m x rank view (column-major storage), B a rank x n row-major view.  a_lo_ready: an
+    optional torch.cuda.Event recorded after a_lo's last write on another stream; the call waits
+    on it right before its first read of a_lo."""
     return _dense_call(_lib.load().qb_ei_dense, "qb_ei_dense", A, tol, b, P, seed, relative,
                        rank_cap, None, row_by_row, prec, a_lo, src_norm2, stream, out, workspace,
-                       flags)
+                       flags, a_lo_ready)
 
 
 def qb_fp_dense(A, tol, b, P=0, seed=0, relative=True, rank_cap=None, l_tilde=None,
                 row_by_row=True, prec="fp64", a_lo=None, src_norm2=None, stream=None, out=None,
-                workspace=None, flags=0):
-    """randQB_FP (Algorithm 4) on a dense row-major A; returns (Q, B, QBInfo)."""
+                workspace=None, flags=0, a_lo_ready=None):
+    """randQB_FP (Algorithm 4) on a dense row-major A; returns (Q, B, QBInfo).  a_lo_ready as in
+    qb_ei_dense: the power scheme's sketches read A_hi only, so A_lo can still be arriving."""
     return _dense_call(_lib.load().qb_fp_dense, "qb_fp_dense", A, tol, b, P, seed, relative,
                        rank_cap, l_tilde, row_by_row, prec, a_lo, src_norm2, stream, out,
-                       workspace, flags)
+                       workspace, flags, a_lo_ready)
 
 
 def _csr_call(fn, name, rowptr, colind, val, shape, tol, b, P, seed, relative, rank_cap, l_tilde,

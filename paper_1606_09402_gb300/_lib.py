@@ -35,7 +35,7 @@ QB_PREC_FP64, QB_PREC_MIXED = 0, 1
 class qb_dense(C.Structure):
     _fields_ = [("m", C.c_int64), ("n", C.c_int64), ("ld", C.c_int64), ("dtype", C.c_int32),
                 ("reserved", C.c_int32), ("a", C.c_void_p), ("a_lo", C.c_void_p),
-                ("src_norm2", C.c_double)]
+                ("src_norm2", C.c_double), ("a_lo_ready", C.c_void_p)]
 
 
 class qb_csr(C.Structure):

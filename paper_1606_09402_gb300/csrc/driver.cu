@@ -416,7 +416,16 @@ struct DenseOp : AOp {
     size_t tc_bytes = 0;
     bf16* Xb = nullptr;      // bf16 copy of the sketch operand (tensor-core path)
     int64_t wmax = 0;
+    bool lo_waited = false;
     explicit DenseOp(const qb_dense& dd) : d(dd) { m = dd.m; n = dd.n; }
+    // before the first read of a_lo: wait for the caller's event (a_lo may still be arriving)
+    void wait_lo(Ctx& c) {
+        if (d.a_lo_ready && d.a_lo && !lo_waited) {
+            cudaEvent_t ev = reinterpret_cast<cudaEvent_t>(const_cast<void*>(d.a_lo_ready));
+            QB_CUDA(cudaStreamWaitEvent(c.st, ev, 0));
+            lo_waited = true;
+        }
+    }
     XOp xa(bool precise) const {
         switch (d.dtype) {
             case QB_F64: return XOp{X_F64, d.a, nullptr, d.ld};
@@ -476,6 +485,7 @@ struct DenseOp : AOp {
     void apply_t(Ctx& c, const void* X, int64_t ldx, int64_t w, void* Y, int64_t ldy,
                  int mode) override {
         Ctx::Scope sc(c, PH_TRANS);
+        if (mode >= 2) wait_lo(c);                 // mode 1 reads a_hi only
         if (use_tc && mode >= 2) {
             // The passes that feed the indicator (B_i = Q_i^T A, H = A^T G): full A, the operand
             // split exactly into bf16 terms, the leading product summed per MMA in registers with
@@ -511,6 +521,7 @@ struct DenseOp : AOp {
     }
     double norm2(Ctx& c) override {
         if (!std::isnan(d.src_norm2)) return d.src_norm2;
+        wait_lo(c);
         dense_norm2(c.st, xa(true), m, n, c.part, c.state + 4, c.flags);
         double h = 0;
         QB_CUDA(cudaMemcpyAsync(&h, c.state + 4, sizeof h, cudaMemcpyDeviceToHost, c.st));

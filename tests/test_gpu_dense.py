@@ -293,3 +293,32 @@ def test_mixed_tall_panels(A_tall, alg):
     orth = (Qd.T @ Qd - torch.eye(info.rank, dtype=torch.float64, device="cuda")).abs().max().item()
     assert orth <= 1e-4
     assert abs(info.err2_est - (err ** 2) * info.normA2) <= 4 * 2.0 ** -24 * info.normA2
+
+
+@pytest.mark.parametrize("alg", ["ei", "fp"])
+def test_a_lo_ready_event(A_mixed, alg):
+    """A_lo still arriving when the call starts: a second stream first spins (~20 ms of device
+    clock cycles) and only then copies A_lo from the host, recording the event the call receives.
+    The call must wait for it before its first read of A_lo: Q, B and the rank are bit-identical
+    to the call on a fully resident A_lo (a missed wait would read the zeros A_lo starts from)."""
+    A = torch.tensor(A_mixed, device="cuda")
+    hi, lo, norms = qb.quantize_bf16x2(A)
+    del A
+    f = qb.qb_ei_dense if alg == "ei" else qb.qb_fp_dense
+    Q0, B0, i0 = f(hi, 1e-3, 32, P=1, seed=21, a_lo=lo, src_norm2=norms[0], prec="mixed")
+    Q0, B0 = Q0.clone(), B0.clone()
+    lo_h = lo.cpu().pin_memory()
+    lo_d = torch.zeros_like(lo)
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    ready = torch.cuda.Event()
+    with torch.cuda.stream(side):
+        torch.cuda._sleep(40_000_000)
+        lo_d.copy_(lo_h, non_blocking=True)
+        ready.record(side)
+    Q1, B1, i1 = f(hi, 1e-3, 32, P=1, seed=21, a_lo=lo_d, src_norm2=norms[0], prec="mixed",
+                   a_lo_ready=ready)
+    torch.cuda.synchronize()
+    assert i1.rank == i0.rank and i1.status == i0.status
+    assert torch.equal(Q1, Q0) and torch.equal(B1, B0)
+
