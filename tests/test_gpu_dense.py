@@ -322,3 +322,27 @@ def test_a_lo_ready_event(A_mixed, alg):
     assert i1.rank == i0.rank and i1.status == i0.status
     assert torch.equal(Q1, Q0) and torch.equal(B1, B0)
 
+
+@pytest.mark.parametrize("alg", ["ei", "fp"])
+def test_mixed_ill_conditioned_blocks(alg):
+    """sigma_j = exp(-j / 10): inside one 64-column block the singular values fall by
+    e^6.4 ~ 600, so both Q_i panels (rank ~70: the first block, and the second, which gets one
+    CholeskyQR pass before its re-orthogonalisation) reach kappa above the float32 factor's
+    weak-pivot limit (~100) and go through the float64 refactor of the fused CholeskyQR.  The
+    result must still meet the tolerance, with a rank close to the float64 oracle's and Q
+    orthonormal to float32 accuracy."""
+    A = synth.dense_from_spectrum(4000, 3000, synth.sigma_exp(3000, 10.0, 1e-9), seed=33)
+    tol = 1e-3
+    Ad = torch.tensor(A, device="cuda")
+    hi, lo, norms = qb.quantize_bf16x2(Ad)
+    del Ad
+    f = qb.qb_ei_dense if alg == "ei" else qb.qb_fp_dense
+    Q, B, info = f(hi, tol, 64, P=1, seed=5, a_lo=lo, src_norm2=norms[0], prec="mixed")
+    assert info.converged
+    err = np.linalg.norm(A - _qb(Q, B)) / np.linalg.norm(A)
+    assert err < tol, err
+    ref = (oracle.randqb_ei if alg == "ei" else oracle.randqb_fp)(A, tol, 64, seed=5, P=1)
+    assert ref.rank - 2 <= info.rank <= ref.rank + max(4, 0.05 * ref.rank), (info.rank, ref.rank)
+    Qd = Q.double()
+    orth = float(torch.linalg.norm(Qd.T @ Qd - torch.eye(Q.shape[1], device=Q.device, dtype=torch.float64)))
+    assert orth < 1e-4, orth
