@@ -915,13 +915,13 @@ void run_fp(Ctx& c, AOp& A, const Plan& p, const qb_opts& o, Bufs& bf, void* Q, 
                 char* Bs = c.col(B, ldb, k);
                 {
                     Ctx::Scope scb(c, PH_BFORM);
-                    // S^T = H_i - B^T (Q^T Y_i + B Omega_i), i.e. S = H_i^T - Y_i^T Q B - Omega_i^T B^T B
-                    char* S = bf.Z;
-                    c.copy_cols_(c.col(bf.H, n, c0), n, n, bi, S, n);
+                    // S^T = H_i - B^T (Q^T Y_i + B Omega_i), i.e. S = H_i^T - Y_i^T Q B - Omega_i^T B^T B,
+                    // formed in place in H_i's columns (H_i is read only here)
+                    char* S = c.col(bf.H, n, c0);
                     if (k > 0) {
-                        c.copy_cols_(bf.T1, k, k, bi, bf.C2, k);                      // C2 = B Omega_i
-                        c.qt_x(k, bi, Q, ldq, m, bf.Ys, m, 1.0, bf.C2, k, c.acc_fine); // += Q^T Y_i
-                        c.bt_t(k, bi, B, ldb, n, -1.0, bf.C2, k, S, n, c.acc_fine);    // S^T -= B^T C2
+                        // T1 still holds B Omega_i from the projection of Y_i
+                        c.qt_x(k, bi, Q, ldq, m, bf.Ys, m, 1.0, bf.T1, k, c.acc_fine); // += Q^T Y_i
+                        c.bt_t(k, bi, B, ldb, n, -1.0, bf.T1, k, S, n, c.acc_fine);    // S^T -= B^T T1
                     }
                     // B_i = R_i^-T S  <=>  B_i^T = S^T R_i^-1, R_i the product of the CholeskyQR
                     // factors (R~_2 R~_1 R_1 on the mixed path, R~_2 R~_1 R_2 R_1 on the float64

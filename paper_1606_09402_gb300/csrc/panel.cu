@@ -937,6 +937,34 @@ k_apply_rinv(T* __restrict__ P, int64_t ldp, int64_t m, int bi, const double* __
     }
 }
 
+// Squared norm of a float32 row: exact products summed as float32 pairs (two-sum), ~n u32^2 of
+// relative error; the float64 chain it replaces ran on GB300's slow float64 pipe.  The block's
+// partial pairs are combined in a fixed order (lanes by shuffles, then warps in order).
+__global__ void k_row_norm2_f32(const float* __restrict__ B, int64_t ldb, int64_t n, double* rn) {
+    const int j = blockIdx.x;
+    const float* row = B + int64_t(j) * ldb;
+    float hi = 0.f, lo = 0.f;
+    for (int64_t c = threadIdx.x; c < n; c += blockDim.x) {
+        const float v = row[c];
+        df_add(hi, lo, v, v);
+    }
+    float2 s = make_float2(hi, lo);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float2 t = make_float2(__shfl_down_sync(0xffffffffu, s.x, o),
+                                     __shfl_down_sync(0xffffffffu, s.y, o));
+        s = fp_add(s, t);
+    }
+    __shared__ float2 sh[32];
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float2 t = make_float2(0.f, 0.f);
+        for (int w = 0; w < int(blockDim.x >> 5); ++w) t = fp_add(t, sh[w]);
+        rn[j] = double(t.x) + double(t.y);
+    }
+}
+
 template <class T>
 __global__ void k_row_norm2(const T* __restrict__ B, int64_t ldb, int64_t n, double* rn) {
     const int j = blockIdx.x;
@@ -1125,7 +1153,7 @@ void row_norm2(cudaStream_t st, bool f64, const void* B, int64_t ldb, int rows, 
                double* rn) {
     if (rows <= 0) return;
     if (f64) k_row_norm2<double><<<rows, 256, 0, st>>>(reinterpret_cast<const double*>(B), ldb, n, rn);
-    else k_row_norm2<float><<<rows, 256, 0, st>>>(reinterpret_cast<const float*>(B), ldb, n, rn);
+    else k_row_norm2_f32<<<rows, 512, 0, st>>>(reinterpret_cast<const float*>(B), ldb, n, rn);
     QB_LAUNCHED();
 }
 
