@@ -228,6 +228,17 @@ struct Ctx {
         if (coop_precise(P, ld, rows, bi, acc_r, 1)) return;
         cholqr(P, ld, rows, bi, acc_r);
     }
+    // orth(P) inside a power step, where only the span matters: one float32 CholeskyQR pass on
+    // the mixed path (a well-conditioned basis is enough for the next application of A or A^T),
+    // CholeskyQR2 on the float64 path
+    void orth_span(void* P, int64_t ld, int64_t rows, int bi) {
+        if (f64) {
+            cholqr2(P, ld, rows, bi, false);
+            return;
+        }
+        Scope sc(*this, PH_ORTHW);
+        cholqr(P, ld, rows, bi, false, true);
+    }
     // P <- P - Qk (Qk^T P), Qk = first k columns of Q (ld ldq); T: k x bi scratch (ld k)
     void project_out(const void* Q, int64_t ldq, int64_t k, void* P, int64_t ldp, int64_t rows, int bi,
                      void* T, bool sketch = false) {
@@ -781,7 +792,7 @@ void run_ei(Ctx& c, AOp& A, const Plan& p, const qb_opts& o, Bufs& bf, void* Q, 
             c.q_t(k, bi, Q, ldq, m, -1.0, bf.T1, k, Y, ldq, c.acc_proj);          // Y -= Q (.)
         }
         for (int it = 0; it < p.P; ++it) {
-            c.cholqr2(Y, ldq, m, bi, false);                                      // Y = orth(Y)
+            c.orth_span(Y, ldq, m, bi);                                           // Y = orth(Y)
             A.round_operand(c, Y, ldq, m, bi);
             A.apply_t(c, Y, ldq, bi, bf.Z, n, 1);                                 // Z = A^T Y
             out.passes += 1;
@@ -790,7 +801,7 @@ void run_ei(Ctx& c, AOp& A, const Plan& p, const qb_opts& o, Bufs& bf, void* Q, 
                 c.qt_x(k, bi, Q, ldq, m, Y, ldq, 0.0, bf.T1, k, c.acc_proj);      // Q^T Y
                 c.bt_t(k, bi, B, ldb, n, -1.0, bf.T1, k, bf.Z, n, c.acc_proj);    // Z -= B^T (.)
             }
-            c.cholqr2(bf.Z, n, n, bi, false);                                     // Z = orth(Z)
+            c.orth_span(bf.Z, n, n, bi);                                          // Z = orth(Z)
             A.round_operand(c, bf.Z, n, n, bi);
             A.apply(c, bf.Z, n, bi, Y, ldq);                                      // Y = A Z
             out.passes += 1;
