@@ -910,9 +910,8 @@ template <int BN, bool TRANS, int NA, int NB>
 void run(cudaStream_t st, const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& b0,
          const CUtensorMap& b1, Params p, int G) {
     using C = Cfg<BN, TRANS, NA, NB>;
-    auto kern = k_tc_gemm<BN, TRANS, NA, NB>;
-    QB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
-    kern<<<G, NUM_THREADS, C::SMEM, st>>>(a0, a1, b0, b1, p);
+    smem_limit_once<k_tc_gemm<BN, TRANS, NA, NB>>(C::SMEM);
+    k_tc_gemm<BN, TRANS, NA, NB><<<G, NUM_THREADS, C::SMEM, st>>>(a0, a1, b0, b1, p);
     QB_LAUNCHED();
     if (p.s.streamk) {
         const dim3 grid(unsigned(split_units(p.s)), unsigned(BM * BN / 256));
@@ -933,9 +932,8 @@ template <int BN, bool TRANS, int NA, int NB>
 void run_prec(cudaStream_t st, const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& a2,
               const CUtensorMap& b0, const CUtensorMap& b1, const CUtensorMap& b2, Params p, int G) {
     using C = PCfg<BN, NA, NB>;
-    auto kern = k_tc_prec<BN, TRANS, NA, NB>;
-    QB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
-    kern<<<G, PREC_THREADS, C::SMEM, st>>>(a0, a1, a2, b0, b1, b2, p);
+    smem_limit_once<k_tc_prec<BN, TRANS, NA, NB>>(C::SMEM);
+    k_tc_prec<BN, TRANS, NA, NB><<<G, PREC_THREADS, C::SMEM, st>>>(a0, a1, a2, b0, b1, b2, p);
     QB_LAUNCHED();
     if (p.s.streamk) {
         const dim3 grid(unsigned(split_units(p.s)), unsigned(BM * BN / 256));

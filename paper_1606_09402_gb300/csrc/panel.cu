@@ -1028,39 +1028,34 @@ constexpr size_t chol_smem() {
 }
 constexpr size_t TRI_SMEM = sizeof(double) * 2 * MAXB * LDS;
 
-template <class K>
-void allow_smem(K kernel, size_t bytes) {
-    // idempotent, cheap; called before every launch so each device gets it
-    QB_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)));
-}
 
 void chol_rinv(cudaStream_t st, const double* W, int bi, double tau_rel, double* R, double* Rinv,
                double* R_acc, int* flags, CholPrec prec) {
     switch (prec) {
         case CHOL_F64: {
             constexpr size_t sm = chol_smem<double, double>();
-            allow_smem(k_chol<double, double, false>, sm);
+            smem_limit_once<k_chol<double, double, false>>(sm);
             k_chol<double, double, false><<<1, CHOL_THREADS, sm, st>>>(W, bi, tau_rel, R, Rinv,
                                                                        R_acc, flags);
             break;
         }
         case CHOL_F64_INV_F32: {
             constexpr size_t sm = chol_smem<double, float>();
-            allow_smem(k_chol<double, float, false>, sm);
+            smem_limit_once<k_chol<double, float, false>>(sm);
             k_chol<double, float, false><<<1, CHOL_THREADS, sm, st>>>(W, bi, tau_rel, R, Rinv,
                                                                       R_acc, flags);
             break;
         }
         case CHOL_ADAPTIVE: {
             constexpr size_t sm = chol_smem<double, float>();
-            allow_smem(k_chol<double, float, true>, sm);
+            smem_limit_once<k_chol<double, float, true>>(sm);
             k_chol<double, float, true><<<1, CHOL_THREADS, sm, st>>>(W, bi, tau_rel, R, Rinv,
                                                                      R_acc, flags);
             break;
         }
         default: {
             constexpr size_t sm = chol_smem<float, float>();
-            allow_smem(k_chol<float, float, false>, sm);
+            smem_limit_once<k_chol<float, float, false>>(sm);
             k_chol<float, float, false><<<1, CHOL_THREADS, sm, st>>>(W, bi, tau_rel, R, Rinv,
                                                                      R_acc, flags);
             break;
@@ -1128,7 +1123,7 @@ void set_identity(cudaStream_t st, double* R, int bi) {
 }
 
 void tri_inv(cudaStream_t st, const double* R, int bi, double* Rinv) {
-    allow_smem(k_tri_inv, TRI_SMEM);
+    smem_limit_once<k_tri_inv>(TRI_SMEM);
     k_tri_inv<<<1, 64, TRI_SMEM, st>>>(R, bi, Rinv);
     QB_LAUNCHED();
 }
@@ -1139,11 +1134,11 @@ void apply_rinv(cudaStream_t st, bool f64, void* P, int64_t ldp, int64_t m, int 
     const unsigned g = unsigned(cdiv(m, APPLY_ROWS));
     if (f64) {
         const size_t sm = sizeof(double) * (MAXB * MAXB + APPLY_ROWS * LDS);
-        allow_smem(k_apply_rinv<double>, sm);
+        smem_limit_once<k_apply_rinv<double>>(sm);
         k_apply_rinv<double><<<g, 256, sm, st>>>(reinterpret_cast<double*>(P), ldp, m, bi, Rinv);
     } else {
         const size_t sm = sizeof(float) * (MAXB * MAXB + APPLY_ROWS * LDS);
-        allow_smem(k_apply_rinv<float>, sm);
+        smem_limit_once<k_apply_rinv<float>>(sm);
         k_apply_rinv<float><<<g, 256, sm, st>>>(reinterpret_cast<float*>(P), ldp, m, bi, Rinv);
     }
     QB_LAUNCHED();

@@ -44,6 +44,20 @@ int64_t launches_total();
         }                                                                    \
     } while (0)
 
+// Raise kernel KERN's dynamic shared-memory limit to `bytes`, once per device (the attribute
+// outlives the call); later calls cost one cudaGetDevice.
+template <auto KERN>
+void smem_limit_once(size_t bytes) {
+    static std::atomic<unsigned> done{0};   // bit d: set on device d (devices 0..31)
+    int dev = 0;
+    QB_CUDA(cudaGetDevice(&dev));
+    const unsigned bit = dev < 32 ? 1u << dev : 0u;
+    if (bit && (done.load(std::memory_order_relaxed) & bit)) return;
+    QB_CUDA(cudaFuncSetAttribute(reinterpret_cast<const void*>(KERN),
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)));
+    done.fetch_or(bit, std::memory_order_relaxed);
+}
+
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 inline int64_t align_up(int64_t a, int64_t b) { return cdiv(a, b) * b; }
 
