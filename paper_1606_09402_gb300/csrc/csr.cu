@@ -111,7 +111,7 @@ template <> struct Vec<double, 4> {
 
 // acc += sum over p in [b, e) of val[p] * X[idx[p], lane*NQ .. lane*NQ+NQ).  The 32 (index, value)
 // pairs of a chunk are loaded once by the warp and broadcast; full chunks are unrolled so that
-// eight row gathers are in flight per warp.
+// 32 / NQ row gathers are in flight per warp (32 registers of gathered X per lane).
 // Positions are int64 so that p0 + 32 cannot wrap for nnz near INT32_MAX.
 template <class T, int NQ>
 __device__ __forceinline__ void row_acc(const int32_t* __restrict__ idx, const T* __restrict__ val,
@@ -133,7 +133,8 @@ __device__ __forceinline__ void row_acc(const int32_t* __restrict__ idx, const T
             for (int q = 0; q < NQ; ++q) acc[q] = fma(vv, x[q], acc[q]);
         };
         if (cnt == 32) {
-#pragma unroll 8
+            constexpr int UNR = 32 / NQ;
+#pragma unroll UNR
             for (int t = 0; t < 32; ++t) step(t);
         } else {
             for (int t = 0; t < cnt; ++t) step(t);
