@@ -21,12 +21,12 @@ constexpr int LDS = MAXB + 1;
 //
 // Work split: the 64 x 64 matrices are cut into 4 x 4 tiles held in registers.  Threads 0..135
 // own the upper tiles of W in row-major order (so the tiles that are finished form a prefix and
-// whole warps drop out), threads 160..295 the lower tiles of L^-1.  The elimination takes two
-// pivots per barrier: before the double step (j, j + 1) row j is final in shared memory and row
-// j + 1 waits there for the update by row j; every thread applies that update itself to the
-// entries of row j + 1 it needs (the same arithmetic its owner does), so the two rank-one updates
-// of a tile run back to back.  The owners then publish rows j + 1, j + 2 (final) and j + 3
-// (pending), the owner of the diagonal of row j + 2 also its pivot.
+// whole warps drop out), threads 160..295 the lower tiles of L^-1.  The elimination takes the four
+// pivots of a tile row per block barrier (a quad step): the tile row waits in shared memory with
+// every earlier update applied; every thread factors its 4 x 4 diagonal block and brings the block
+// rows up to date at the indices it needs (the same arithmetic as their owners), then applies the
+// four rank-one updates to its tile; the owners publish the tile row (final) and the next one
+// (pending).
 constexpr int CLD = MAXB + 4;          // shared row stride: rows stay 16-byte aligned
 // Pivot test of the adaptive factorisation: a float32 factor is kept when every pivot keeps at
 // least this fraction of its column's squared norm (kappa of the panel below about 100, so the
@@ -40,7 +40,7 @@ constexpr int CHOL_L0 = 160;           // first thread of the L^-1 tiles
 template <class TF, class TI>
 struct CholShared {
     TF (*S)[CLD];    // rows W'[j][.] of the elimination as they are finished (TF)
-    TI (*Sf)[CLD];   // scratch of MAXB rows of TI: holds the two-slot rings of pending rows
+    TI (*Sf)[CLD];   // scratch of MAXB rows of TI: holds the two-slot rings of pending tile rows
     TI (*Li)[CLD];   // rows of L^-1 as they are finished
     TF* dpiv;        // [MAXB] pivots d_j
     TF* invd;        // [MAXB] 1 / d_j
