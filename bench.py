@@ -379,7 +379,18 @@ def run_adjoint(torch, qb, dev, stream):
     qb.qb_fixed_rank_bwd(A, k, 9, Q, R, GQ, GB)
     tf = event_time(torch, lambda: qb.qb_fixed_rank_fwd(A, k, 9), 3, stream)
     tb = event_time(torch, lambda: qb.qb_fixed_rank_bwd(A, k, 9, Q, R, GQ, GB), 3, stream)
-    return {"m": m, "n": n, "k": k, "forward_s": tf, "backward_s": tb}
+    # algorithmic work: the forward is two passes over A (Y = A Omega, B = Q^T A), 4 m n k flops
+    # and 2 m n bf16 bytes each; the backward is A G_B^T and the K = 2k product for Abar
+    # (6 m n k flops), reading A once and writing the float32 Abar
+    pk, src = peaks()
+    fl_f, by_f = 4.0 * m * n * k, 2.0 * m * n * 2
+    fl_b, by_b = 6.0 * m * n * k, m * n * 2.0 + m * n * 4.0
+    frac = lambda fl, by, t: {"tflops": fl / t / 1e12, "gbs": by / t / 1e9,
+                              "tensor_frac": fl / t / 1e12 / pk["bf16_tflops"],
+                              "hbm_frac": by / t / 1e9 / pk["hbm_gbs"]}
+    return {"m": m, "n": n, "k": k, "forward_s": tf, "backward_s": tb,
+            "forward": frac(fl_f, by_f, tf), "backward": frac(fl_b, by_b, tb),
+            "peak_source": src + " (burst bf16, copy bandwidth)"}
 
 
 def run_paper_dense(torch, qb, dev, stream):

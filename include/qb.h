@@ -330,7 +330,7 @@ int32_t qb_svd_from_qb(int64_t m, int64_t n, int64_t k, int32_t prec, const void
  * V (align8(n) * w * 2 bytes, rounded up to 256) plus 10 MiB + 256 bytes of partial tiles and
  * flag must fit in the 16 MiB, so n <= 49144 at w = 64.  Larger calls return QB_ERR_WORKSPACE
  * before anything is launched.  The first call on a device looks the array's address up
- * (cudaGetSymbolAddress) and should come before any stream capture.  All calls share the array:
+ * (cudaGetSymbolAddress) and keeps it.  All calls share the array:
  * calls that overlap on the GPU (other streams, other host threads) race.  Every call ends by
  * copying the kernel's timeout flag to the host and synchronising the stream, so it returns
  * only after its work has completed.

@@ -202,6 +202,14 @@ struct Ctx {
                   f64 ? CHOL_F64 : (fast ? CHOL_F32 : CHOL_ADAPTIVE));
         apply_rinv(st, f64, P, ld, rows, bi, ri);
     }
+    // Fused CholeskyQR2 with the adaptive factor on the mixed path; Rinv receives
+    // R_1^-1 R_2^-1 = (R_2 R_1)^-1 (the fixed-rank map inverts it to keep R).  False: not launched.
+    bool coop_rinv(void* P, int64_t ld, int64_t rows, int bi) {
+        if (f64) return false;
+        return cholqr_coop(st, reinterpret_cast<float*>(P), ld, rows, bi, 2, true, tau, nullptr,
+                           Rinv, coop_scr, coop_bytes, reinterpret_cast<unsigned*>(flags + 4), flags,
+                           flags + 2);
+    }
     // CholeskyQR pass accumulating the factor: Racc <- R Racc (the fixed-rank map keeps R)
     void cholqr_racc(void* P, int64_t ld, int64_t rows, int bi) {
         gram(st, P, ld, rows, bi, f64, f64 ? ACC_D : acc_gram, W, scr);
@@ -1076,6 +1084,12 @@ void fixed_reserve(Arena& ar, Ctx& c, DenseOp& A, int64_t k, FixedBufs& f, bool 
         f.Gb = ar.get<char>(n * k * es);
     }
     A.reserve(ar, c, k);
+    if (!c.f64 && A.tc_scratch(&c.tcs, &c.tcs_bytes)) {
+        // three-term bf16 shadows of the finished panels of Q: the forward's Gram-Schmidt
+        // projections run on the tensor cores at float32 accuracy
+        c.ldqs = align_up(m, 8);
+        for (int t = 0; t < 3; ++t) c.qs[t] = ar.get<bf16>(c.ldqs * k);
+    }
     if (bwd && A.use_tc && n >= 128 && m >= 1) {
         f.kp = std::max<int64_t>(align_up(3 * k, 64), 128);   // at least one 128-wide K tile
         f.P1 = ar.get<bf16>(n * f.kp);
@@ -1097,16 +1111,23 @@ void fixed_fwd(Ctx& c, DenseOp& A, int64_t k, uint64_t seed, FixedBufs& f, void*
         char* Rj = c.col(R, ldr, j0);                           // R(0:j0, j0:j0+bj)
         if (j0 > 0) {
             for (int pass = 0; pass < 2; ++pass) {              // Gram-Schmidt, then re-orthogonalise
-                c.tn(j0, bj, m, 1.0, Q, ldq, Pj, ldq, 0.0, f.T, j0, c.acc_fine);
-                c.nn(m, bj, j0, -1.0, Q, ldq, f.T, j0, 1.0, Pj, ldq, c.acc_proj);
+                c.qt_x(j0, bj, Q, ldq, m, Pj, ldq, 0.0, f.T, j0, c.acc_fine);
+                c.q_t(j0, bj, Q, ldq, m, -1.0, f.T, j0, Pj, ldq, c.acc_proj);
                 axpy(c.st, c.f64, j0, bj, 1.0, f.T, j0, Rj, ldr);
             }
         }
-        set_identity(c.st, c.Racc, bj);
-        c.cholqr_racc(Pj, ldq, m, bj);                           // Q_j R_jj = P_j
-        c.cholqr_racc(Pj, ldq, m, bj);
         char* Rjj = reinterpret_cast<char*>(Rj) + size_t(j0) * c.es;
-        from_f64(c.st, c.f64, c.Racc, MAXB, bj, bj, Rjj, ldr);
+        if (c.coop_rinv(Pj, ldq, m, bj)) {                      // Q_j R_jj = P_j
+            tri_inv_from_f64(c.st, false, c.Rinv, MAXB, bj, Rjj, ldr);
+        } else {
+            set_identity(c.st, c.Racc, bj);
+            c.cholqr_racc(Pj, ldq, m, bj);
+            c.cholqr_racc(Pj, ldq, m, bj);
+            from_f64(c.st, c.f64, c.Racc, MAXB, bj, bj, Rjj, ldr);
+        }
+        if (c.tcg() && j0 + bj < k)
+            split3_bf16(c.st, reinterpret_cast<const float*>(Pj), ldq, m, bj, c.qs[0] + j0 * c.ldqs,
+                        c.qs[1] + j0 * c.ldqs, c.qs[2] + j0 * c.ldqs, c.ldqs);
     }
     A.apply_t(c, Q, ldq, k, B, ldb, 3);                         // B = Q^T A
 }

@@ -322,7 +322,8 @@ __global__ void k_axpy(int64_t rows, int64_t cols, T alpha, const T* __restrict_
 }
 
 // Inverse of an upper-triangular k x k R (column-major, ld), one column of X per thread, R read
-// through the cache; any k.
+// through the cache; any k.  Used only where k_tri_inv_cols' running sums do not fit in shared
+// memory.
 template <class T>
 __global__ void k_tri_inv_big(const T* __restrict__ R, int64_t ldr, int64_t k, T* __restrict__ X,
                               int64_t ldx) {
@@ -335,6 +336,42 @@ __global__ void k_tri_inv_big(const T* __restrict__ R, int64_t ldr, int64_t k, T
         for (int64_t l = i + 1; l <= c; ++l) s = fma(R[i + l * ldr], X[l + c * ldx], s);
         X[i + c * ldx] = -s / R[i + i * ldr];
     }
+}
+
+// Column c of X = R^-1 (R upper triangular, column-major) by one CTA: back substitution by
+// columns of R.  With s = e_c, for l = c, c - 1, ..., 0: x_l = s_l / R[l][l], then
+// s_i -= R[i][l] x_l for every i < l.  Row i's running sum lives in shared memory and is only
+// ever touched by thread i mod blockDim, so the one cross-thread value of a step is x_l
+// (double-buffered, one barrier per step); the reads of column l of R are coalesced.  Computed
+// in TC; R is read as TI and X written as TO.
+constexpr int64_t TRI_COLS_SMEM = 48 * 1024;
+template <class TI, class TO, class TC>
+__global__ void k_tri_inv_cols(const TI* __restrict__ R, int64_t ldr, int64_t k,
+                               TO* __restrict__ X, int64_t ldx) {
+    extern __shared__ __align__(16) unsigned char tri_smem[];
+    TC* s = reinterpret_cast<TC*>(tri_smem);
+    __shared__ TC xs[2];
+    const int64_t c = blockIdx.x;
+    const int t = threadIdx.x, nt = blockDim.x;
+    for (int64_t i = t; i <= c; i += nt) s[i] = i == c ? TC(1) : TC(0);
+    for (int64_t i = c + 1 + t; i < k; i += nt) X[i + c * ldx] = TO(0);
+    for (int64_t l = c; l >= 0; --l) {
+        if (t == int(l % nt)) {            // the owner of row l: s_l is final
+            const TC x = s[l] / TC(R[l + l * ldr]);
+            xs[l & 1] = x;
+            X[l + c * ldx] = TO(x);
+        }
+        __syncthreads();
+        const TC x = xs[l & 1];
+        const TI* Rl = R + l * ldr;
+        for (int64_t i = t; i < l; i += nt) s[i] = fma(-TC(Rl[i]), x, s[i]);
+    }
+}
+
+template <class TI, class TO, class TC>
+void launch_tri_inv(cudaStream_t st, const TI* R, int64_t ldr, int64_t k, TO* X, int64_t ldx) {
+    const int nt = k <= 64 ? 64 : (k <= 128 ? 128 : 256);
+    k_tri_inv_cols<TI, TO, TC><<<unsigned(k), nt, size_t(k) * sizeof(TC), st>>>(R, ldr, k, X, ldx);
 }
 }  // namespace
 
@@ -384,9 +421,27 @@ void axpy(cudaStream_t st, bool f64, int64_t rows, int64_t cols, double alpha, c
 void tri_inv_big(cudaStream_t st, bool f64, const void* R, int64_t ldr, int64_t k, void* X,
                  int64_t ldx) {
     if (k <= 0) return;
-    const unsigned g = unsigned(cdiv(k, 64));
-    if (f64) k_tri_inv_big<double><<<g, 64, 0, st>>>(reinterpret_cast<const double*>(R), ldr, k, reinterpret_cast<double*>(X), ldx);
-    else k_tri_inv_big<float><<<g, 64, 0, st>>>(reinterpret_cast<const float*>(R), ldr, k, reinterpret_cast<float*>(X), ldx);
+    if (k * int64_t(f64 ? sizeof(double) : sizeof(float)) <= TRI_COLS_SMEM) {
+        if (f64)
+            launch_tri_inv<double, double, double>(st, reinterpret_cast<const double*>(R), ldr, k,
+                                                   reinterpret_cast<double*>(X), ldx);
+        else
+            launch_tri_inv<float, float, float>(st, reinterpret_cast<const float*>(R), ldr, k,
+                                                reinterpret_cast<float*>(X), ldx);
+    } else {
+        const unsigned g = unsigned(cdiv(k, 64));
+        if (f64) k_tri_inv_big<double><<<g, 64, 0, st>>>(reinterpret_cast<const double*>(R), ldr, k, reinterpret_cast<double*>(X), ldx);
+        else k_tri_inv_big<float><<<g, 64, 0, st>>>(reinterpret_cast<const float*>(R), ldr, k, reinterpret_cast<float*>(X), ldx);
+    }
+    QB_LAUNCHED();
+}
+
+void tri_inv_from_f64(cudaStream_t st, bool f64, const double* R, int64_t ldr, int64_t k, void* X,
+                      int64_t ldx) {
+    if (k <= 0) return;
+    if (k > TRI_COLS_SMEM / int64_t(sizeof(double))) throw Error{QB_ERR_INVALID_ARG, "triangular inverse too large"};
+    if (f64) launch_tri_inv<double, double, double>(st, R, ldr, k, reinterpret_cast<double*>(X), ldx);
+    else launch_tri_inv<double, float, double>(st, R, ldr, k, reinterpret_cast<float*>(X), ldx);
     QB_LAUNCHED();
 }
 }  // namespace qb

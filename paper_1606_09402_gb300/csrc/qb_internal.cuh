@@ -196,6 +196,10 @@ void axpy(cudaStream_t st, bool f64, int64_t rows, int64_t cols, double alpha, c
 // X = R^-1 for upper-triangular k x k R (any k)
 void tri_inv_big(cudaStream_t st, bool f64, const void* R, int64_t ldr, int64_t k, void* X,
                  int64_t ldx);
+// X = R^-1 for a float64 upper-triangular k x k R (k <= 6144), computed in float64 and written as
+// float64 (f64) or float32
+void tri_inv_from_f64(cudaStream_t st, bool f64, const double* R, int64_t ldr, int64_t k, void* X,
+                      int64_t ldx);
 
 // ------------------------------------------------------------------------------------ panel
 // Small b x b float64 matrices are column-major with ld = 64.

@@ -72,7 +72,24 @@ def test_autograd_function(small):
     assert np.linalg.norm(Ad.grad.cpu().numpy() - ref) <= 1e-10 * np.linalg.norm(ref)
 
 
-@pytest.mark.parametrize("m,n,k", [(2048, 1536, 64), (8192, 8192, 256)])
+def test_fixed_rank_fp64_ragged_panels():
+    """k = 150: three panels (64, 64, 22) of the blocked QR, the multi-panel Gram-Schmidt, and the
+    column-parallel triangular inverse of the backward at k > 128."""
+    m, n, k = 700, 500, 150
+    A = synth.dense_from_spectrum(m, n, synth.sigma_pow(n, 1.0), seed=12)
+    GQ, GB = synth.cotangents(m, n, k, seed=13)
+    Ad = torch.tensor(A).cuda()
+    Q, B, R = qb.qb_fixed_rank_fwd(Ad, k, 4)
+    Qr, Br, Rr = oracle.qb_fixed_rank(A, k, 4)
+    assert np.linalg.norm((Q @ B).cpu().numpy() - Qr @ Br) / np.linalg.norm(A) <= 1e-10
+    assert np.linalg.norm(Q.cpu().numpy() - Qr) <= 1e-9 * np.sqrt(k)
+    assert np.linalg.norm(R.cpu().numpy() - Rr) <= 1e-10 * np.linalg.norm(Rr)
+    GA = qb.qb_fixed_rank_bwd(Ad, k, 4, Q, R, torch.tensor(GQ).cuda(), torch.tensor(GB).cuda())
+    ref = oracle.qb_fixed_rank_adjoint(A, k, 4, GQ, GB)
+    assert np.linalg.norm(GA.cpu().numpy() - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("m,n,k", [(2048, 1536, 64), (1000, 904, 150), (8192, 8192, 256)])
 def test_fixed_rank_mixed_bf16(m, n, k):
     """BF16 storage with float32 accumulation against the float64 oracle evaluated on the same
     (bf16-valued) A and the same bf16-rounded Omega."""
@@ -88,5 +105,7 @@ def test_fixed_rank_mixed_bf16(m, n, k):
     ref = oracle.qb_fixed_rank_adjoint(A64, k, 9, GQ, GB, Omega=Om)
     QB = (Q.double() @ B.double()).cpu().numpy()
     assert np.linalg.norm(QB - Qr @ Br) / np.linalg.norm(A64) <= 1e-5
+    Rr = oracle.qb_fixed_rank(A64, k, 9, Omega=Om)[2]
+    assert np.linalg.norm(R.double().cpu().numpy() - Rr) <= 5e-4 * np.linalg.norm(Rr)
     err = np.linalg.norm(GA.double().cpu().numpy() - ref) / np.linalg.norm(ref)
     assert err <= 2e-3, err
