@@ -864,31 +864,6 @@ __global__ void k_identity(double* R, int bi) {
     }
 }
 
-__global__ void k_tri_inv(const double* __restrict__ Rg, int bi, double* __restrict__ Xg) {
-    extern __shared__ double smem[];
-    double (*R)[LDS] = reinterpret_cast<double (*)[LDS]>(smem);
-    double (*X)[LDS] = reinterpret_cast<double (*)[LDS]>(smem + MAXB * LDS);
-    for (int e = threadIdx.x; e < MAXB * MAXB; e += blockDim.x) {
-        const int i = e % MAXB, j = e / MAXB;
-        R[i][j] = Rg[i + j * MAXB];
-        X[i][j] = 0.0;
-    }
-    __syncthreads();
-    for (int c = threadIdx.x; c < bi; c += blockDim.x) {
-        X[c][c] = 1.0 / R[c][c];
-        for (int i = c - 1; i >= 0; --i) {
-            double s = 0.0;
-            for (int l = i + 1; l <= c; ++l) s = fma(R[i][l], X[l][c], s);
-            X[i][c] = -s / R[i][i];
-        }
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < MAXB * MAXB; e += blockDim.x) {
-        const int i = e % MAXB, j = e / MAXB;
-        Xg[i + j * MAXB] = X[i][j];
-    }
-}
-
 // P (rows x bi) <- P * Rinv, in place, 128 rows per CTA (each CTA owns its rows).  Thread t
 // computes rows t % 64 and t % 64 + 64 for columns 16 (t / 64) .. 16 (t / 64) + 15; Rinv rows are
 // read as broadcast vectors.  Terms run l = 0, 1, ... (the zero lower part of Rinv adds exact
@@ -1026,7 +1001,6 @@ template <class TF, class TI>
 constexpr size_t chol_smem() {
     return (2 * sizeof(TF) + 2 * sizeof(TI)) * MAXB * CLD;
 }
-constexpr size_t TRI_SMEM = sizeof(double) * 2 * MAXB * LDS;
 
 
 void chol_rinv(cudaStream_t st, const double* W, int bi, double tau_rel, double* R, double* Rinv,
@@ -1119,12 +1093,6 @@ bool cholqr_coop(cudaStream_t st, float* P, int64_t ldp, int64_t rows, int bi, i
 
 void set_identity(cudaStream_t st, double* R, int bi) {
     k_identity<<<1, 256, 0, st>>>(R, bi);
-    QB_LAUNCHED();
-}
-
-void tri_inv(cudaStream_t st, const double* R, int bi, double* Rinv) {
-    smem_limit_once<k_tri_inv>(TRI_SMEM);
-    k_tri_inv<<<1, 64, TRI_SMEM, st>>>(R, bi, Rinv);
     QB_LAUNCHED();
 }
 

@@ -229,8 +229,6 @@ bool cholqr_coop(cudaStream_t st, float* P, int64_t ldp, int64_t rows, int bi, i
 void chol_rinv(cudaStream_t st, const double* W, int bi, double tau_rel, double* R,
                double* Rinv, double* R_acc, int* flags, CholPrec prec);
 void set_identity(cudaStream_t st, double* R, int bi);
-// R_out = Rinv of an upper-triangular R (bi x bi)
-void tri_inv(cudaStream_t st, const double* R, int bi, double* Rinv);
 // P (m x bi, col-major, f32/f64) <- P * Rinv (upper triangular)
 void apply_rinv(cudaStream_t st, bool f64, void* P, int64_t ldp, int64_t m, int bi,
                 const double* Rinv);
