@@ -54,12 +54,13 @@ def parse():
     ap.add_argument("--steps-only", action="store_true",
                     help="time the mixed randQB_FP steps only (no side measurements); for profiling")
     ap.add_argument("--profile-small", nargs="?", const="fp", default=None,
-                    choices=["fp", "ei", "csr", "coo", "batched", "adjoint", "svd"],
+                    choices=["fp", "ei", "csr", "coo", "batched", "adjoint", "adjoint8192", "svd"],
                     help="small cases for ncu section captures: two mixed randQB_FP (fp) or "
                          "randQB_EI (ei) factorisations of a 16384 x 8192 matrix; the sparse "
                          "passes on a 50000 x 25000 Zipf CSR / COO matrix (csr, coo); a batch of "
                          "32 matrices (batched); the 4096 x 4096 fixed-rank map and adjoint "
-                         "(adjoint); the SVD from a rank-1024 QB (svd)")
+                         "(adjoint; adjoint8192 at the benchmark's 8192 x 8192 for one-pass "
+                         "launch lists); the SVD from a rank-1024 QB (svd)")
     return ap.parse_args()
 
 
@@ -772,8 +773,8 @@ def run_profile_other(kind):
             res = qb.qb_ei_batched(mats, [s.tol for s in specs], seed=9402)
             torch.cuda.synchronize()
             print("ranks", [r[2].rank for r in res[:8]], flush=True)
-    elif kind == "adjoint":
-        m = n = 4096
+    elif kind in ("adjoint", "adjoint8192"):
+        m = n = 4096 if kind == "adjoint" else 8192
         k = 256
         A = synth.dense_from_spectrum_torch(m, n, 1.0 / np.arange(1, n + 1), 1606, dev,
                                             dtype=torch.float32).to(torch.bfloat16)

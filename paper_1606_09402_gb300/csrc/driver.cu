@@ -270,6 +270,14 @@ struct Ctx {
         }
         tn(k, bi, m, 1.0, Q, ldq, X, ldx, beta, T, ldt, acc);
     }
+    // [T1 | T2] (k x 2 bi, ld ldt) += Q^T [X1 | X2] (X1, X2: m x bi) in one pass over Q's shadows
+    // (tensor-core path only)
+    void qt_x2(int64_t k, int bi, int64_t m, const void* X1, int64_t ldx1, const void* X2,
+               int64_t ldx2, void* T, int64_t ldt) {
+        tc_prec_gemm2(st, false, qs, 3, ldqs, k, m, reinterpret_cast<const float*>(X1), ldx1, bi,
+                      reinterpret_cast<const float*>(X2), ldx2, bi, 1.f, 1.f,
+                      reinterpret_cast<float*>(T), ldt, tcs, tcs_bytes);
+    }
     // Y (m x bi) += alpha Q T, T k x bi
     void q_t(int64_t k, int bi, const void* Q, int64_t ldq, int64_t m, double alpha, const void* T,
              int64_t ldt, void* Y, int64_t ldy, Acc acc) {
@@ -734,6 +742,7 @@ struct Bufs {
     char* T1 = nullptr;   // cap x lt
     char* C2 = nullptr;   // cap x b
     char* Tw = nullptr;   // lt x b (orth_wide)
+    char* TT = nullptr;   // cap x 2b (FP, tensor-core path): [Q^T Q_i | B Omega_i + Q^T Y_i]
 };
 
 void reserve_all(Arena& ar, Ctx& c, AOp& A, const Plan& p, bool fp, Bufs& bf) {
@@ -764,6 +773,8 @@ void reserve_all(Arena& ar, Ctx& c, AOp& A, const Plan& p, bool fp, Bufs& bf) {
         c.ldbs = align_up(p.n, 8);
         for (int t = 0; t < 3; ++t) c.qs[t] = ar.get<bf16>(c.ldqs * cap);
         for (int t = 0; t < 3; ++t) c.bs[t] = ar.get<bf16>(c.ldbs * cap);
+        // the merged Q^T [Q_i | Y_i] product splits 2b columns into the scratch sized for lt
+        if (fp && p.lt >= 2 * p.b) bf.TT = ar.get<char>(cap * 2 * p.b * es);
     }
 }
 
@@ -912,12 +923,17 @@ void run_fp(Ctx& c, AOp& A, const Plan& p, const qb_opts& o, Bufs& bf, void* Q, 
                     h_done += hw;
                 }
                 const char* Om_i = c.col(bf.Om, n, c0);
+                // with the tensor-core products, Q^T Q_i (re-orthogonalisation) and Q^T Y_i (B_i
+                // formula) come from one pass over Q's shadows: T1 then sits right after the
+                // coefficients' bi columns in TT
+                const bool merged = k > 0 && bf.TT && c.tcg();
+                char* T1 = merged ? bf.TT + size_t(bi) * size_t(k) * c.es : bf.T1;   // ld k
                 // Y_i = G_i - Q (B Omega_i), kept for the B_i formula
                 c.copy_cols_(c.col(bf.G, m, c0), m, m, bi, bf.Ys, m);
                 if (k > 0) {
                     Ctx::Scope sc(c, PH_PROJ);
-                    c.b_x(k, bi, B, ldb, n, Om_i, n, 0.0, bf.T1, k, c.acc_proj);
-                    c.q_t(k, bi, Q, ldq, m, -1.0, bf.T1, k, bf.Ys, m, c.acc_proj);
+                    c.b_x(k, bi, B, ldb, n, Om_i, n, 0.0, T1, k, c.acc_proj);
+                    c.q_t(k, bi, Q, ldq, m, -1.0, T1, k, bf.Ys, m, c.acc_proj);
                 }
                 // [Q_i, R_i] = qr(Y_i) in the slot of Q_i; the inverses of the factors go to Rchain
                 char* Qi = c.col(Q, ldq, k);
@@ -928,7 +944,14 @@ void run_fp(Ctx& c, AOp& A, const Plan& p, const qb_opts& o, Bufs& bf, void* Q, 
                 else c.cholqr2(Qi, ldq, m, bi, true);
                 if (k > 0) {
                     // [Q_i, R~_i] = qr(Q_i - Q (Q^T Q_i)), R_i = R~_i R_i
-                    c.reorth_q(k, Q, ldq, m, Qi, ldq, bi, bf.C2);
+                    if (merged) {
+                        Ctx::Scope sp(c, PH_PROJ);
+                        QB_CUDA(cudaMemsetAsync(bf.TT, 0, size_t(bi) * size_t(k) * c.es, c.st));
+                        c.qt_x2(k, bi, m, Qi, ldq, bf.Ys, m, bf.TT, k);   // T1 += Q^T Y_i too
+                        c.q_t(k, bi, Q, ldq, m, -1.0, bf.TT, k, Qi, ldq, c.acc_proj);
+                    } else {
+                        c.reorth_q(k, Q, ldq, m, Qi, ldq, bi, bf.C2);
+                    }
                     c.cholqr2(Qi, ldq, m, bi, true);
                 }
                 char* Bs = c.col(B, ldb, k);
@@ -939,8 +962,9 @@ void run_fp(Ctx& c, AOp& A, const Plan& p, const qb_opts& o, Bufs& bf, void* Q, 
                     char* S = c.col(bf.H, n, c0);
                     if (k > 0) {
                         // T1 still holds B Omega_i from the projection of Y_i
-                        c.qt_x(k, bi, Q, ldq, m, bf.Ys, m, 1.0, bf.T1, k, c.acc_fine); // += Q^T Y_i
-                        c.bt_t(k, bi, B, ldb, n, -1.0, bf.T1, k, S, n, c.acc_fine);    // S^T -= B^T T1
+                        if (!merged)
+                            c.qt_x(k, bi, Q, ldq, m, bf.Ys, m, 1.0, T1, k, c.acc_fine); // += Q^T Y_i
+                        c.bt_t(k, bi, B, ldb, n, -1.0, T1, k, S, n, c.acc_fine);        // S^T -= B^T T1
                     }
                     // B_i = R_i^-T S  <=>  B_i^T = S^T R_i^-1, R_i the product of the CholeskyQR
                     // factors (R~_2 R~_1 R_1 on the mixed path, R~_2 R~_1 R_2 R_1 on the float64

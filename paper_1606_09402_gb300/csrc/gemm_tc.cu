@@ -1111,17 +1111,40 @@ void tc_trans(cudaStream_t st, const bf16* A_hi, const bf16* A_lo, int64_t lda, 
 void tc_prec_gemm(cudaStream_t st, bool trans, const bf16* const* A, int na, int64_t lda,
                   int64_t M, int64_t K, const float* V, int64_t ldv, int64_t N, float alpha,
                   float beta, float* D, int64_t ldd, void* scratch, size_t scratch_bytes) {
+    if (N > 64) throw Error{QB_ERR_INVALID_ARG, "tc_prec_gemm shape"};
+    tc_prec_gemm2(st, trans, A, na, lda, M, K, V, ldv, N, nullptr, 0, 0, alpha, beta, D, ldd,
+                  scratch, scratch_bytes);
+}
+
+// The same product with the operand [V1 | V2] (N1 + N2 <= 128 columns, each block column-major
+// with its own ld): both are split into one scratch operand and the output has N1 + N2 columns.
+// Above 64 columns the tile is 128 wide (trans = false, three A terms only), so each A tile is
+// read once for all the columns.
+void tc_prec_gemm2(cudaStream_t st, bool trans, const bf16* const* A, int na, int64_t lda,
+                   int64_t M, int64_t K, const float* V1, int64_t ldv1, int64_t N1,
+                   const float* V2, int64_t ldv2, int64_t N2, float alpha, float beta, float* D,
+                   int64_t ldd, void* scratch, size_t scratch_bytes) {
+    const int64_t N = N1 + std::max<int64_t>(N2, 0);
     if (M <= 0 || N <= 0) return;
-    if (na < 1 || na > 3 || N > 64 || lda % 8 != 0)
+    if (na < 1 || na > 3 || N1 < 0 || N > 128 || (N2 > 0 && !V2) || lda % 8 != 0)
         throw Error{QB_ERR_INVALID_ARG, "tc_prec_gemm shape"};
     Scratch s = carve(scratch, scratch_bytes, K, N);
     const int64_t ldo = align_up(std::max<int64_t>(K, 1), 8);
     if (K > 0) {
-        k_split3_bf16<<<unsigned(cdiv(K * N, 256)), 256, 0, st>>>(V, ldv, K, N, s.vhi, s.vmid, s.vlo,
-                                                                  ldo);
-        QB_LAUNCHED();
+        if (N1 > 0) {
+            k_split3_bf16<<<unsigned(cdiv(K * N1, 256)), 256, 0, st>>>(V1, ldv1, K, N1, s.vhi,
+                                                                       s.vmid, s.vlo, ldo);
+            QB_LAUNCHED();
+        }
+        if (N2 > 0) {
+            const int64_t o = N1 * ldo;
+            k_split3_bf16<<<unsigned(cdiv(K * N2, 256)), 256, 0, st>>>(V2, ldv2, K, N2, s.vhi + o,
+                                                                       s.vmid + o, s.vlo + o, ldo);
+            QB_LAUNCHED();
+        }
     }
-    const int bn = 64;
+    const int bn = N > 64 ? 128 : 64;
+    if (bn == 128 && (trans || na != 3)) throw Error{QB_ERR_INVALID_ARG, "tc_prec_gemm shape"};
     Params p{};
     p.M = int(M);
     p.N = int(N);
@@ -1150,6 +1173,8 @@ void tc_prec_gemm(cudaStream_t st, bool trans, const bf16* const* A, int na, int
         if (na == 3) run_prec<64, true, 3, 3>(st, am[0], am[1], am[2], b0, b1, b2, p, G);
         else if (na == 2) run_prec<64, true, 2, 3>(st, am[0], am[1], am[2], b0, b1, b2, p, G);
         else run_prec<64, true, 1, 3>(st, am[0], am[1], am[2], b0, b1, b2, p, G);
+    } else if (bn == 128) {
+        run_prec<128, false, 3, 3>(st, am[0], am[1], am[2], b0, b1, b2, p, G);
     } else {
         if (na == 3) run_prec<64, false, 3, 3>(st, am[0], am[1], am[2], b0, b1, b2, p, G);
         else if (na == 2) run_prec<64, false, 2, 3>(st, am[0], am[1], am[2], b0, b1, b2, p, G);

@@ -155,6 +155,12 @@ void tc_trans(cudaStream_t st, const bf16* A_hi, const bf16* A_lo, int64_t lda, 
 void tc_prec_gemm(cudaStream_t st, bool trans, const bf16* const* A, int na, int64_t lda,
                   int64_t M, int64_t K, const float* V, int64_t ldv, int64_t N, float alpha,
                   float beta, float* D, int64_t ldd, void* scratch, size_t scratch_bytes);
+// The same with V = [V1 | V2] (two column blocks with their own ld, N1 + N2 <= 128): one pass
+// over A's terms for both; the scratch must hold the split of K x (N1 + N2).
+void tc_prec_gemm2(cudaStream_t st, bool trans, const bf16* const* A, int na, int64_t lda,
+                   int64_t M, int64_t K, const float* V1, int64_t ldv1, int64_t N1,
+                   const float* V2, int64_t ldv2, int64_t N2, float alpha, float beta, float* D,
+                   int64_t ldd, void* scratch, size_t scratch_bytes);
 // hi + mid + lo == X exactly (three bf16 terms of a float32 column-major block)
 void split3_bf16(cudaStream_t st, const float* X, int64_t ldx, int64_t rows, int64_t cols, bf16* hi,
                  bf16* mid, bf16* lo, int64_t ldo);
