@@ -368,6 +368,82 @@ __global__ void k_tri_inv_cols(const TI* __restrict__ R, int64_t ldr, int64_t k,
     }
 }
 
+// Columns TRI_WARPS * blockIdx.x + warp of X = R^-1, one warp per column, for k small enough that
+// the upper triangle of R fits in shared memory: it is staged packed (column l at l (l + 1) / 2,
+// rows 0..l; eight loads in flight per thread) with the reciprocals of the diagonal beside it,
+// and lane j keeps the running sums of rows j, j + 32, ... in registers.  Step l
+// (l = c, ..., 0): every lane takes s_l from its owner by a shuffle and forms
+// x_l = s_l * (1 / R[l][l]) itself, then updates its rows i < l; after the staging there is no
+// block barrier.
+constexpr int TRI_WARPS = 8;
+constexpr int TRI_RPL = 10;                  // rows per lane: k <= 320
+constexpr int TRI_STAGE_UNROLL = 8;
+constexpr int64_t TRI_WARP_SMEM = 208 * 1024;
+template <class TI, class TO, class TC>
+__global__ void __launch_bounds__(TRI_WARPS * 32)
+k_tri_inv_warp(const TI* __restrict__ R, int64_t ldr, int k, TO* __restrict__ X, int64_t ldx) {
+    extern __shared__ __align__(16) unsigned char tri_smem[];
+    TC* rdiag = reinterpret_cast<TC*>(tri_smem);   // k reciprocals of the diagonal
+    TC* Rs = rdiag + k;                            // packed upper triangle
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int last = min(k - 1, int(blockIdx.x + 1) * TRI_WARPS - 1);
+    const int T = (last + 1) * (last + 2) / 2;
+    const int nt = blockDim.x;
+    for (int e0 = threadIdx.x; e0 < T; e0 += TRI_STAGE_UNROLL * nt) {
+        TI v[TRI_STAGE_UNROLL];
+#pragma unroll
+        for (int u = 0; u < TRI_STAGE_UNROLL; ++u) {
+            const int e = e0 + u * nt;
+            if (e < T) {
+                int l = int((sqrtf(8.f * float(e) + 1.f) - 1.f) * 0.5f);
+                while (l > 0 && l * (l + 1) / 2 > e) --l;
+                while ((l + 1) * (l + 2) / 2 <= e) ++l;
+                v[u] = R[(e - l * (l + 1) / 2) + int64_t(l) * ldr];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < TRI_STAGE_UNROLL; ++u) {
+            const int e = e0 + u * nt;
+            if (e < T) Rs[e] = TC(v[u]);
+        }
+    }
+    for (int l = threadIdx.x; l <= last; l += nt) rdiag[l] = TC(1) / TC(R[l + int64_t(l) * ldr]);
+    __syncthreads();
+    const int c = int(blockIdx.x) * TRI_WARPS + warp;
+    if (c >= k) return;   // the whole warp
+    TC s[TRI_RPL];
+#pragma unroll
+    for (int j = 0; j < TRI_RPL; ++j) s[j] = lane + 32 * j == c ? TC(1) : TC(0);
+    for (int i = c + 1 + lane; i < k; i += 32) X[i + int64_t(c) * ldx] = TO(0);
+    for (int l = c; l >= 0; --l) {
+        const TC* col = Rs + l * (l + 1) / 2;
+        const int jl = l >> 5;
+        TC sl = TC(0);
+#pragma unroll
+        for (int j = 0; j < TRI_RPL; ++j)
+            if (j == jl) sl = s[j];
+        sl = __shfl_sync(0xffffffffu, sl, l & 31);
+        const TC x = sl * rdiag[l];
+        if (lane == (l & 31)) X[l + int64_t(c) * ldx] = TO(x);
+#pragma unroll
+        for (int j = 0; j < TRI_RPL; ++j)
+            if (lane + 32 * j < l) s[j] = fma(-col[lane + 32 * j], x, s[j]);
+    }
+}
+
+template <class TC>
+bool tri_warp_fits(int64_t k) {
+    return k <= 32 * TRI_RPL && (k * (k + 1) / 2 + k) * int64_t(sizeof(TC)) <= TRI_WARP_SMEM;
+}
+
+template <class TI, class TO, class TC>
+void launch_tri_inv_warp(cudaStream_t st, const TI* R, int64_t ldr, int64_t k, TO* X, int64_t ldx) {
+    smem_limit_once<k_tri_inv_warp<TI, TO, TC>>(size_t(TRI_WARP_SMEM));
+    const size_t sm = size_t(k * (k + 1) / 2 + k) * sizeof(TC);
+    k_tri_inv_warp<TI, TO, TC><<<unsigned(cdiv(k, TRI_WARPS)), TRI_WARPS * 32, sm, st>>>(
+        R, ldr, int(k), X, ldx);
+}
+
 template <class TI, class TO, class TC>
 void launch_tri_inv(cudaStream_t st, const TI* R, int64_t ldr, int64_t k, TO* X, int64_t ldx) {
     const int nt = k <= 64 ? 64 : (k <= 128 ? 128 : 256);
@@ -421,7 +497,14 @@ void axpy(cudaStream_t st, bool f64, int64_t rows, int64_t cols, double alpha, c
 void tri_inv_big(cudaStream_t st, bool f64, const void* R, int64_t ldr, int64_t k, void* X,
                  int64_t ldx) {
     if (k <= 0) return;
-    if (k * int64_t(f64 ? sizeof(double) : sizeof(float)) <= TRI_COLS_SMEM) {
+    if (f64 ? tri_warp_fits<double>(k) : tri_warp_fits<float>(k)) {
+        if (f64)
+            launch_tri_inv_warp<double, double, double>(st, reinterpret_cast<const double*>(R), ldr,
+                                                        k, reinterpret_cast<double*>(X), ldx);
+        else
+            launch_tri_inv_warp<float, float, float>(st, reinterpret_cast<const float*>(R), ldr, k,
+                                                     reinterpret_cast<float*>(X), ldx);
+    } else if (k * int64_t(f64 ? sizeof(double) : sizeof(float)) <= TRI_COLS_SMEM) {
         if (f64)
             launch_tri_inv<double, double, double>(st, reinterpret_cast<const double*>(R), ldr, k,
                                                    reinterpret_cast<double*>(X), ldx);
@@ -439,9 +522,11 @@ void tri_inv_big(cudaStream_t st, bool f64, const void* R, int64_t ldr, int64_t 
 void tri_inv_from_f64(cudaStream_t st, bool f64, const double* R, int64_t ldr, int64_t k, void* X,
                       int64_t ldx) {
     if (k <= 0) return;
-    if (k > TRI_COLS_SMEM / int64_t(sizeof(double))) throw Error{QB_ERR_INVALID_ARG, "triangular inverse too large"};
-    if (f64) launch_tri_inv<double, double, double>(st, R, ldr, k, reinterpret_cast<double*>(X), ldx);
-    else launch_tri_inv<double, float, double>(st, R, ldr, k, reinterpret_cast<float*>(X), ldx);
+    if (!tri_warp_fits<double>(k)) throw Error{QB_ERR_INVALID_ARG, "triangular inverse too large"};
+    if (f64)
+        launch_tri_inv_warp<double, double, double>(st, R, ldr, k, reinterpret_cast<double*>(X), ldx);
+    else
+        launch_tri_inv_warp<double, float, float>(st, R, ldr, k, reinterpret_cast<float*>(X), ldx);
     QB_LAUNCHED();
 }
 }  // namespace qb

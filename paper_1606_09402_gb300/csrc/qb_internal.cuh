@@ -202,8 +202,8 @@ void axpy(cudaStream_t st, bool f64, int64_t rows, int64_t cols, double alpha, c
 // X = R^-1 for upper-triangular k x k R (any k)
 void tri_inv_big(cudaStream_t st, bool f64, const void* R, int64_t ldr, int64_t k, void* X,
                  int64_t ldx);
-// X = R^-1 for a float64 upper-triangular k x k R (k <= 6144), computed in float64 and written as
-// float64 (f64) or float32
+// X = R^-1 for a float64 upper-triangular k x k R (k <= 229), written as float64 (f64, computed
+// in float64) or float32 (computed in float32)
 void tri_inv_from_f64(cudaStream_t st, bool f64, const double* R, int64_t ldr, int64_t k, void* X,
                       int64_t ldx);
 
