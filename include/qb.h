@@ -285,6 +285,11 @@ int32_t qb_ei_batched(int32_t count, const qb_dense* As, const double* tols,
  *             Y is not stored: Omega is regenerated from the seed.
  *   prec QB_PREC_FP64 (float64 A and buffers) or QB_PREC_MIXED (bf16 / bf16x2 A, float32
  *   buffers, tensor-core sketch, round-to-nearest B pass).  1 <= k <= min(m, n).
+ *   The QR of Y is blocked over panels of 64 columns: each panel is projected twice against the
+ *   finished ones, then orthonormalised by CholeskyQR2.  On the mixed path the projections run on
+ *   the tensor cores against three-term bf16 copies of the finished panels (float32 accuracy;
+ *   the workspace holds them), and a panel's diagonal block of R is the float32 inverse of the
+ *   product of its two CholeskyQR factors' inverses.
  *   Both calls synchronise the stream before returning.
  * ------------------------------------------------------------------------------------------- */
 size_t qb_fixed_rank_workspace(const qb_dense* A, int64_t k, int32_t prec);
