@@ -126,6 +126,17 @@ int main() {
     check(40000, 512, 20000, 256, 152, modes);   // sketch chunk
     check(20000, 512, 40000, 256, 152, modes);   // power-step transposed chunk
     shapes += 3;
+    // Q^T [Q_i | Y_i] of a randQB_FP block (M = rank so far, N = 2 b_i, K = m; 128-wide tile when
+    // N > 64), and the fixed-rank map's Gram-Schmidt products (M = j0, N = 64, K = m)
+    for (int64_t M : {int64_t(1), int64_t(64), int64_t(200), int64_t(700), int64_t(1439)})
+        for (int64_t N : {int64_t(40), int64_t(100), int64_t(128)}) {
+            check(M, N, 40000, N > 64 ? 128 : 64, 152, modes);
+            ++shapes;
+        }
+    for (int64_t M : {int64_t(64), int64_t(128), int64_t(192)}) {
+        check(M, 64, 8192, 64, 152, modes);
+        ++shapes;
+    }
     std::printf("%d shapes: raster %d, stream-K %d, hybrid %d; %d failures\n", shapes, modes[0],
                 modes[1], modes[2], g_fail);
     return g_fail == 0 && modes[2] > 0 ? 0 : 1;
